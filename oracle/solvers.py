@@ -1,0 +1,199 @@
+"""Solvers and the block preconditioner in FP64.
+
+TEST INFRASTRUCTURE (oracle): see the package docstring.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import cnn as _cnn
+
+
+def direct_solve(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
+    """x = A^{-1} b by sparse LU (the plain definition of the solve every
+    Krylov method of Section 4 converges to)."""
+    return spla.spsolve(A.tocsc(), b)
+
+
+def jacobi_cg(A: sp.spmatrix, b: np.ndarray, tol: float, maxit: int = 100000, x0=None):
+    """Conjugate gradients preconditioned by diag(A)^{-1}.  A is SPD (remark
+    after eq. setB).  Stops when the recursively updated ||r|| / ||b|| <= tol.
+    Returns (x, iterations, true relative residual)."""
+    dinv = 1.0 / A.diagonal()
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A @ x
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, 0, 0.0
+    z = dinv * r
+    p = z.copy()
+    rho = r @ z
+    it = 0
+    while np.linalg.norm(r) / nb > tol and it < maxit:
+        q = A @ p
+        a = rho / (p @ q)
+        x += a * p
+        r -= a * q
+        z = dinv * r
+        rho_new = r @ z
+        p = z + (rho_new / rho) * p
+        rho = rho_new
+        it += 1
+    return x, it, float(np.linalg.norm(b - A @ x) / nb)
+
+
+def fgmres(A, b: np.ndarray, precond, tol: float, restart: int = 30, maxit: int = 10000,
+           history: list | None = None):
+    """Right-preconditioned flexible GMRES(k) (Saad 1993; the solver of Section 4).
+
+    Each cycle: r = b - A x, v_0 = r / ||r||; for j: z_j = P(v_j), w = A z_j,
+    modified Gram-Schmidt against v_0..v_j into column j of the Hessenberg H,
+    Givens rotations keep the least-squares residual estimate |g_{j+1}|;
+    the cycle ends when the estimate <= tol ||b|| or after k steps, then
+    x += Z y with H y = g.  Stops when the true ||b - A x|| / ||b|| <= tol.
+    `precond` maps a vector to a vector (may be nonlinear); None is identity.
+    Returns (x, iterations, true relative residual)."""
+    n = len(b)
+    x = np.zeros(n)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return x, 0, 0.0
+    P = precond if precond is not None else (lambda v: v)
+    it = 0
+    while it < maxit:
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta / nb <= tol:
+            break
+        k = restart
+        V = np.zeros((k + 1, n))
+        Z = np.zeros((k, n))
+        H = np.zeros((k + 1, k))
+        cs = np.zeros(k)
+        sn = np.zeros(k)
+        g = np.zeros(k + 1)
+        g[0] = beta
+        V[0] = r / beta
+        m = 0
+        for j in range(k):
+            Z[j] = P(V[j])
+            w = A @ Z[j]
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = math.hypot(H[j, j], H[j + 1, j])
+            cs[j] = H[j, j] / den
+            sn[j] = H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            m = j + 1
+            if history is not None:
+                history.append(abs(g[j + 1]) / nb)
+            if abs(g[j + 1]) <= tol * nb or it >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:m, :m]), g[:m])
+        x = x + Z[:m].T @ y
+    return x, it, float(np.linalg.norm(b - A @ x) / nb)
+
+
+class BlockPreconditioner:
+    """Q~: inverse of the block upper-triangular part of A, eq. (right-prec)
+    and the two-step back substitution of eq. (twosteps):
+
+        z1 = B11^{-1} r1                       (exact 1D solve)
+        b0 = r0 - beta M01 z1 = r0 + l,  l = beta Pi^T W Psi z1   (eq. decoupled_3d_problem)
+        z0 ~= C^{-1} b0                        (the 3D solve)
+
+    The 3D solve is `mode`:
+        'exact'  -- sparse direct solve with C;
+        'cnn'    -- the network: s = ||b0||, X = [r0/s, l/s, d], z0 = (s/alpha) N(X)
+                    on interior nodes (alpha as in the training loss of Section 5.1,
+                    evaluated for this instance), z0 = r0 on Dirichlet nodes;
+        'jacobi' -- z0 = b0 / diag(C).
+    """
+
+    def __init__(self, prob, mode: str = "cnn", params=None, bf16: bool = True):
+        self.p = prob
+        self.mode = mode
+        self.params = params
+        self.bf16 = bf16
+        self.B11_lu = spla.splu(prob.B11.tocsc())
+        self.C_lu = spla.splu(prob.C.tocsc()) if mode == "exact" else None
+
+    def lift(self, z1):
+        return -self.p.beta * (self.p.M01 @ z1)
+
+    def __call__(self, r):
+        p = self.p
+        r0, r1 = r[:p.n3], r[p.n3:]
+        z1 = self.B11_lu.solve(r1)
+        l = self.lift(z1)
+        b0 = r0 + l
+        if self.mode == "exact":
+            z0 = self.C_lu.solve(b0)
+        elif self.mode == "jacobi":
+            z0 = b0 / p.C.diagonal()
+        else:
+            z0 = network_solve(p, r0, l, self.params, self.bf16)
+        return np.concatenate([z0, z1])
+
+
+def network_input(prob, r0, l):
+    """X = [r0/s, l/s, d] on the grid (3, N+1, N+1, N+1), s = ||r0 + l||."""
+    n = prob.N + 1
+    s = float(np.linalg.norm(r0 + l))
+    if s == 0.0:
+        return None, 0.0
+    X = np.stack([r0 / s, l / s, prob.dist]).reshape(3, n, n, n)
+    return X, s
+
+
+def network_solve(prob, r0, l, params, bf16=True):
+    """z0 = (s/alpha) N([r0/s, l/s, d]) on interior nodes, r0 on Dirichlet nodes."""
+    X, s = network_input(prob, r0, l)
+    if X is None:
+        return r0.copy()
+    Y = _cnn.forward(X, params, bf16=bf16).reshape(-1)
+    z0 = (s / prob.alpha) * Y
+    z0[prob.bd] = r0[prob.bd]
+    return z0
+
+
+def training_loss(prob, r0, l, params, bf16=False, grad=False):
+    """Unsupervised residual loss of one sample (Section 3.2 eq. risk with the
+    squared norm of Section 5.1): with b0 = r0 + l, s = ||b0||,
+        L = || C z0 - b0 ||^2 / ||b0||^2 = || C_II Y_I / alpha - b0_I / s ||^2,
+    z0 = (s/alpha) Y restricted to interior nodes (Dirichlet rows excluded).
+    grad=True also returns the parameter gradients (by hand, eq. of backward)."""
+    p = prob
+    X, s = network_input(p, r0, l)
+    Y, saved = _cnn.forward(X, params, bf16=bf16, keep=True)
+    y = Y.reshape(-1).copy()
+    y[p.bd] = 0.0
+    b_hat = (r0 + l) / s
+    b_hat[p.bd] = 0.0
+    Cy = p.C @ y
+    Cy[p.bd] = 0.0
+    res = Cy / p.alpha - b_hat
+    L = float(res @ res)
+    if not grad:
+        return L
+    dy = (2.0 / p.alpha) * (p.C.T @ res)
+    dy[p.bd] = 0.0
+    n = p.N + 1
+    grads, _ = _cnn.backward(dy.reshape(1, n, n, n), params, saved)
+    return L, grads

@@ -1,0 +1,147 @@
+"""Pins of the oracle solvers and block preconditioner (oracle/solvers.py)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import mdgen
+from oracle import cnn, fem, solvers
+
+
+@pytest.fixture(scope="module")
+def seg16():
+    w = mdgen.WORKLOADS["single_segment_16"]
+    g = mdgen.straight_segment(w["p0"], w["p1"], w["elems"], w["radius"])
+    return fem.Problem(16, g, beta=1.0)
+
+
+@pytest.fixture(scope="module")
+def tree8():
+    return fem.Problem(8, mdgen.random_tree(77, 0, depth=3, elems=4), beta=10.0)
+
+
+def test_direct_solve_manufactured(seg16):
+    rng = np.random.default_rng(0)
+    xm = rng.standard_normal(seg16.n)
+    x = solvers.direct_solve(seg16.A, seg16.A @ xm)
+    assert np.linalg.norm(x - xm) / np.linalg.norm(xm) < 1e-10
+
+
+def test_jacobi_cg_single_segment(seg16):
+    """Single segment, f = 0, g = 1: Jacobi-CG to 1e-10 agrees with the direct solve."""
+    b = seg16.rhs(None, 1.0)
+    x, it, rel = solvers.jacobi_cg(seg16.A, b, 1e-10)
+    assert rel <= 2e-10
+    xd = solvers.direct_solve(seg16.A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-7
+    assert 10 < it < 5000
+
+
+def test_fgmres_exact_preconditioner_one_iteration(tree8):
+    b = tree8.rhs(tree8.source(5), 1.0)
+    lu = sp.linalg.splu(tree8.A.tocsc())
+    x, it, rel = solvers.fgmres(tree8.A, b, lu.solve, 1e-10, restart=10)
+    assert it == 1
+    assert rel < 1e-12
+
+
+def test_fgmres_identity_is_minimal_residual():
+    """With P = I each iterate minimises ||b - A x|| over the Krylov space
+    K_j(A, b): compare with least squares on an explicit orthonormal basis."""
+    p = fem.Problem(4, mdgen.straight_segment((0.3, 0.4, 0.5), (0.7, 0.6, 0.5), 3, 0.05), beta=2.0)
+    A = p.A.toarray()
+    rng = np.random.default_rng(1)
+    b = rng.standard_normal(p.n)
+    hist = []
+    solvers.fgmres(p.A, b, None, 1e-30, restart=12, maxit=12, history=hist)
+    nb = np.linalg.norm(b)
+    K = [b / nb]
+    for j in range(1, 9):
+        Q, _ = np.linalg.qr(np.array(K).T)
+        y, *_ = np.linalg.lstsq(A @ Q, b, rcond=None)
+        best = np.linalg.norm(b - A @ Q @ y) / nb
+        # the power basis loses digits as j grows, hence the loose relative bound
+        assert hist[j - 1] == pytest.approx(best, rel=1e-6, abs=1e-13)
+        K.append(A @ K[-1])
+        K[-1] /= np.linalg.norm(K[-1])
+
+
+def test_fgmres_jacobi_reaches_tolerance(tree8):
+    b = tree8.rhs(tree8.source(9), 1.0)
+    dinv = 1.0 / tree8.A.diagonal()
+    x, it, rel = solvers.fgmres(tree8.A, b, lambda v: dinv * v, 1e-8, restart=30)
+    assert rel <= 1e-8
+    xd = solvers.direct_solve(tree8.A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+
+
+def test_block_preconditioner_inverts_upper_triangular_part(tree8):
+    """Q~ with the exact 3D solve is the inverse of [[C, beta M01], [0, B11]]."""
+    p = tree8
+    U = sp.bmat([[p.C, p.beta * p.M01], [None, p.B11]], format="csr")
+    Q = solvers.BlockPreconditioner(p, mode="exact")
+    x = np.random.default_rng(2).standard_normal(p.n)
+    assert np.linalg.norm(Q(U @ x) - x) / np.linalg.norm(x) < 1e-10
+    # U differs from A only in the lower-left block
+    L = p.A - U
+    assert abs(L[:p.n3, :]).max() == 0
+    assert abs(L[p.n3:, p.n3:]).max() == 0
+
+
+def test_cnn_preconditioner_homogeneous(tree8):
+    """P(c v) = c P(v) for c > 0 (input normalisation by s = ||b0||)."""
+    params = cnn.init_params(3)
+    Q = solvers.BlockPreconditioner(tree8, mode="cnn", params=params, bf16=False)
+    v = np.random.default_rng(3).standard_normal(tree8.n)
+    v[:tree8.n3][tree8.bd] = 0
+    z = Q(v)
+    assert np.allclose(Q(3.5 * v), 3.5 * z, rtol=1e-12, atol=1e-14)
+    # identity rows on Dirichlet nodes
+    v2 = v.copy()
+    v2[:tree8.n3][tree8.bd] = 1.25
+    assert np.all(Q(v2)[:tree8.n3][tree8.bd] == 1.25)
+
+
+def identity_params(offset=10.0):
+    """A network whose output is channel 0 + channel 1 of its input: hidden
+    channel 0 carries x + offset, where GELU(x + offset) = x + offset to FP64
+    rounding for |x| << offset, and the next bias removes the offset."""
+    chans = cnn.CHANNELS
+    params = []
+    for l, (ci, co) in enumerate(zip(chans[:-1], chans[1:])):
+        W = np.zeros((co, ci, 3, 3, 3))
+        b = np.zeros(co)
+        if l == 0:
+            W[0, 0, 1, 1, 1] = 1.0
+            W[0, 1, 1, 1, 1] = 1.0
+        else:
+            W[0, 0, 1, 1, 1] = 1.0
+            b[0] = -offset
+        if l < len(chans) - 2:
+            b[0] += offset
+        params.append((W, b))
+    return params
+
+
+def test_cnn_preconditioner_with_identity_network(tree8):
+    """Plumbing pin: with a network that returns r0/s + l/s, the CNN
+    preconditioner equals z0 = b0 / alpha, z1 = B11^{-1} r1."""
+    p = tree8
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=identity_params(), bf16=False)
+    v = np.random.default_rng(4).standard_normal(p.n)
+    v[:p.n3][p.bd] = 0
+    z = Q(v)
+    z1 = solvers.direct_solve(p.B11, v[p.n3:])
+    b0 = v[:p.n3] - p.beta * (p.M01 @ z1)
+    assert np.allclose(z[p.n3:], z1, rtol=1e-12, atol=1e-14)
+    assert np.max(np.abs(z[:p.n3] - b0 / p.alpha)) <= 1e-12 * np.max(np.abs(b0 / p.alpha))
+
+
+def test_fgmres_cnn_preconditioner_converges(tree8):
+    """FGMRES with the network preconditioner reaches the tolerance and the
+    solution matches the direct solve (identity network, FP64)."""
+    Q = solvers.BlockPreconditioner(tree8, mode="cnn", params=identity_params(), bf16=False)
+    b = tree8.rhs(tree8.source(1), 1.0)
+    x, it, rel = solvers.fgmres(tree8.A, b, Q, 1e-8, restart=30, maxit=3000)
+    assert rel <= 1e-8
+    xd = solvers.direct_solve(tree8.A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
