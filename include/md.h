@@ -1,0 +1,241 @@
+/*
+ * md.h -- C ABI of the GB300 library for the neural-preconditioned solve of
+ * the discretised 3D-1D coupled elliptic problem (arXiv 2505.08491).
+ *
+ * The problem (Section 2, eq. (problem)) couples Q1 diffusion on the unit
+ * cube Omega to a P1 problem on an embedded 1D graph Lambda through the
+ * cross-section average T_Lambda.  Its Galerkin discretisation is the block
+ * system of eq. (mainsys),
+ *
+ *     A u = b,   A = K + beta M,   u = [u0 ; u1],
+ *
+ * u0: Q1 nodal values on the (N+1)^3 grid of the unit cube (x fastest),
+ * u1: P1 nodal values on the 1D mesh of the graph.  The solve is flexible
+ * GMRES (Section 4) right-preconditioned by the block upper-triangular
+ * preconditioner of eq. (twosteps): an exact 1D solve followed by a
+ * convolutional network standing in for the inverse of the 3D block
+ * C = K00 + beta M00 (eq. (decoupled_3d_problem), (matrixC)).
+ *
+ * Conventions shared by every entry point
+ *   - Vectors are DEVICE pointers owned by the caller, laid out as
+ *     [u0 (n3 entries, grid node (i,j,k) at i + (N+1)(j + (N+1)k)) ; u1 (n1)].
+ *   - Handles (md_op, md_cnn, md_batch) own their device memory; only the
+ *     matching *_destroy frees it.
+ *   - md_stream is a cudaStream_t passed as void*.  Calls are asynchronous on
+ *     that stream unless stated; scalar outputs written to host memory are
+ *     valid when the call returns (those calls synchronise the stream).
+ *   - Every call returns an md_status; md_last_error() gives a thread-local
+ *     message for the last failure.  No exception crosses the ABI.  There is
+ *     no CPU fallback: without a usable GPU the calls return MD_ERR_CUDA.
+ *   - Calls on one handle must not overlap on the GPU (a handle keeps scratch
+ *     buffers); order them on one stream or synchronise between streams.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* md_stream;
+typedef struct md_op md_op;
+typedef struct md_cnn md_cnn;
+typedef struct md_batch md_batch;
+
+typedef enum {
+    MD_OK = 0,
+    MD_NOT_CONVERGED = 1,       /* solve ended at maxit above tol; x holds the last iterate */
+    MD_ERR_ARG = -1,            /* invalid argument (sizes, null pointers, graph not a forest ...) */
+    MD_ERR_OOM = -2,            /* device allocation failed */
+    MD_ERR_CUDA = -3,           /* a CUDA runtime call failed (no GPU, launch error ...) */
+    MD_ERR_TIMEOUT = -4,        /* a bounded device-side wait ran out */
+    MD_ERR_NAN = -5,            /* non-finite value where a finite one is required */
+    MD_ERR_IO = -6,             /* file missing, short, or failed checksum */
+    MD_ERR_UNIMPLEMENTED = -7
+} md_status;
+
+typedef enum { MD_FP32 = 0, MD_FP64 = 1 } md_prec;
+
+/* The 1D graph Lambda (Section 2): straight segments between nodes.  The
+ * graph must be a forest (no cycles).  Every edge is split into
+ * elems_per_edge P1 elements of equal length.  Host pointers. */
+typedef struct {
+    int n_nodes;
+    const double* xyz;          /* n_nodes * 3 coordinates inside (0,1)^3 */
+    int n_edges;
+    const int* edges;           /* n_edges * 2 node ids */
+    int elems_per_edge;         /* >= 1 */
+} md_graph;
+
+/* Coefficients of eq. (problem).  NULL selects k_omega = 1, sigma_omega = 0,
+ * k_lambda = 1.  The 1D diffusion coefficient used is k_lambda * pi R^2 (the
+ * |D| weight of a_Lambda, eq. (alambda)). */
+typedef struct {
+    double k_omega;
+    double sigma_omega;
+    double k_lambda;
+} md_params;
+
+/* Sizes of an assembled instance. */
+typedef struct {
+    int N;                      /* Q1 elements per cube edge */
+    int n3;                     /* (N+1)^3 grid nodes */
+    int n1;                     /* 1D mesh nodes */
+    int nq;                     /* 1D quadrature points (2 per element) */
+    int n_touch;                /* grid nodes reached by the averaging operator */
+    long long n;                /* n3 + n1 */
+    double alpha;               /* ||diag(C_II)||_2 / sqrt(#interior nodes), Section 5.1 */
+    double beta;
+} md_op_info_t;
+
+/* ---- assembly ------------------------------------------------------------
+ * md_assemble -- eq. (mainsys), Section 2.1.  Builds, for grid N (>= 2) and
+ * the graph with radius R (> 0) and coupling beta (>= 0; the factor 2 pi eps
+ * of eq. (mainsys)):
+ *   K00: the Q1 stiffness (+ sigma mass) of a_Omega, applied matrix-free as a
+ *        27-point stencil, homogeneous Dirichlet rows/columns on the cube
+ *        boundary (identity there);
+ *   Pi:  the cross-section average at 2 Gauss points per 1D element, each
+ *        the mean of the trilinear interpolant at 8 circle points;
+ *   W, Psi, K1 and the tree LDL^T factorisation of B11 = kappa K1 + beta
+ *        Psi^T W Psi; the distance field d_h (Section 2.1) on the grid.
+ * Host geometry runs in FP64 on the CPU; d_h and diag(A) are computed on the
+ * GPU.  Synchronous.  *out receives a handle freed by md_op_destroy. */
+md_status md_assemble(int N, const md_graph* g, double radius, double beta,
+                      const md_params* p, md_op** out);
+void md_op_destroy(md_op* op);
+md_status md_op_get_info(const md_op* op, md_op_info_t* info);
+/* Copy the device distance field d_h (n3 floats) into a device buffer. */
+md_status md_op_distance(const md_op* op, float* d, md_stream s);
+
+/* md_rhs -- the load vector of eq. (problem_weak): b0 = M_Omega f (Q1 mass
+ * times nodal values f, device FP64, n3 entries, NULL for f = 0) with b0 = 0
+ * on Dirichlet nodes, b1_i = g * int_Lambda psi_i ds.  b: device FP64, n. */
+md_status md_rhs(const md_op* op, const double* f, double g, double* b, md_stream s);
+
+/* md_apply -- y = A u, eq. (mainsys), matrix-free.  prec selects FP32 (u, y
+ * float*) or FP64 (double*).  u and y must not alias.  Asynchronous. */
+md_status md_apply(const md_op* op, md_prec prec, const void* u, void* y, md_stream s);
+
+/* ---- the network -----------------------------------------------------------
+ * Six 3x3x3 'same' convolutions 3->32->32->32->32->32->1 with bias, GELU
+ * (x Phi(x)) after layers 1-5 (the fully convolutional hypothesis space of
+ * Section 4.2; channel pattern of this library).  Weights BF16, biases FP32,
+ * FP32 accumulation.
+ * Parameter layout (host float array, MD_CNN_NPARAMS entries): for each layer
+ * l, the weights W[co][ci][kz][ky][kx] (cross-correlation orientation,
+ * Y(p) = b + sum_q W(q) X(p+q), q in {-1,0,1}^3 at index q+1) followed by the
+ * biases b[co].  Weights are rounded to BF16 (nearest even) on upload. */
+#define MD_CNN_LAYERS 6
+#define MD_CNN_NPARAMS 114209
+md_status md_cnn_create(const float* host_params, long long n_params, md_cnn** out);
+md_status md_cnn_get_params(const md_cnn* c, float* host_params, long long n_params);
+void md_cnn_destroy(md_cnn* c);
+/* File: magic "MDCNN001", int64 count, count FP32 values, uint64 FNV-1a
+ * checksum of the value bytes.  MD_ERR_IO on a short file or bad checksum. */
+md_status md_cnn_save(const md_cnn* c, const char* path);
+md_status md_cnn_load(const char* path, md_cnn** out);
+
+/* md_cnn_forward -- raw network pass on `batch` grids of (n+1)^3 nodes:
+ * X: device float, batch * 3 * (n+1)^3, channel-major per sample
+ * (sample, channel, z, y, x); Y: device float, batch * (n+1)^3.  The input
+ * is rounded to BF16 like the preconditioner's.  Asynchronous. */
+md_status md_cnn_forward(const md_cnn* c, int n_nodes_edge, int batch, const float* X, float* Y, md_stream s);
+
+/* md_cnn_backward -- gradients of sum(dY * Y) for the pass above: dparams
+ * (device float, MD_CNN_NPARAMS, overwritten) and optionally dX (device
+ * float, like X, nullable).  Recomputes the forward activations. */
+md_status md_cnn_backward(const md_cnn* c, int n_nodes_edge, int batch, const float* X,
+                          const float* dY, float* dparams, float* dX, md_stream s);
+
+/* md_precondition -- z = Q~ r, eq. (twosteps) with the network as the 3D
+ * solve (eq. (decoupled_3d_problem)):
+ *   z1 = B11^{-1} r1;  l = beta Pi^T W Psi z1;  b0 = r0 + l;  s = ||b0||;
+ *   z0 = (s / alpha) N([r0/s, l/s, d_h]) on interior nodes, z0 = r0 on
+ *   Dirichlet nodes.
+ * cnn == NULL gives the Jacobi preconditioner z = diag(A)^{-1} r.
+ * r, z: device float, n.  Asynchronous. */
+md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream s);
+
+/* ---- solves -----------------------------------------------------------------
+ * md_solve -- solve A x = b to ||b - A x||_2 / ||b||_2 <= tol.
+ *   cnn != NULL: flexible GMRES(restart) (Section 4, Saad 1993), right-
+ *     preconditioned by md_precondition; Krylov vectors FP32, Hessenberg and
+ *     Givens in FP64, and at every restart x += Z y and r = b - A x in FP64.
+ *   cnn == NULL: conjugate gradients with the Jacobi preconditioner in FP64.
+ * b: device FP64 (n); x: device FP64 (n), in: initial guess, out: solution.
+ * maxit bounds the total iterations.  *iters and *relres (host) receive the
+ * iterations done and the final true relative residual.  Synchronises s.
+ * Returns MD_NOT_CONVERGED when maxit is reached above tol. */
+md_status md_solve(const md_op* op, const md_cnn* cnn, const double* b, double* x,
+                   double tol, int restart, int maxit, int* iters, double* relres, md_stream s);
+
+typedef enum {
+    MD_SOLVER_FGMRES_CNN = 0,      /* FGMRES + block preconditioner with the network */
+    MD_SOLVER_FGMRES_JACOBI = 1,   /* FGMRES + diag(A)^{-1} */
+    MD_SOLVER_CG_JACOBI = 2        /* Jacobi-CG, FP64 */
+} md_solver;
+
+/* md_batch -- many instances solved together, one launch per kernel across
+ * all instances (the ensembled stacking of Section 5.7), every restart cycle
+ * replayed as one CUDA graph; instances stop independently on their own
+ * convergence.  Vectors of the batch are concatenated: instance i occupies
+ * [offset[i], offset[i] + n_i) of a batched vector. */
+md_status md_batch_create(int n_ops, const md_op* const* ops, const md_cnn* cnn, md_solver solver,
+                          int restart, md_batch** out);
+void md_batch_destroy(md_batch* b);
+/* host array of n_ops + 1 offsets (the last is the total length) */
+md_status md_batch_offsets(const md_batch* b, long long* offsets);
+/* b_all, x_all: device FP64 batched vectors; x_all in: initial guesses.
+ * iters, relres: host arrays of n_ops (nullable).  Synchronises s. */
+md_status md_batch_solve(md_batch* b, const double* b_all, double* x_all, double tol, int maxit,
+                         int* iters, double* relres, md_stream s);
+/* Per-instance device timestamps (ns, globaltimer) of convergence for the
+ * last md_batch_solve, relative to its start; host array of n_ops. */
+md_status md_batch_times(const md_batch* b, double* seconds);
+
+/* md_solve_batched -- one-shot form: create, solve (per-instance device
+ * pointers given as host arrays), destroy. */
+md_status md_solve_batched(int n, const md_op* const* ops, const md_cnn* cnn, const double* const* b,
+                           double* const* x, double tol, int restart, int maxit, int* iters,
+                           double* relres, md_stream s);
+
+/* ---- training ----------------------------------------------------------------
+ * md_train -- unsupervised training of the network (Section 3.2 eq. (risk),
+ * (trained_preconditioner); the loss of Section 5.1):
+ *   per sample (instance op_k, residual r = [r0; r1]):
+ *     b0 = r0 + beta Pi^T W Psi B11^{-1} r1,  s = ||b0||,
+ *     L = || C z0 - b0 ||^2 / ||b0||^2,  z0 = (s / alpha) N([r0/s, l/s, d_h]),
+ *   mean over a minibatch, AdamW, cosine learning-rate decay from lr to lr_min.
+ * Samples of one minibatch share a grid size (the sampler groups them).
+ * cnn: in/out network (trained in place).  Synchronous. */
+typedef struct {
+    int n_ops;
+    const md_op* const* ops;       /* training instances (host array) */
+    int n_samples;
+    const int* sample_op;          /* host, n_samples: index into ops */
+    const float* const* sample_r;  /* host array of device pointers: residual of length n of its op */
+    int epochs;
+    int batch;
+    double lr, lr_min, beta1, beta2, weight_decay, eps;
+    uint64_t seed;                 /* shuffling */
+    double* loss_history;          /* host, epochs entries (mean loss per epoch), nullable */
+} md_train_cfg;
+md_status md_train(md_cnn* cnn, const md_train_cfg* cfg);
+
+/* md_train_loss -- the loss above and optionally its gradient for `count`
+ * samples (mean), without updating the network.  dparams: device float
+ * MD_CNN_NPARAMS or NULL.  *loss written on return (synchronises s). */
+md_status md_train_loss(const md_cnn* cnn, int count, const md_op* const* ops, const float* const* r,
+                        double* loss, float* dparams, md_stream s);
+
+const char* md_last_error(void);
+const char* md_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MD_H */

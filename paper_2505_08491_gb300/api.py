@@ -1,0 +1,209 @@
+"""Python binding of the md library: argument marshalling over the C ABI.
+
+Every computation runs in the library's CUDA kernels; this module only
+checks shapes/devices, passes pointers and streams, and raises on errors.
+Tensors are torch CUDA tensors (torch provides device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} entries, got {t.numel()}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Operator:
+    """One assembled instance: grid N, graph, radius, coupling beta (md_assemble)."""
+
+    def __init__(self, N: int, graph: dict, beta: float, *, k_omega=1.0, sigma_omega=0.0, k_lambda=1.0):
+        lib = L.load()
+        xyz = np.ascontiguousarray(graph["xyz"], dtype=np.float64)
+        edges = np.ascontiguousarray(graph["edges"], dtype=np.int32)
+        g = L.MdGraph(len(xyz), xyz.ctypes.data_as(C.POINTER(C.c_double)), len(edges),
+                      edges.ctypes.data_as(C.POINTER(C.c_int)), int(graph["elems"]))
+        prm = L.MdParams(k_omega, sigma_omega, k_lambda)
+        h = C.c_void_p()
+        torch.cuda.init()
+        L.check(lib.md_assemble(int(N), C.byref(g), float(graph["radius"]), float(beta), C.byref(prm), C.byref(h)),
+                "md_assemble")
+        self._h = h
+        info = L.MdOpInfo()
+        L.check(lib.md_op_get_info(h, C.byref(info)), "md_op_get_info")
+        self.N, self.n3, self.n1, self.nq, self.n_touch = info.N, info.n3, info.n1, info.nq, info.n_touch
+        self.n, self.alpha, self.beta = info.n, info.alpha, info.beta
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.load().md_op_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def distance(self) -> torch.Tensor:
+        d = torch.empty(self.n3, dtype=torch.float32, device="cuda")
+        L.check(L.load().md_op_distance(self._h, _ptr(d), _stream()), "md_op_distance")
+        return d
+
+    def rhs(self, f: torch.Tensor | None, g: float = 1.0) -> torch.Tensor:
+        b = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        L.check(L.load().md_rhs(self._h, _ptr(f, torch.float64, self.n3, "f"), float(g), _ptr(b), _stream()), "md_rhs")
+        return b
+
+    def apply(self, u: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if u.dtype not in (torch.float32, torch.float64):
+            raise ValueError("u must be float32 or float64")
+        y = torch.empty_like(u) if out is None else out
+        prec = L.MD_FP32 if u.dtype == torch.float32 else L.MD_FP64
+        L.check(L.load().md_apply(self._h, prec, _ptr(u, u.dtype, self.n, "u"), _ptr(y, u.dtype, self.n, "y"),
+                                  _stream()), "md_apply")
+        return y
+
+    def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None) -> torch.Tensor:
+        z = torch.empty_like(r) if out is None else out
+        L.check(L.load().md_precondition(self._h, net.handle if net is not None else None,
+                                         _ptr(r, torch.float32, self.n, "r"), _ptr(z, torch.float32, self.n, "z"),
+                                         _stream()), "md_precondition")
+        return z
+
+    def solve(self, b: torch.Tensor, x0: torch.Tensor | None = None, net: "Network | None" = None,
+              tol: float = 1e-8, restart: int = 30, maxit: int = 10000):
+        """FGMRES with the network preconditioner (net given) or Jacobi-CG.
+        Returns (x, iterations, true relative residual, converged)."""
+        x = torch.zeros(self.n, dtype=torch.float64, device="cuda") if x0 is None else x0.clone()
+        it = C.c_int()
+        rr = C.c_double()
+        s = L.check(L.load().md_solve(self._h, net.handle if net is not None else None,
+                                      _ptr(b, torch.float64, self.n, "b"), _ptr(x), float(tol), int(restart),
+                                      int(maxit), C.byref(it), C.byref(rr), _stream()),
+                    "md_solve", allow=(L.MD_OK, L.MD_NOT_CONVERGED))
+        return x, it.value, rr.value, s == L.MD_OK
+
+
+class Network:
+    """The 6-layer convolutional preconditioner (weights on the device)."""
+
+    def __init__(self, params: np.ndarray | None = None, *, handle=None):
+        lib = L.load()
+        if handle is not None:
+            self._h = handle
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        h = C.c_void_p()
+        L.check(lib.md_cnn_create(p.ctypes.data_as(C.POINTER(C.c_float)), p.size, C.byref(h)), "md_cnn_create")
+        self._h = h
+
+    @classmethod
+    def load(cls, path: str) -> "Network":
+        h = C.c_void_p()
+        L.check(L.load().md_cnn_load(path.encode(), C.byref(h)), "md_cnn_load")
+        return cls(handle=h)
+
+    def save(self, path: str):
+        L.check(L.load().md_cnn_save(self._h, path.encode()), "md_cnn_save")
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(L.MD_CNN_NPARAMS, dtype=np.float32)
+        L.check(L.load().md_cnn_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size),
+                "md_cnn_get_params")
+        return out
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.load().md_cnn_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        """X: (batch, 3, n, n, n) float32 CUDA -> (batch, 1, n, n, n)."""
+        if X.dim() != 5 or X.shape[1] != 3 or not (X.shape[2] == X.shape[3] == X.shape[4]):
+            raise ValueError("X must be (batch, 3, n, n, n)")
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], 1) + tuple(X.shape[2:]), dtype=torch.float32, device="cuda")
+        L.check(L.load().md_cnn_forward(self._h, X.shape[2], X.shape[0], _ptr(X, torch.float32), _ptr(Y), _stream()),
+                "md_cnn_forward")
+        return Y
+
+
+class Batch:
+    """Many instances solved together (md_batch_*)."""
+
+    SOLVERS = {"fgmres_cnn": L.MD_SOLVER_FGMRES_CNN, "fgmres_jacobi": L.MD_SOLVER_FGMRES_JACOBI,
+               "cg_jacobi": L.MD_SOLVER_CG_JACOBI}
+
+    def __init__(self, ops: list[Operator], solver: str = "fgmres_cnn", net: Network | None = None, restart: int = 30):
+        lib = L.load()
+        self.ops = list(ops)
+        arr = (C.c_void_p * len(ops))(*[o.handle.value for o in ops])
+        h = C.c_void_p()
+        L.check(lib.md_batch_create(len(ops), arr, net.handle if net is not None else None, self.SOLVERS[solver],
+                                    int(restart), C.byref(h)), "md_batch_create")
+        self._h = h
+        offs = (C.c_longlong * (len(ops) + 1))()
+        L.check(lib.md_batch_offsets(h, offs), "md_batch_offsets")
+        self.offsets = list(offs)
+        self.total = self.offsets[-1]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.load().md_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b_all: torch.Tensor, x_all: torch.Tensor, tol: float = 1e-8, maxit: int = 10000):
+        n = len(self.ops)
+        it = (C.c_int * n)()
+        rr = (C.c_double * n)()
+        s = L.check(L.load().md_batch_solve(self._h, _ptr(b_all, torch.float64, self.total, "b"),
+                                            _ptr(x_all, torch.float64, self.total, "x"), float(tol), int(maxit),
+                                            it, rr, _stream()),
+                    "md_batch_solve", allow=(L.MD_OK, L.MD_NOT_CONVERGED))
+        return list(it), list(rr), s == L.MD_OK
+
+    def times(self):
+        n = len(self.ops)
+        t = (C.c_double * n)()
+        L.check(L.load().md_batch_times(self._h, t), "md_batch_times")
+        return list(t)

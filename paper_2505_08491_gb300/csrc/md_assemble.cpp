@@ -1,0 +1,383 @@
+// md_assemble: geometry and sparse structure of one 3D-1D instance
+// (eq. (mainsys), Section 2.1), built on the host in FP64 and uploaded.
+//
+// Readings of points the paper leaves open, shared with the oracle by
+// specification only (no code is shared):
+//   - homogeneous Dirichlet rows/columns on the cube boundary;
+//   - beta multiplies the coupling form with unit line weight;
+//   - 1D diffusion kappa = k_lambda * pi R^2;
+//   - 2 Gauss points per 1D element; 8 circle points at theta_k = 2 pi k / 8
+//     with exact cosines/sines; frame n1 = unit(t x e_a) with e_a the axis of
+//     smallest |t_a| (lowest index on ties), n2 = t x n1;
+//   - circle point in cell clamp(floor(x N), 0, N-1), trilinear weights,
+//     boundary-node weights dropped.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "md_internal.h"
+
+namespace {
+
+struct Vec3 { double x, y, z; };
+inline Vec3 sub(Vec3 a, Vec3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline Vec3 add(Vec3 a, Vec3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline Vec3 scale(double s, Vec3 a) { return {s * a.x, s * a.y, s * a.z}; }
+inline double norm(Vec3 a) { return std::sqrt(a.x * a.x + a.y * a.y + a.z * a.z); }
+inline Vec3 cross(Vec3 a, Vec3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+struct Entry { int col; double val; };
+
+}  // namespace
+
+extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double beta,
+                                 const md_params* prm, md_op** out) {
+    if (!out) { md_set_error("md_assemble: out is NULL"); return MD_ERR_ARG; }
+    *out = nullptr;
+    if (N < 2 || N > 1024) { md_set_error("md_assemble: N=%d outside [2, 1024]", N); return MD_ERR_ARG; }
+    if (!g || !g->xyz || !g->edges || g->n_nodes < 2 || g->n_edges < 1 || g->elems_per_edge < 1) {
+        md_set_error("md_assemble: invalid graph"); return MD_ERR_ARG;
+    }
+    if (!(radius > 0.0) || !(beta >= 0.0)) { md_set_error("md_assemble: radius must be > 0 and beta >= 0"); return MD_ERR_ARG; }
+    const double k_omega = prm ? prm->k_omega : 1.0;
+    const double sigma_omega = prm ? prm->sigma_omega : 0.0;
+    const double k_lambda = prm ? prm->k_lambda : 1.0;
+    const int V = g->n_nodes, E = g->n_edges, m = g->elems_per_edge;
+    for (int e = 0; e < E; ++e) {
+        int a = g->edges[2 * e], b = g->edges[2 * e + 1];
+        if (a < 0 || a >= V || b < 0 || b >= V || a == b) { md_set_error("md_assemble: bad edge %d", e); return MD_ERR_ARG; }
+    }
+    for (int i = 0; i < 3 * V; ++i) {
+        double c = g->xyz[i];
+        if (!(c > 0.0 && c < 1.0)) { md_set_error("md_assemble: node coordinate %d outside (0,1)", i); return MD_ERR_ARG; }
+    }
+
+    const int M = N + 1;
+    const long long n3ll = (long long)M * M * M;
+    if (n3ll > (1LL << 30)) { md_set_error("md_assemble: grid too large"); return MD_ERR_ARG; }
+    const int n3 = (int)n3ll;
+    const double h = 1.0 / N;
+
+    // ---- 1D mesh: graph nodes first, then interior points of each edge
+    const int n1 = V + E * (m - 1);
+    std::vector<Vec3> X1(n1);
+    for (int i = 0; i < V; ++i) X1[i] = {g->xyz[3 * i], g->xyz[3 * i + 1], g->xyz[3 * i + 2]};
+    std::vector<int> elA, elB;
+    elA.reserve((size_t)E * m); elB.reserve((size_t)E * m);
+    for (int e = 0; e < E; ++e) {
+        int p = g->edges[2 * e], q = g->edges[2 * e + 1];
+        Vec3 pa = X1[p], pb = X1[q];
+        Vec3 d = sub(pb, pa);
+        std::vector<int> chain;
+        chain.push_back(p);
+        for (int i = 1; i < m; ++i) {
+            int id = V + e * (m - 1) + (i - 1);
+            X1[id] = add(pa, scale((double)i / (double)m, d));
+            chain.push_back(id);
+        }
+        chain.push_back(q);
+        for (int i = 0; i < m; ++i) { elA.push_back(chain[i]); elB.push_back(chain[i + 1]); }
+    }
+    const int ne = (int)elA.size();
+    const int nq = 2 * ne;
+
+    // ---- forest check and elimination order (children before parents)
+    std::vector<std::vector<int>> adj(n1);
+    for (int e = 0; e < ne; ++e) { adj[elA[e]].push_back(elB[e]); adj[elB[e]].push_back(elA[e]); }
+    std::vector<int> parent(n1, -2), bfs;
+    bfs.reserve(n1);
+    for (int r = 0; r < n1; ++r) {
+        if (parent[r] != -2) continue;
+        parent[r] = -1;
+        size_t head = bfs.size();
+        bfs.push_back(r);
+        while (head < bfs.size()) {
+            int u = bfs[head++];
+            for (int v : adj[u]) {
+                if (v == parent[u]) continue;
+                if (parent[v] != -2) { md_set_error("md_assemble: the graph has a cycle"); return MD_ERR_ARG; }
+                parent[v] = u;
+                bfs.push_back(v);
+            }
+        }
+    }
+    // a repeated edge between the same two nodes is a cycle too
+    {
+        std::vector<std::pair<int, int>> ed;
+        for (int e = 0; e < E; ++e) {
+            int a = g->edges[2 * e], b = g->edges[2 * e + 1];
+            ed.push_back({std::min(a, b), std::max(a, b)});
+        }
+        std::sort(ed.begin(), ed.end());
+        if (std::adjacent_find(ed.begin(), ed.end()) != ed.end()) { md_set_error("md_assemble: repeated edge"); return MD_ERR_ARG; }
+    }
+    std::vector<int> order(bfs.rbegin(), bfs.rend());
+
+    // ---- quadrature points, circle points, averaging rows
+    const double gxi[2] = {(1.0 - 1.0 / std::sqrt(3.0)) / 2.0, (1.0 + 1.0 / std::sqrt(3.0)) / 2.0};
+    const double S = std::sqrt(0.5);
+    const double ccos[8] = {1.0, S, 0.0, -S, -1.0, -S, 0.0, S};
+    const double csin[8] = {0.0, S, 1.0, S, 0.0, -S, -1.0, -S};
+    auto is_bd = [&](int i, int j, int k) { return i == 0 || i == N || j == 0 || j == N || k == 0 || k == N; };
+
+    std::vector<int> qa(nq), qb(nq);
+    std::vector<double> psa(nq), psb(nq), wq(nq), elen(ne);
+    std::vector<int> pi_ptr(nq + 1, 0);
+    std::vector<int> pi_col;
+    std::vector<double> pi_val;
+    std::vector<Entry> row;
+    for (int el = 0; el < ne; ++el) {
+        Vec3 a = X1[elA[el]], b = X1[elB[el]];
+        Vec3 d = sub(b, a);
+        double L = norm(d);
+        if (!(L > 0.0)) { md_set_error("md_assemble: zero-length element"); return MD_ERR_ARG; }
+        elen[el] = L;
+        Vec3 t = {d.x / L, d.y / L, d.z / L};
+        double at[3] = {std::fabs(t.x), std::fabs(t.y), std::fabs(t.z)};
+        int ax = 0;
+        if (at[1] < at[ax]) ax = 1;
+        if (at[2] < at[ax]) ax = 2;
+        Vec3 ea = {ax == 0 ? 1.0 : 0.0, ax == 1 ? 1.0 : 0.0, ax == 2 ? 1.0 : 0.0};
+        Vec3 v = cross(t, ea);
+        double nv = norm(v);
+        Vec3 n1v = {v.x / nv, v.y / nv, v.z / nv};
+        Vec3 n2v = cross(t, n1v);
+        for (int gp = 0; gp < 2; ++gp) {
+            int q = 2 * el + gp;
+            double xi = gxi[gp];
+            Vec3 c = add(a, scale(xi, d));
+            qa[q] = elA[el]; qb[q] = elB[el];
+            psa[q] = 1.0 - xi; psb[q] = xi;
+            wq[q] = L / 2.0;
+            row.clear();
+            for (int k = 0; k < 8; ++k) {
+                Vec3 tmp = add(scale(ccos[k], n1v), scale(csin[k], n2v));
+                Vec3 x = add(c, scale(radius, tmp));
+                if (!(x.x >= 0.0 && x.x <= 1.0 && x.y >= 0.0 && x.y <= 1.0 && x.z >= 0.0 && x.z <= 1.0)) {
+                    md_set_error("md_assemble: a cross-section circle leaves the cube (element %d)", el);
+                    return MD_ERR_ARG;
+                }
+                double xs[3] = {x.x * (double)N, x.y * (double)N, x.z * (double)N};
+                int cell[3];
+                double fr[3];
+                for (int dd = 0; dd < 3; ++dd) {
+                    int ci = (int)std::floor(xs[dd]);
+                    if (ci < 0) ci = 0;
+                    if (ci > N - 1) ci = N - 1;
+                    cell[dd] = ci;
+                    fr[dd] = xs[dd] - (double)ci;
+                }
+                for (int corner = 0; corner < 8; ++corner) {
+                    int ca = corner & 1, cb = (corner >> 1) & 1, cc = (corner >> 2) & 1;
+                    double wx = ca ? fr[0] : 1.0 - fr[0];
+                    double wy = cb ? fr[1] : 1.0 - fr[1];
+                    double wz = cc ? fr[2] : 1.0 - fr[2];
+                    int ii = cell[0] + ca, jj = cell[1] + cb, kk = cell[2] + cc;
+                    if (is_bd(ii, jj, kk)) continue;
+                    row.push_back({ii + M * (jj + M * kk), (wx * wy * wz) / 8.0});
+                }
+            }
+            std::sort(row.begin(), row.end(), [](const Entry& p, const Entry& r) { return p.col < r.col; });
+            for (size_t i = 0; i < row.size();) {
+                size_t j = i;
+                double s = 0.0;
+                while (j < row.size() && row[j].col == row[i].col) { s += row[j].val; ++j; }
+                pi_col.push_back(row[i].col);
+                pi_val.push_back(s);
+                i = j;
+            }
+            pi_ptr[q + 1] = (int)pi_col.size();
+        }
+    }
+
+    // ---- Pi^T W over touched nodes: entries (q, Pi[q,n] w_q), sorted by node then q
+    struct TE { int node, q; double v; };
+    std::vector<TE> te;
+    te.reserve(pi_col.size());
+    for (int q = 0; q < nq; ++q)
+        for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) te.push_back({pi_col[j], q, pi_val[j] * wq[q]});
+    std::sort(te.begin(), te.end(), [](const TE& p, const TE& r) { return p.node != r.node ? p.node < r.node : p.q < r.q; });
+    std::vector<int> tn_node, tn_ptr(1, 0), tn_q;
+    std::vector<double> tn_v, touch_m;  // touch_m: diag of Pi^T W Pi at the node
+    for (size_t i = 0; i < te.size();) {
+        size_t j = i;
+        double dm = 0.0;
+        while (j < te.size() && te[j].node == te[i].node) {
+            tn_q.push_back(te[j].q);
+            tn_v.push_back(te[j].v);
+            // Pi[q,n]^2 w_q = (Pi[q,n] w_q) * Pi[q,n]
+            dm += te[j].v * (te[j].v / wq[te[j].q]);
+            ++j;
+        }
+        tn_node.push_back(te[i].node);
+        tn_ptr.push_back((int)tn_q.size());
+        touch_m.push_back(dm);
+        i = j;
+    }
+    const int ntouch = (int)tn_node.size();
+
+    // ---- 1D operators
+    const double kappa = k_lambda * M_PI * radius * radius;
+    // kappa K1 rows and Psi^T W rows per 1D node
+    std::vector<std::map<int, double>> k1rows(n1);
+    std::vector<std::vector<std::pair<int, double>>> pwrows(n1);
+    std::vector<std::map<int, double>> brows(n1);  // B11
+    std::vector<double> load1(n1, 0.0);
+    for (int el = 0; el < ne; ++el) {
+        int a = elA[el], b = elB[el];
+        double L = elen[el];
+        double kk = kappa / L;
+        k1rows[a][a] += kk; k1rows[a][b] -= kk;
+        k1rows[b][b] += kk; k1rows[b][a] -= kk;
+        brows[a][a] += kk; brows[a][b] -= kk;
+        brows[b][b] += kk; brows[b][a] -= kk;
+        load1[a] += L / 2.0;
+        load1[b] += L / 2.0;
+        for (int gp = 0; gp < 2; ++gp) {
+            int q = 2 * el + gp;
+            pwrows[a].push_back({q, psa[q] * wq[q]});
+            pwrows[b].push_back({q, psb[q] * wq[q]});
+            brows[a][a] += beta * wq[q] * psa[q] * psa[q];
+            brows[a][b] += beta * wq[q] * psa[q] * psb[q];
+            brows[b][a] += beta * wq[q] * psb[q] * psa[q];
+            brows[b][b] += beta * wq[q] * psb[q] * psb[q];
+        }
+    }
+    std::vector<int> k1_ptr(1, 0), k1_col, pw_ptr(1, 0), pw_q;
+    std::vector<double> k1_v, pw_v, d1(n1);
+    for (int i = 0; i < n1; ++i) {
+        for (auto& kv : k1rows[i]) { k1_col.push_back(kv.first); k1_v.push_back(kv.second); }
+        k1_ptr.push_back((int)k1_col.size());
+        std::sort(pwrows[i].begin(), pwrows[i].end());
+        for (auto& kv : pwrows[i]) { pw_q.push_back(kv.first); pw_v.push_back(kv.second); }
+        pw_ptr.push_back((int)pw_q.size());
+        d1[i] = brows[i][i];
+    }
+    // tree LDL^T of B11
+    std::vector<double> dd(n1), tl(n1, 0.0), tdinv(n1);
+    for (int i = 0; i < n1; ++i) dd[i] = brows[i][i];
+    for (int idx = 0; idx < n1; ++idx) {
+        int i = order[idx];
+        if (!(dd[i] > 0.0)) { md_set_error("md_assemble: B11 is not positive definite (beta = 0?)"); return MD_ERR_ARG; }
+        int p = parent[i];
+        if (p >= 0) {
+            double bpi = brows[p][i];
+            tl[i] = bpi / dd[i];
+            dd[p] -= tl[i] * bpi;
+        }
+    }
+    for (int i = 0; i < n1; ++i) tdinv[i] = 1.0 / dd[i];
+    std::vector<int> tr_order = order, tr_parent(n1);
+    for (int i = 0; i < n1; ++i) tr_parent[i] = parent[i];
+
+    // ---- stencils and diagonal
+    // Q1 stencil by offset class |dx|+|dy|+|dz| (h-scaled): stiffness {8/3, 0, -1/6, -1/12} h,
+    // mass (h/6)^3 {64, 16, 4, 1}
+    const double Kst[4] = {8.0 / 3.0 * h, 0.0, -1.0 / 6.0 * h, -1.0 / 12.0 * h};
+    const double h3 = h * h * h;
+    const double Mst[4] = {64.0 * h3 / 216.0, 16.0 * h3 / 216.0, 4.0 * h3 / 216.0, 1.0 * h3 / 216.0};
+    md_op* op = new md_op();
+    InstDesc& D = op->h;
+    memset(&D, 0, sizeof(D));
+    D.N = N; D.n3 = n3; D.n1 = n1; D.nq = nq; D.ntouch = ntouch; D.nsegs = E;
+    D.n = (long long)n3 + n1;
+    D.h = h; D.beta = beta;
+    for (int c = 0; c < 4; ++c) {
+        D.st64[c] = k_omega * Kst[c] + sigma_omega * Mst[c];
+        D.st32[c] = (float)D.st64[c];
+        D.ms64[c] = Mst[c];
+    }
+    // alpha = ||diag(C_II)|| / sqrt(n_I)
+    {
+        long long nI = (long long)(N - 1) * (N - 1) * (N - 1);
+        double c0 = D.st64[0];
+        double ss = (double)nI * c0 * c0;
+        for (int i = 0; i < ntouch; ++i) {
+            double dc = c0 + beta * touch_m[i];
+            ss += dc * dc - c0 * c0;
+        }
+        D.alpha = nI > 0 ? std::sqrt(ss / (double)nI) : 1.0;
+    }
+
+    auto fail = [&](md_status s) { dev_free_all(&op->allocs); delete op; return s; };
+    std::vector<float> f32;
+    auto up64 = [&](const double** dst, const std::vector<double>& v) {
+        double* p; md_status s = dev_upload(&op->allocs, &p, v.data(), v.size()); *dst = p; return s; };
+    auto up32 = [&](const float** dst, const std::vector<double>& v) {
+        f32.assign(v.begin(), v.end());
+        float* p; md_status s = dev_upload(&op->allocs, &p, f32.data(), f32.size()); *dst = p; return s; };
+    auto upi = [&](const int** dst, const std::vector<int>& v) {
+        int* p; md_status s = dev_upload(&op->allocs, &p, v.data(), v.size()); *dst = p; return s; };
+#define UP(x) do { md_status s_ = (x); if (s_ != MD_OK) return fail(s_); } while (0)
+    UP(upi(&D.pi_ptr, pi_ptr)); UP(upi(&D.pi_col, pi_col)); UP(up64(&D.pi_v64, pi_val)); UP(up32(&D.pi_v32, pi_val));
+    UP(upi(&D.qa, qa)); UP(upi(&D.qb, qb));
+    UP(up64(&D.psa64, psa)); UP(up64(&D.psb64, psb)); UP(up32(&D.psa32, psa)); UP(up32(&D.psb32, psb));
+    UP(upi(&D.tn_node, tn_node)); UP(upi(&D.tn_ptr, tn_ptr)); UP(upi(&D.tn_q, tn_q));
+    UP(up64(&D.tn_v64, tn_v)); UP(up32(&D.tn_v32, tn_v));
+    UP(upi(&D.k1_ptr, k1_ptr)); UP(upi(&D.k1_col, k1_col)); UP(up64(&D.k1_v64, k1_v)); UP(up32(&D.k1_v32, k1_v));
+    UP(upi(&D.pw_ptr, pw_ptr)); UP(upi(&D.pw_q, pw_q)); UP(up64(&D.pw_v64, pw_v)); UP(up32(&D.pw_v32, pw_v));
+    UP(up64(&D.load1, load1));
+    {
+        std::vector<double> lo(n1), dio(n1);
+        for (int i = 0; i < n1; ++i) { lo[i] = tl[i]; dio[i] = tdinv[i]; }
+        UP(upi(&D.tr_order, tr_order)); UP(upi(&D.tr_parent, tr_parent));
+        UP(up64(&D.tr_l64, lo)); UP(up64(&D.tr_dinv64, dio)); UP(up32(&D.tr_l32, lo)); UP(up32(&D.tr_dinv32, dio));
+    }
+    {
+        std::vector<double> segs((size_t)E * 6);
+        for (int e = 0; e < E; ++e) {
+            int a = g->edges[2 * e], b = g->edges[2 * e + 1];
+            for (int c = 0; c < 3; ++c) { segs[6 * e + c] = g->xyz[3 * a + c]; segs[6 * e + 3 + c] = g->xyz[3 * b + c]; }
+        }
+        UP(up64(&D.segs, segs));
+    }
+    {
+        float* p; UP(dev_alloc(&op->allocs, &p, (size_t)n3, false)); D.dist = p;
+        double* dp; UP(dev_alloc(&op->allocs, &dp, (size_t)D.n, false)); D.dinv64 = dp;
+        UP(dev_alloc(&op->allocs, &p, (size_t)D.n, false)); D.dinv32 = p;
+        UP(dev_alloc(&op->allocs, &D.t64, (size_t)nq)); UP(dev_alloc(&op->allocs, &D.t32, (size_t)nq));
+        UP(dev_alloc(&op->allocs, &D.lift32, (size_t)n3)); UP(dev_alloc(&op->allocs, &D.ltouch32, (size_t)ntouch));
+    }
+    UP(dev_upload(&op->allocs, &op->d, &D, 1));
+    {
+        std::vector<const InstDesc*> one{&op->h};
+        UP(build_tables(one, &op->tabs, &op->allocs));
+        long long z = 0;
+        UP(dev_upload(&op->allocs, &op->off0, &z, 1));
+    }
+    UP(launch_dist(op, 0));
+    UP(launch_dinv_fill(op, touch_m, d1, 0));
+    {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(md_cuda_status(e, "md_assemble sync", __FILE__, __LINE__));
+    }
+#undef UP
+    op->n_touch_nodes = ntouch;
+    *out = op;
+    return MD_OK;
+}
+
+extern "C" void md_op_destroy(md_op* op) {
+    if (!op) return;
+    for (int i = 0; i < 3; ++i)
+        if (op->solver_cache[i]) md_batch_destroy(op->solver_cache[i]);
+    dev_free_all(&op->allocs);
+    delete op;
+}
+
+extern "C" md_status md_op_get_info(const md_op* op, md_op_info_t* info) {
+    if (!op || !info) { md_set_error("md_op_get_info: NULL argument"); return MD_ERR_ARG; }
+    info->N = op->h.N; info->n3 = op->h.n3; info->n1 = op->h.n1; info->nq = op->h.nq;
+    info->n_touch = op->h.ntouch; info->n = op->h.n; info->alpha = op->h.alpha; info->beta = op->h.beta;
+    return MD_OK;
+}
+
+extern "C" md_status md_op_distance(const md_op* op, float* d, md_stream s) {
+    if (!op || !d) { md_set_error("md_op_distance: NULL argument"); return MD_ERR_ARG; }
+    MD_CUDA(cudaMemcpyAsync(d, op->h.dist, sizeof(float) * op->h.n3, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+    return MD_OK;
+}

@@ -1,0 +1,383 @@
+// The preconditioner network: parameter storage, input packing and the
+// convolution layers on CUDA cores (the reference path of the network and
+// the one training uses for its backward pass).
+//
+// Layer l computes Y = b + sum_q W(q) X(p + q) over q in {-1,0,1}^3 with zero
+// 'same' padding (the convolution of Section 4.2 in cross-correlation
+// orientation), then GELU(x) = x Phi(x) for l < 5.  Weights and hidden
+// activations are BF16, accumulation FP32.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "md_cnn.h"
+#include "md_common.cuh"
+
+namespace {
+const int kCin[MD_CNN_LAYERS] = {3, 32, 32, 32, 32, 32};
+const int kCout[MD_CNN_LAYERS] = {32, 32, 32, 32, 32, 1};
+const int kCinPad[MD_CNN_LAYERS] = {8, 32, 32, 32, 32, 32};
+
+size_t host_w_off(int l) {
+    size_t o = 0;
+    for (int i = 0; i < l; ++i) o += (size_t)kCout[i] * kCin[i] * 27 + kCout[i];
+    return o;
+}
+
+uint64_t fnv1a(const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    uint64_t h = 1469598103934665603ULL;
+    for (size_t i = 0; i < n; ++i) { h ^= c[i]; h *= 1099511628211ULL; }
+    return h;
+}
+}  // namespace
+
+// ---- parameters --------------------------------------------------------------
+static md_status cnn_upload(md_cnn* c) {
+    // packed weights per layer: [tap][cin_pad][cout] BF16 (RN), biases FP32
+    std::vector<__nv_bfloat16> w;
+    std::vector<float> b;
+    for (int l = 0; l < MD_CNN_LAYERS; ++l) {
+        c->w_off[l] = w.size();
+        c->b_off[l] = b.size();
+        const float* W = c->host.data() + host_w_off(l);
+        const float* B = W + (size_t)kCout[l] * kCin[l] * 27;
+        for (int tap = 0; tap < 27; ++tap)
+            for (int ci = 0; ci < kCinPad[l]; ++ci)
+                for (int co = 0; co < kCout[l]; ++co) {
+                    float v = ci < kCin[l] ? W[((size_t)co * kCin[l] + ci) * 27 + tap] : 0.0f;
+                    w.push_back(__float2bfloat16_rn(v));
+                }
+        for (int co = 0; co < kCout[l]; ++co) b.push_back(B[co]);
+    }
+    c->w_off[MD_CNN_LAYERS] = w.size();
+    c->b_off[MD_CNN_LAYERS] = b.size();
+    std::vector<void*> tmp;
+    if (c->w) { cudaFree(c->w); c->w = nullptr; }
+    if (c->b) { cudaFree(c->b); c->b = nullptr; }
+    MD_TRY(dev_upload(&tmp, &c->w, w.data(), w.size()));
+    MD_TRY(dev_upload(&tmp, &c->b, b.data(), b.size()));
+    return MD_OK;
+}
+
+extern "C" md_status md_cnn_create(const float* host_params, long long n_params, md_cnn** out) {
+    if (!out || !host_params) { md_set_error("md_cnn_create: NULL argument"); return MD_ERR_ARG; }
+    *out = nullptr;
+    if (n_params != MD_CNN_NPARAMS) { md_set_error("md_cnn_create: %lld parameters, expected %d", n_params, MD_CNN_NPARAMS); return MD_ERR_ARG; }
+    for (long long i = 0; i < n_params; ++i)
+        if (!std::isfinite(host_params[i])) { md_set_error("md_cnn_create: parameter %lld is not finite", i); return MD_ERR_NAN; }
+    md_cnn* c = new md_cnn();
+    c->host.assign(host_params, host_params + n_params);
+    md_status st = cnn_upload(c);
+    if (st != MD_OK) { md_cnn_destroy(c); return st; }
+    *out = c;
+    return MD_OK;
+}
+
+md_status cnn_set_params(md_cnn* c, const float* host_params) {
+    c->host.assign(host_params, host_params + MD_CNN_NPARAMS);
+    return cnn_upload(c);
+}
+
+extern "C" md_status md_cnn_get_params(const md_cnn* c, float* host_params, long long n_params) {
+    if (!c || !host_params || n_params != MD_CNN_NPARAMS) { md_set_error("md_cnn_get_params: bad argument"); return MD_ERR_ARG; }
+    memcpy(host_params, c->host.data(), sizeof(float) * MD_CNN_NPARAMS);
+    return MD_OK;
+}
+
+extern "C" void md_cnn_destroy(md_cnn* c) {
+    if (!c) return;
+    if (c->w) cudaFree(c->w);
+    if (c->b) cudaFree(c->b);
+    if (c->wmma) cudaFree(c->wmma);
+    delete c;
+}
+
+extern "C" md_status md_cnn_save(const md_cnn* c, const char* path) {
+    if (!c || !path) { md_set_error("md_cnn_save: NULL argument"); return MD_ERR_ARG; }
+    FILE* f = fopen(path, "wb");
+    if (!f) { md_set_error("md_cnn_save: cannot open %s", path); return MD_ERR_IO; }
+    const char magic[8] = {'M', 'D', 'C', 'N', 'N', '0', '0', '1'};
+    int64_t n = MD_CNN_NPARAMS;
+    uint64_t h = fnv1a(c->host.data(), sizeof(float) * n);
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(&n, 8, 1, f) == 1 &&
+              fwrite(c->host.data(), sizeof(float), n, f) == (size_t)n && fwrite(&h, 8, 1, f) == 1;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) { md_set_error("md_cnn_save: write failed for %s", path); return MD_ERR_IO; }
+    return MD_OK;
+}
+
+extern "C" md_status md_cnn_load(const char* path, md_cnn** out) {
+    if (!path || !out) { md_set_error("md_cnn_load: NULL argument"); return MD_ERR_ARG; }
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) { md_set_error("md_cnn_load: cannot open %s", path); return MD_ERR_IO; }
+    char magic[8];
+    int64_t n = 0;
+    uint64_t h = 0;
+    std::vector<float> v;
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "MDCNN001", 8) == 0 && fread(&n, 8, 1, f) == 1 &&
+              n == MD_CNN_NPARAMS;
+    if (ok) {
+        v.resize(n);
+        ok = fread(v.data(), sizeof(float), n, f) == (size_t)n && fread(&h, 8, 1, f) == 1;
+    }
+    fclose(f);
+    if (!ok) { md_set_error("md_cnn_load: %s is not a network file of %d parameters", path, MD_CNN_NPARAMS); return MD_ERR_IO; }
+    if (fnv1a(v.data(), sizeof(float) * n) != h) { md_set_error("md_cnn_load: checksum mismatch in %s", path); return MD_ERR_IO; }
+    return md_cnn_create(v.data(), n, out);
+}
+
+// ---- workspace -----------------------------------------------------------------
+template <int CIN8, int COUT, bool LAST>
+__global__ void k_conv_simt(const __nv_bfloat16* __restrict__, const long long* __restrict__, __nv_bfloat16* __restrict__,
+                            const long long* __restrict__, const __nv_bfloat16* __restrict__, const float* __restrict__,
+                            const Seg* __restrict__, const int* __restrict__, OutIO, int);
+
+// Kernel attributes are set once, outside any stream capture.
+static md_status cnn_prepare() {
+    static bool done = false;
+    if (done) return MD_OK;
+    MD_CUDA(cudaFuncSetAttribute(k_conv_simt<1, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 8 * 32 * 2));
+    MD_CUDA(cudaFuncSetAttribute(k_conv_simt<4, 32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 32 * 32 * 2));
+    MD_CUDA(cudaFuncSetAttribute(k_conv_simt<4, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 27 * 32 * 1 * 2));
+    done = true;
+    return MD_OK;
+}
+
+md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
+    MD_TRY(cnn_prepare());
+    CnnWork* w = new CnnWork();
+    w->ninst = (int)Ns.size();
+    w->hN = Ns;
+    long long rx = 0, rab = 0, nodes = 0;
+    std::vector<Seg> segs;
+    std::vector<InstRange> ranges;
+    const int CH = 512;
+    for (int i = 0; i < w->ninst; ++i) {
+        long long Pd = Ns[i] + 3, P = Pd * Pd * Pd;
+        w->h_off_x0.push_back(rx * 8);
+        w->h_off_ab.push_back(rab * 8);
+        rx += P;
+        rab += 4 * P;
+        int n3 = (Ns[i] + 1) * (Ns[i] + 1) * (Ns[i] + 1);
+        nodes += n3;
+        ranges.push_back({(int)segs.size(), 0});
+        for (int b = 0; b < n3; b += CH) segs.push_back({i, 0, b, std::min(n3, b + CH)});
+        ranges.back().count = (int)segs.size() - ranges.back().first;
+    }
+    w->total_nodes = nodes;
+    md_status st = MD_OK;
+    auto chk = [&](md_status s) { if (st == MD_OK) st = s; };
+    chk(dev_upload(&w->allocs, &w->N, Ns.data(), Ns.size()));
+    chk(dev_upload(&w->allocs, &w->off_x0, w->h_off_x0.data(), w->h_off_x0.size()));
+    chk(dev_upload(&w->allocs, &w->off_ab, w->h_off_ab.data(), w->h_off_ab.size()));
+    chk(dev_alloc(&w->allocs, &w->x0, (size_t)rx * 8));
+    chk(dev_alloc(&w->allocs, &w->a, (size_t)rab * 8));
+    chk(dev_alloc(&w->allocs, &w->b, (size_t)rab * 8));
+    w->nodes.nblocks = (int)segs.size();
+    w->nodes.hrange = ranges;
+    chk(dev_upload(&w->allocs, &w->nodes.seg, segs.data(), segs.size()));
+    chk(dev_upload(&w->allocs, &w->nodes.range, ranges.data(), ranges.size()));
+    if (st != MD_OK) { cnn_work_destroy(w); return st; }
+    *out = w;
+    return MD_OK;
+}
+
+void cnn_work_destroy(CnnWork* w) {
+    if (!w) return;
+    dev_free_all(&w->allocs);
+    delete w;
+}
+
+// ---- kernels ---------------------------------------------------------------------
+__device__ inline float gelu_exact(float x) { return x * normcdff(x); }
+
+__device__ inline void unpack8(const uint4& r, float (&x)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float2 f = __bfloat1622float2(h[k]);
+        x[2 * k] = f.x;
+        x[2 * k + 1] = f.y;
+    }
+}
+
+__device__ inline uint4 pack8(const float* v) {
+    uint4 r;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    return r;
+}
+
+// One thread per grid node, all output channels in registers.
+template <int CIN8, int COUT, bool LAST>
+__global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restrict__ in, const long long* __restrict__ in_off,
+                                                   __nv_bfloat16* __restrict__ outb, const long long* __restrict__ out_off,
+                                                   const __nv_bfloat16* __restrict__ W, const float* __restrict__ Bias,
+                                                   const Seg* __restrict__ seg, const int* __restrict__ Ns, OutIO io, int mode) {
+    constexpr int CIN = CIN8 * 8;
+    constexpr int NW = 27 * CIN * COUT;
+    if (io.st && !io.st[seg[blockIdx.x].inst].active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) sw[i] = W[i];
+    __syncthreads();
+    const Seg sg = seg[blockIdx.x];
+    const int N = Ns[sg.inst], M = N + 1;
+    const long long Pd = N + 3, P = Pd * Pd * Pd;
+    const __nv_bfloat16* xi = in + in_off[sg.inst];
+    for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
+        const int i = n % M, r = n / M, j = r % M, k = r / M;
+        const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
+        float acc[COUT];
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = Bias[co];
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+            const long long q = p + dx + Pd * (dy + Pd * dz);
+#pragma unroll
+            for (int c = 0; c < CIN8; ++c) {
+                const uint4 raw = *reinterpret_cast<const uint4*>(xi + (c * P + q) * 8);
+                float x[8];
+                unpack8(raw, x);
+#pragma unroll
+                for (int ci = 0; ci < 8; ++ci) {
+                    const __nv_bfloat16* wr = sw + ((size_t)tap * CIN + c * 8 + ci) * COUT;
+                    if (COUT % 8 == 0) {
+#pragma unroll
+                        for (int co = 0; co < COUT; co += 8) {
+                            float wv[8];
+                            unpack8(*reinterpret_cast<const uint4*>(wr + co), wv);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) acc[co + e] = fmaf(wv[e], x[ci], acc[co + e]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(__bfloat162float(wr[co]), x[ci], acc[co]);
+                    }
+                }
+            }
+        }
+        if (!LAST) {
+            __nv_bfloat16* o = outb + out_off[sg.inst];
+#pragma unroll
+            for (int c = 0; c < COUT / 8; ++c) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = gelu_exact(acc[c * 8 + e]);
+                *reinterpret_cast<uint4*>(o + (c * P + p) * 8) = pack8(v);
+            }
+        } else {
+            float* o = io.out + io.off[sg.inst];
+            if (mode == CONV_PREC) {
+                const bool bd = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
+                const double s = io.st[sg.inst].s;
+                const float scale = (float)(s / io.D[sg.inst].alpha);
+                o[n] = bd ? io.vin[io.vin_off[sg.inst] + n] : scale * acc[0];
+            } else {
+                o[n] = acc[0];
+            }
+        }
+    }
+}
+
+template <int CIN8, int COUT, bool LAST>
+static md_status launch_conv(const __nv_bfloat16* in, const long long* in_off, __nv_bfloat16* outb,
+                             const long long* out_off, const __nv_bfloat16* W, const float* B, const CnnWork* w,
+                             const OutIO& io, int mode, cudaStream_t s) {
+    const size_t smem = (size_t)27 * CIN8 * 8 * COUT * sizeof(__nv_bfloat16);
+    auto kern = k_conv_simt<CIN8, COUT, LAST>;
+    kern<<<w->nodes.nblocks, 128, smem, s>>>(in, in_off, outb, out_off, W, B, w->nodes.seg, w->N, io, mode);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s) {
+    const __nv_bfloat16* W = c->w;
+    const float* B = c->b;
+    MD_TRY((launch_conv<1, 32, false>(w->x0, w->off_x0, w->a, w->off_ab, W + c->w_off[0], B + c->b_off[0], w, io, 0, s)));
+    __nv_bfloat16* src = w->a;
+    __nv_bfloat16* dst = w->b;
+    for (int l = 1; l <= 4; ++l) {
+        MD_TRY((launch_conv<4, 32, false>(src, w->off_ab, dst, w->off_ab, W + c->w_off[l], B + c->b_off[l], w, io, 0, s)));
+        std::swap(src, dst);
+    }
+    MD_TRY((launch_conv<4, 1, true>(src, w->off_ab, nullptr, nullptr, W + c->w_off[5], B + c->b_off[5], w, io, (int)last, s)));
+    return MD_OK;
+}
+
+// ---- input packing -------------------------------------------------------------------
+__global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__ Ns, const InstDesc* __restrict__ D,
+                            const float* __restrict__ v, const long long* __restrict__ voff, const KState* __restrict__ st,
+                            __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off) {
+    const Seg sg = seg[blockIdx.x];
+    if (!st[sg.inst].active) return;
+    const InstDesc& d = D[sg.inst];
+    const int N = Ns[sg.inst], M = N + 1;
+    const long long Pd = N + 3;
+    const double s = st[sg.inst].s;
+    const float sf = (float)s;
+    const float* vi = v + voff[sg.inst];
+    __nv_bfloat16* xo = x0 + x0off[sg.inst];
+    for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
+        const int i = n % M, r = n / M, j = r % M, k = r / M;
+        const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
+        float c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (s > 0.0) {
+            c[0] = vi[n] / sf;
+            c[1] = d.lift32[n] / sf;
+        }
+        c[2] = d.dist[n];
+        *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
+    }
+}
+
+md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
+                        cudaStream_t s) {
+    k_pack_prec<<<w->nodes.nblocks, 128, 0, s>>>(w->nodes.seg, w->N, D, v, voff, st, w->x0, w->off_x0);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+__global__ void k_pack_raw(const Seg* __restrict__ seg, const int* __restrict__ Ns, const float* __restrict__ X,
+                           __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off) {
+    const Seg sg = seg[blockIdx.x];
+    const int N = Ns[sg.inst], M = N + 1;
+    const long long Pd = N + 3, n3 = (long long)M * M * M;
+    const float* xi = X + (long long)sg.inst * 3 * n3;
+    __nv_bfloat16* xo = x0 + x0off[sg.inst];
+    for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
+        const int i = n % M, r = n / M, j = r % M, k = r / M;
+        const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
+        float c[8] = {xi[n], xi[n3 + n], xi[2 * n3 + n], 0, 0, 0, 0, 0};
+        *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
+    }
+}
+
+md_status cnn_pack_raw(CnnWork* w, const float* X, cudaStream_t s) {
+    k_pack_raw<<<w->nodes.nblocks, 128, 0, s>>>(w->nodes.seg, w->N, X, w->x0, w->off_x0);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+// ---- raw forward API -----------------------------------------------------------------
+extern "C" md_status md_cnn_forward(const md_cnn* c, int n_nodes_edge, int batch, const float* X, float* Y, md_stream s) {
+    if (!c || !X || !Y || n_nodes_edge < 2 || batch < 1) { md_set_error("md_cnn_forward: bad argument"); return MD_ERR_ARG; }
+    std::vector<int> Ns(batch, n_nodes_edge - 1);
+    CnnWork* w = nullptr;
+    MD_TRY(cnn_work_create(Ns, &w));
+    std::vector<long long> off(batch);
+    const long long n3 = (long long)n_nodes_edge * n_nodes_edge * n_nodes_edge;
+    for (int i = 0; i < batch; ++i) off[i] = i * n3;
+    long long* doff = nullptr;
+    md_status st = dev_upload(&w->allocs, &doff, off.data(), off.size());
+    OutIO io{Y, doff, nullptr, nullptr, nullptr, nullptr};
+    if (st == MD_OK) st = cnn_pack_raw(w, X, (cudaStream_t)s);
+    if (st == MD_OK) st = cnn_forward_layers(c, w, io, CONV_RAW, (cudaStream_t)s);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)s);
+    cnn_work_destroy(w);
+    if (st == MD_OK && e != cudaSuccess) st = md_cuda_status(e, "md_cnn_forward", __FILE__, __LINE__);
+    return st;
+}

@@ -1,0 +1,48 @@
+// Network workspace and convolution launches (internal).
+#pragma once
+#include "md_internal.h"
+
+// Activation layout: per instance a zero-haloed padded grid of P = Pd^3 rows,
+// Pd = N + 3, row p = (i+1) + Pd((j+1) + Pd(k+1)) for grid node (i,j,k);
+// channels in chunks of 8: element (chunk c, row p, lane l) at
+// (c * P + p) * 8 + l.  Halo rows are never written and stay zero, which is
+// the zero 'same' padding of every layer.
+struct CnnWork {
+    int ninst = 0;
+    std::vector<void*> allocs;
+    std::vector<int> hN;
+    int* N = nullptr;              // device, per instance
+    __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
+    __nv_bfloat16* a = nullptr;    // 4 chunks
+    __nv_bfloat16* b = nullptr;    // 4 chunks
+    long long* off_x0 = nullptr;   // per instance, element offset into x0
+    long long* off_ab = nullptr;   // per instance, element offset into a / b
+    std::vector<long long> h_off_x0, h_off_ab;
+    Table nodes;                   // grid-node ranges per instance
+    long long total_nodes = 0;
+};
+
+md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out);
+void cnn_work_destroy(CnnWork* w);
+
+// Output handling of the last layer.
+enum ConvOut {
+    CONV_PREC = 1,     // z0 = (s / alpha) y on interior nodes, v0 on Dirichlet nodes
+    CONV_RAW = 2       // y (FP32) at the grid node
+};
+
+struct OutIO {
+    float* out;                // instance i's 3D part starts at out + off[i]
+    const long long* off;
+    const float* vin;          // CONV_PREC: preconditioner input (Dirichlet copy), + vin_off[i]
+    const long long* vin_off;
+    const KState* st;          // CONV_PREC: st[i].s
+    const InstDesc* D;         // CONV_PREC: D[i].alpha
+};
+
+md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s);
+// X0 = [v0 / s, l / s, d] from a preconditioner input (instance 3D part at v + voff[i])
+md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
+                        cudaStream_t s);
+// X0 from a raw channel-major FP32 input (sample, channel, z, y, x)
+md_status cnn_pack_raw(CnnWork* w, const float* X, cudaStream_t s);

@@ -1,0 +1,175 @@
+// Internal declarations of the md library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+
+#define MD_KMAX 64              // largest FGMRES restart length
+#define MD_MAXR (MD_KMAX + 4)   // reduction values per block
+#define MD_TB 256               // threads per block of the streaming kernels
+
+// ---------------------------------------------------------------------------
+// error handling
+void md_set_error(const char* fmt, ...);
+md_status md_cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define MD_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) return md_cuda_status(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+#define MD_TRY(call)                      \
+    do {                                  \
+        md_status s_ = (call);            \
+        if (s_ != MD_OK) return s_;       \
+    } while (0)
+#define MD_CHECK_LAUNCH() MD_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------
+// One assembled instance, as the kernels see it.  All pointers are device
+// pointers owned by the md_op.
+struct InstDesc {
+    int N, n3, n1, nq, ntouch, nsegs;
+    long long n;
+    double h, beta, alpha;
+    double st64[4];   // K00 (+ sigma mass) stencil by offset class: centre, face, edge, corner
+    float st32[4];
+    double ms64[4];   // Q1 mass stencil (load vector)
+    // Pi, row per quadrature point: columns = grid nodes, values = averaging weights
+    const int* pi_ptr; const int* pi_col; const double* pi_v64; const float* pi_v32;
+    // per quadrature point: 1D element end nodes and P1 values there
+    const int* qa; const int* qb;
+    const double* psa64; const double* psb64; const float* psa32; const float* psb32;
+    // Pi^T W, row per touched grid node: entries (q, Pi[q,n] w_q)
+    const int* tn_node; const int* tn_ptr; const int* tn_q; const double* tn_v64; const float* tn_v32;
+    // 1D rows: kappa K1 (CSR) and Psi^T W (entries (q, psi w_q))
+    const int* k1_ptr; const int* k1_col; const double* k1_v64; const float* k1_v32;
+    const int* pw_ptr; const int* pw_q; const double* pw_v64; const float* pw_v32;
+    const double* load1;
+    // tree LDL^T of B11 in elimination order (children before parents)
+    const int* tr_order; const int* tr_parent;
+    const double* tr_l64; const double* tr_dinv64; const float* tr_l32; const float* tr_dinv32;
+    // per grid / per dof
+    const float* dist;      // n3
+    const double* dinv64;   // n, 1 / diag(A)
+    const float* dinv32;
+    const double* segs;     // nsegs * 6 segment end points (distance field)
+    // scratch owned by the op
+    double* t64; float* t32;  // nq
+    float* lift32;            // n3, zero except touched nodes
+    float* ltouch32;          // ntouch
+};
+
+// A block of a batched launch: instance, work kind, [begin, end) range.
+struct Seg { int inst, kind, begin, end; };
+// Blocks of one instance inside a table.
+struct InstRange { int first, count; };
+
+struct Table {
+    Seg* seg = nullptr;         // device
+    InstRange* range = nullptr; // device, per instance
+    int nblocks = 0;
+    std::vector<InstRange> hrange;
+};
+
+// Tables for the launches of a set of instances.
+struct Tables {
+    Table apply_a;   // kind 0: stencil over n3 ; kind 1: gather over nq
+    Table apply_b;   // kind 2: Pi^T scatter over touched ; kind 3: 1D rows over n1
+    Table vec;       // kind 0: ranges over n (whole instance vector)
+    Table n3;        // kind 0: ranges over n3
+    Table touch;     // kind 0: ranges over ntouch
+};
+
+// ---------------------------------------------------------------------------
+// handles
+struct md_op {
+    InstDesc h;                  // host copy of the descriptor (device pointers)
+    InstDesc* d = nullptr;       // device copy
+    std::vector<void*> allocs;   // device allocations to free
+    int n_touch_nodes = 0;
+    Tables tabs;                 // launch tables of this instance alone
+    long long* off0 = nullptr;   // device {0}
+    md_batch* solver_cache[3] = {nullptr, nullptr, nullptr};
+    int solver_cache_restart[3] = {0, 0, 0};
+    const md_cnn* solver_cache_cnn = nullptr;
+};
+
+struct CnnLayer { int cin, cout, cin_pad; };
+
+struct md_cnn {
+    std::vector<float> host;     // FP32 master copy (MD_CNN_NPARAMS)
+    __nv_bfloat16* w = nullptr;  // device packed weights, per layer [tap][cout][cin_pad]
+    float* b = nullptr;          // device biases, per layer [cout]
+    size_t w_off[MD_CNN_LAYERS + 1];
+    size_t b_off[MD_CNN_LAYERS + 1];
+    // tcgen05 operand images of the weights (see md_conv)
+    __nv_bfloat16* wmma = nullptr;
+    size_t wmma_off[MD_CNN_LAYERS + 1];
+};
+
+// Per-instance Krylov state (device).
+struct KState {
+    double H[(MD_KMAX + 1) * MD_KMAX];   // Hessenberg, column j at H[j * (KMAX+1)]
+    double cs[MD_KMAX], sn[MD_KMAX];
+    double g[MD_KMAX + 1];
+    double y[MD_KMAX];
+    double sig[MD_KMAX + 1];             // 1 / ||V_j||: v_j = sig_j V_j
+    double coef[MD_KMAX + 1];            // update coefficients of the running pass
+    double wn2_before;                   // ||W||^2 before orthogonalisation
+    double bnorm, beta, relres, est;
+    double s2_touch, s, v3n2;            // preconditioner input norm pieces
+    double tol, inner_tol;
+    double rho, alpha_cg, pq;            // CG scalars
+    unsigned long long t_start, t_done;  // globaltimer stamps
+    int j, m, active, converged, iters, reorth, nan_seen, fallback, maxit, cycle_iters;
+    unsigned int counter[8];             // last-block counters per reduction kernel
+};
+
+// Problem-size independent kernel launches (md_apply.cu)
+struct KState;
+// gate: 0 all instances, 1 active ones (inside a cycle), 2 unfinished ones
+md_status launch_apply(const Tables& T, const InstDesc* d, int ninst, md_prec prec, const void* u,
+                       const long long* off, void* y, cudaStream_t s, const KState* st = nullptr, int gate = 0);
+md_status launch_rhs(const md_op* op, const double* f, double g, double* b, cudaStream_t s);
+md_status launch_dist(md_op* op, cudaStream_t s);
+md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_diag, const std::vector<double>& d1,
+                           cudaStream_t s);
+
+// Tables (md_tables.cpp)
+md_status build_tables(const std::vector<const InstDesc*>& insts, Tables* T, std::vector<void*>* allocs);
+void free_tables(Tables* T);
+
+// device memory helpers
+template <class T>
+md_status dev_upload(std::vector<void*>* allocs, T** dst, const T* src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) { md_set_error("cudaMalloc(%zu) failed: %s", count * sizeof(T), cudaGetErrorString(e)); return MD_ERR_OOM; }
+    allocs->push_back(p);
+    if (src) {
+        e = cudaMemcpy(p, src, count * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return md_cuda_status(e, "cudaMemcpy", __FILE__, __LINE__);
+    }
+    *dst = (T*)p;
+    return MD_OK;
+}
+template <class T>
+md_status dev_alloc(std::vector<void*>* allocs, T** dst, size_t count, bool zero = true) {
+    MD_TRY(dev_upload<T>(allocs, dst, nullptr, count));
+    if (zero) MD_CUDA(cudaMemset(*dst, 0, (count ? count : 1) * sizeof(T)));
+    return MD_OK;
+}
+void dev_free_all(std::vector<void*>* allocs);
+
+// preconditioner / network (md_prec.cu, md_cnn.cu)
+struct CnnWork;
+md_status cnn_work_create(const std::vector<const InstDesc*>& insts, CnnWork** out);
+void cnn_work_destroy(CnnWork* w);

@@ -1,0 +1,844 @@
+// Batched Krylov solvers: flexible GMRES(k) with the block preconditioner
+// (Section 4, eq. (twosteps)) and Jacobi-CG, for one or many instances.
+//
+// FGMRES, right preconditioned, per instance:
+//   cycle: r = b - A x (FP64), beta = ||r||, V_0 = r (FP32), v_0 = V_0/||V_0||
+//     for j: Z_j = P(V_j); W = A Z_j;                       (FP32)
+//            h_ij = (w, v_i) by classical Gram-Schmidt on the stored,
+//            unnormalised V_i (v_i = sig_i V_i, P positively homogeneous so
+//            z_j = sig_j Z_j), a second pass when ||w|| drops below half;
+//            Givens rotations on the FP64 Hessenberg, estimate |g_{j+1}|;
+//     x += sum_j y_j sig_j Z_j with H y = g (FP64 x, FP32 correction).
+// Every kernel runs across all instances; an instance leaves the cycle when
+// its estimate reaches max(tol ||b||, 1e-5 beta) (FP32 vectors cannot carry
+// the residual further within one cycle), and the restart's FP64 residual
+// decides convergence.  One restart cycle is captured as a CUDA graph.
+//
+// Jacobi-CG: FP64 conjugate gradients with M = diag(A)^{-1}; stops on the
+// recursive residual, then reports the true one.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "md_cnn.h"
+#include "md_common.cuh"
+
+#define INNER_REL 1e-5
+
+struct md_batch {
+    int ninst = 0;
+    md_solver solver = MD_SOLVER_FGMRES_JACOBI;
+    int k = 30;
+    const md_cnn* cnn = nullptr;
+    std::vector<const md_op*> ops;
+    std::vector<InstDesc> hdesc;
+    InstDesc* d = nullptr;
+    std::vector<void*> allocs;
+    Tables tabs;
+    std::vector<long long> hoff;
+    long long* off = nullptr;
+    long long total = 0;
+    double *x = nullptr, *b = nullptr, *y64 = nullptr, *r64 = nullptr, *p64 = nullptr;
+    float *V = nullptr, *Z = nullptr;
+    KState* st = nullptr;
+    double* part = nullptr;
+    int* ndone = nullptr;
+    int* res_iters = nullptr;
+    double* res_relres = nullptr;
+    double* res_time = nullptr;
+    int max_n1 = 0;
+    CnnWork* cw = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    const md_cnn* graph_cnn = nullptr;
+    std::vector<double> last_times;
+};
+
+// ---------------------------------------------------------------------------
+// reduction helper: each block writes R partials; the last block of the
+// instance sums them in block order (deterministic) into out[0..R)
+template <int MAXV>
+__device__ inline void reduce_values(double* vals, int count, double* part, int blk, const InstRange& rg,
+                                     unsigned int* counter, double* out, double* sh) {
+    // vals: per-thread values [count] in registers/local; reduce in block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = 0; r < count; ++r) {
+        double x = warp_sum(vals[r]);
+        if (lane == 0) sh[r * 32 + warp] = x;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < count; r += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[r * 32 + w];
+        part[(size_t)blk * MD_MAXR + r] = s;
+    }
+    __syncthreads();
+    bool last = last_block_arrive(counter, rg.count);
+    out[0] = last ? 1.0 : 0.0;
+    if (!last) return;
+    for (int r = threadIdx.x; r < count; r += blockDim.x) {
+        double s = 0.0;
+        for (int b2 = rg.first; b2 < rg.first + rg.count; ++b2) s += part[(size_t)b2 * MD_MAXR + r];
+        sh[r] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_init_state(KState* st, int ninst, double tol, int maxit, int* ndone) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *ndone = 0;
+    if (i >= ninst) return;
+    KState& S = st[i];
+    S.tol = tol; S.maxit = maxit; S.iters = 0; S.converged = 0; S.active = 0; S.j = 0; S.m = 0;
+    S.reorth = 0; S.nan_seen = 0; S.fallback = 0; S.bnorm = 0; S.relres = 1; S.cycle_iters = 0;
+    S.inner_tol = INNER_REL;
+    S.t_start = globaltimer();
+    S.t_done = 0;
+    for (int c = 0; c < 8; ++c) S.counter[c] = 0;
+}
+
+// sum of b^2 -> bnorm ; kind: FP64 batched vector
+__global__ void __launch_bounds__(MD_TB) k_norm_b(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                  const long long* __restrict__ off, const double* __restrict__ b,
+                                                  KState* st, double* part) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    const double* bi = b + off[sg.inst];
+    double v[1] = {0.0};
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) v[0] += bi[e] * bi[e];
+    double flag;
+    reduce_values<1>(v, 1, part, blockIdx.x, rng[sg.inst], &st[sg.inst].counter[0], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) st[sg.inst].bnorm = sqrt(sh[0]);
+}
+
+__device__ inline void mark_done(KState& S, int* ndone, int* res_iters, double* res_relres, double* res_time, int inst) {
+    S.active = 0;
+    S.converged = S.relres <= S.tol ? 1 : 0;
+    S.t_done = globaltimer();
+    S.m = 0;
+    res_iters[inst] = S.iters;
+    res_relres[inst] = S.relres;
+    res_time[inst] = (double)(S.t_done - S.t_start) * 1e-9;
+    atomicAdd(ndone, 1);
+}
+
+// FGMRES restart: r = b - y (y = A x in FP64), V_0 = r in FP32
+__global__ void __launch_bounds__(MD_TB) k_resid(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                 const long long* __restrict__ off, const InstDesc* __restrict__ D,
+                                                 const double* __restrict__ b, const double* __restrict__ y, float* V0,
+                                                 KState* st, double* part, int* ndone, int* res_iters,
+                                                 double* res_relres, double* res_time) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (S.t_done) return;  // finished instances skip
+    const long long o = off[sg.inst];
+    const int n3 = D[sg.inst].n3;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        const double r = b[o + e] - y[o + e];
+        const float rf = (float)r;
+        V0[o + e] = rf;
+        v[0] += r * r;
+        v[1] += (double)rf * rf;
+        if (e < n3) v[2] += (double)rf * rf;
+    }
+    double flag;
+    reduce_values<3>(v, 3, part, blockIdx.x, rng[sg.inst], &S.counter[1], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        S.beta = sqrt(sh[0]);
+        S.relres = S.bnorm > 0 ? S.beta / S.bnorm : 0.0;
+        S.m = 0;
+        S.j = 0;
+        if (S.relres <= S.tol || S.iters >= S.maxit) {
+            mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
+        } else {
+            S.active = 1;
+            S.g[0] = S.beta;
+            S.sig[0] = 1.0 / sqrt(sh[1]);
+            S.v3n2 = sh[2];
+        }
+    }
+}
+
+// W (= V_{j+1} slot) dots: d_i = (W, V_i), i <= j, and ||W||^2
+__global__ void __launch_bounds__(MD_TB) k_dots(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                const long long* __restrict__ off, const float* __restrict__ V,
+                                                long long total, int j, int pass, KState* st, double* part) {
+    __shared__ double sh[32 * (MD_KMAX + 2)];
+    __shared__ float sw[2048];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (!S.active || (pass == 1 && !S.reorth)) return;
+    const long long o = off[sg.inst];
+    const float* W = V + (long long)(j + 1) * total + o;
+    const int len = sg.end - sg.begin;
+    float wn = 0.f;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) {
+        float w = W[sg.begin + e];
+        sw[e] = w;
+        wn = fmaf(w, w, wn);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = 0; i <= j; ++i) {
+        const float* Vi = V + (long long)i * total + o + sg.begin;
+        float acc = 0.f;
+        for (int e = threadIdx.x; e < len; e += blockDim.x) acc = fmaf(sw[e], Vi[e], acc);
+        double x = warp_sum((double)acc);
+        if (lane == 0) sh[i * 32 + warp] = x;
+    }
+    {
+        double x = warp_sum((double)wn);
+        if (lane == 0) sh[(j + 1) * 32 + warp] = x;
+    }
+    __syncthreads();
+    const int cnt = j + 2;
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sh[r * 32 + w];
+        part[(size_t)blockIdx.x * MD_MAXR + r] = s;
+    }
+    const InstRange rg = rng[sg.inst];
+    if (!last_block_arrive(&S.counter[2], rg.count)) return;
+    double* H = S.H + (size_t)j * (MD_KMAX + 1);
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        double s = 0.0;
+        for (int b2 = rg.first; b2 < rg.first + rg.count; ++b2) s += part[(size_t)b2 * MD_MAXR + r];
+        if (r <= j) {
+            const double h = S.sig[j] * S.sig[r] * s;
+            if (pass == 0) H[r] = h; else H[r] += h;
+            S.coef[r] = S.sig[r] * S.sig[r] * s;
+        } else if (pass == 0) {
+            S.wn2_before = s;
+        }
+    }
+}
+
+// W -= sum_i coef_i V_i ; ||W||^2, ||W_3D||^2
+__global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                  const long long* __restrict__ off, const InstDesc* __restrict__ D,
+                                                  float* V, long long total, int j, int pass, KState* st, double* part) {
+    __shared__ double sh[32 * 4];
+    __shared__ float sc[MD_KMAX + 1];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (!S.active || (pass == 1 && !S.reorth)) return;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) sc[i] = (float)S.coef[i];
+    __syncthreads();
+    const long long o = off[sg.inst];
+    const int n3 = D[sg.inst].n3;
+    float* W = V + (long long)(j + 1) * total + o;
+    float a = 0.f, a3 = 0.f;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        float w = W[e];
+        for (int i = 0; i <= j; ++i) w = fmaf(-sc[i], V[(long long)i * total + o + e], w);
+        W[e] = w;
+        a = fmaf(w, w, a);
+        if (e < n3) a3 = fmaf(w, w, a3);
+    }
+    double v[2] = {(double)a, (double)a3};
+    double flag;
+    reduce_values<2>(v, 2, part, blockIdx.x, rng[sg.inst], &S.counter[3], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        const double wn2 = sh[0];
+        if (pass == 0 && wn2 < 0.25 * S.wn2_before && wn2 > 0.0) {
+            S.reorth = 1;
+            S.wn2_before = wn2;
+        } else {
+            S.reorth = 0;
+            S.H[(size_t)j * (MD_KMAX + 1) + j + 1] = S.sig[j] * sqrt(wn2);
+            S.sig[j + 1] = wn2 > 0.0 ? 1.0 / sqrt(wn2) : 0.0;
+            S.v3n2 = sh[1];
+        }
+    }
+}
+
+// Givens rotations, residual estimate, cycle exit; one thread per instance
+__global__ void k_givens(KState* st, int ninst, int j, int k) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    KState& S = st[i];
+    if (!S.active) return;
+    double* H = S.H + (size_t)j * (MD_KMAX + 1);
+    const double hlast = H[j + 1];
+    for (int r = 0; r < j; ++r) {
+        const double t = S.cs[r] * H[r] + S.sn[r] * H[r + 1];
+        H[r + 1] = -S.sn[r] * H[r] + S.cs[r] * H[r + 1];
+        H[r] = t;
+    }
+    const double den = hypot(H[j], H[j + 1]);
+    if (den == 0.0 || !isfinite(den)) {
+        S.active = 0;  // breakdown: keep the columns before j
+        S.nan_seen |= !isfinite(den);
+        return;
+    }
+    S.cs[j] = H[j] / den;
+    S.sn[j] = H[j + 1] / den;
+    H[j] = den;
+    H[j + 1] = 0.0;
+    S.g[j + 1] = -S.sn[j] * S.g[j];
+    S.g[j] = S.cs[j] * S.g[j];
+    S.est = fabs(S.g[j + 1]);
+    S.iters += 1;
+    S.m = j + 1;
+    if (S.est <= S.tol * S.bnorm || S.est <= S.inner_tol * S.beta || S.iters >= S.maxit || j + 1 == k ||
+        hlast == 0.0)
+        S.active = 0;
+}
+
+// H y = g on the m columns of this cycle; coef_i = y_i sig_i
+__global__ void k_lsq(KState* st, int ninst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    KState& S = st[i];
+    S.active = 0;
+    if (S.t_done || S.m == 0) return;
+    const int m = S.m;
+    for (int r = m - 1; r >= 0; --r) {
+        double s = S.g[r];
+        for (int l = r + 1; l < m; ++l) s -= S.H[(size_t)l * (MD_KMAX + 1) + r] * S.y[l];
+        S.y[r] = s / S.H[(size_t)r * (MD_KMAX + 1) + r];
+    }
+    for (int r = 0; r < m; ++r) S.coef[r] = S.y[r] * S.sig[r];
+}
+
+// x += sum_i coef_i Z_i  (FP32 correction, FP64 x)
+__global__ void __launch_bounds__(MD_TB) k_xupd(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                const float* __restrict__ Z, long long total, double* x, const KState* st) {
+    __shared__ float sc[MD_KMAX];
+    const Seg sg = seg[blockIdx.x];
+    const KState& S = st[sg.inst];
+    if (S.t_done || S.m == 0) return;
+    const int m = S.m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sc[i] = (float)S.coef[i];
+    __syncthreads();
+    const long long o = off[sg.inst];
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        float c = 0.f;
+        for (int i = 0; i < m; ++i) c = fmaf(sc[i], Z[(long long)i * total + o + e], c);
+        x[o + e] += (double)c;
+    }
+}
+
+// ---- preconditioner kernels ---------------------------------------------------
+// Jacobi: Z = diag(A)^{-1} V
+__global__ void __launch_bounds__(MD_TB) k_jacobi(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                  const InstDesc* __restrict__ D, const float* __restrict__ v, float* z,
+                                                  const KState* st) {
+    const Seg sg = seg[blockIdx.x];
+    if (st && !st[sg.inst].active) return;
+    const long long o = off[sg.inst];
+    const float* dinv = D[sg.inst].dinv32;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) z[o + e] = dinv[e] * v[o + e];
+}
+
+// 1D block solve z1 = B11^{-1} v1 (tree LDL^T sweeps in shared memory), the
+// lift l = beta Pi^T W Psi z1 on the touched grid nodes, and the input norm
+// s = ||v0 + l|| from ||v0||^2 (st.v3n2) and the touched-node correction.
+__global__ void __launch_bounds__(256) k_tree_lift(const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                                                   const float* __restrict__ v, float* z, KState* st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double sh[32];
+    const int inst = blockIdx.x;
+    KState& S = st[inst];
+    if (!S.active) return;
+    const InstDesc& d = D[inst];
+    const int n1 = d.n1;
+    float* y = reinterpret_cast<float*>(smraw);
+    float* sl = y + n1;
+    float* sdi = sl + n1;
+    int* sord = reinterpret_cast<int*>(sdi + n1);
+    int* spar = sord + n1;
+    const long long o = off[inst];
+    const float* v1 = v + o + d.n3;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        y[i] = v1[i];
+        sl[i] = d.tr_l32[i];
+        sdi[i] = d.tr_dinv32[i];
+        sord[i] = d.tr_order[i];
+        spar[i] = d.tr_parent[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int idx = 0; idx < n1; ++idx) {
+            const int i = sord[idx], p = spar[i];
+            if (p >= 0) y[p] -= sl[i] * y[i];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) y[i] *= sdi[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int idx = n1 - 1; idx >= 0; --idx) {
+            const int i = sord[idx], p = spar[i];
+            if (p >= 0) y[i] -= sl[i] * y[p];
+        }
+    }
+    __syncthreads();
+    float* z1 = z + o + d.n3;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) z1[i] = y[i];
+    const float beta = (float)d.beta;
+    const float* v0 = v + o;
+    double part = 0.0;
+    for (int idx = threadIdx.x; idx < d.ntouch; idx += blockDim.x) {
+        float acc = 0.f;
+        for (int jj = d.tn_ptr[idx]; jj < d.tn_ptr[idx + 1]; ++jj) {
+            const int q = d.tn_q[jj];
+            acc += d.tn_v32[jj] * (d.psa32[q] * y[d.qa[q]] + d.psb32[q] * y[d.qb[q]]);
+        }
+        const float l = beta * acc;
+        const int node = d.tn_node[idx];
+        d.ltouch32[idx] = l;
+        d.lift32[node] = l;
+        const float vv = v0[node];
+        part += (double)(2.f * vv * l + l * l);
+    }
+    double x = warp_sum(part);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        S.s2_touch = s;
+        const double s2 = S.v3n2 + s;
+        S.s = s2 > 0.0 ? sqrt(s2) : 0.0;
+    }
+}
+
+// ||v0||^2 of a preconditioner input given from outside the solver
+__global__ void __launch_bounds__(MD_TB) k_norm3(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                 const long long* __restrict__ off, const float* __restrict__ v,
+                                                 KState* st, double* part) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    const float* vi = v + off[sg.inst];
+    float a = 0.f;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) a = fmaf(vi[e], vi[e], a);
+    double vals[1] = {(double)a};
+    double flag;
+    reduce_values<1>(vals, 1, part, blockIdx.x, rng[sg.inst], &S.counter[4], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) S.v3n2 = sh[0];
+}
+
+// ---- CG (FP64) -------------------------------------------------------------------
+__global__ void __launch_bounds__(MD_TB) k_cg_init(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                   const long long* __restrict__ off, const InstDesc* __restrict__ D,
+                                                   const double* __restrict__ b, const double* __restrict__ y,
+                                                   double* r, double* p, KState* st, double* part, int* ndone,
+                                                   int* res_iters, double* res_relres, double* res_time) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    const long long o = off[sg.inst];
+    const double* dinv = D[sg.inst].dinv64;
+    double v[2] = {0.0, 0.0};
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        const double rr = b[o + e] - y[o + e];
+        r[o + e] = rr;
+        const double zz = dinv[e] * rr;
+        p[o + e] = zz;
+        v[0] += rr * zz;
+        v[1] += rr * rr;
+    }
+    double flag;
+    reduce_values<2>(v, 2, part, blockIdx.x, rng[sg.inst], &S.counter[1], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        S.rho = sh[0];
+        S.relres = S.bnorm > 0 ? sqrt(sh[1]) / S.bnorm : 0.0;
+        if (S.relres <= S.tol || S.iters >= S.maxit) mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
+        else S.active = 1;
+    }
+}
+
+__global__ void __launch_bounds__(MD_TB) k_cg_alpha(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                    const long long* __restrict__ off, const double* __restrict__ p,
+                                                    const double* __restrict__ q, KState* st, double* part) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (!S.active) return;
+    const long long o = off[sg.inst];
+    double v[1] = {0.0};
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) v[0] += p[o + e] * q[o + e];
+    double flag;
+    reduce_values<1>(v, 1, part, blockIdx.x, rng[sg.inst], &S.counter[2], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        S.pq = sh[0];
+        S.alpha_cg = S.rho / sh[0];
+    }
+}
+
+__global__ void __launch_bounds__(MD_TB) k_cg_xr(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                 const long long* __restrict__ off, const InstDesc* __restrict__ D,
+                                                 double* x, double* r, const double* __restrict__ p,
+                                                 const double* __restrict__ q, KState* st, double* part, int* ndone,
+                                                 int* res_iters, double* res_relres, double* res_time) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (!S.active) return;
+    const long long o = off[sg.inst];
+    const double a = S.alpha_cg;
+    const double* dinv = D[sg.inst].dinv64;
+    double v[2] = {0.0, 0.0};
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        x[o + e] += a * p[o + e];
+        const double rr = r[o + e] - a * q[o + e];
+        r[o + e] = rr;
+        v[0] += rr * (dinv[e] * rr);
+        v[1] += rr * rr;
+    }
+    double flag;
+    reduce_values<2>(v, 2, part, blockIdx.x, rng[sg.inst], &S.counter[3], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        const double rho_new = sh[0];
+        S.coef[0] = rho_new / S.rho;  // beta of the p update
+        S.rho = rho_new;
+        S.iters += 1;
+        S.relres = S.bnorm > 0 ? sqrt(sh[1]) / S.bnorm : 0.0;
+        if (S.relres <= S.tol || S.iters >= S.maxit || !isfinite(S.relres)) {
+            S.active = 0;
+            S.reorth = 1;  // marks "stopped, needs the true residual"
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MD_TB) k_cg_p(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                const InstDesc* __restrict__ D, const double* __restrict__ r,
+                                                double* p, const KState* st) {
+    const Seg sg = seg[blockIdx.x];
+    const KState& S = st[sg.inst];
+    if (!S.active) return;
+    const long long o = off[sg.inst];
+    const double bc = S.coef[0];
+    const double* dinv = D[sg.inst].dinv64;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) p[o + e] = dinv[e] * r[o + e] + bc * p[o + e];
+}
+
+// true residual after CG stopped: relres = ||b - A x|| / ||b||
+__global__ void __launch_bounds__(MD_TB) k_cg_final(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                    const long long* __restrict__ off, const double* __restrict__ b,
+                                                    const double* __restrict__ y, KState* st, double* part, int* ndone,
+                                                    int* res_iters, double* res_relres, double* res_time) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (S.t_done || !S.reorth) return;
+    const long long o = off[sg.inst];
+    double v[1] = {0.0};
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        const double rr = b[o + e] - y[o + e];
+        v[0] += rr * rr;
+    }
+    double flag;
+    reduce_values<1>(v, 1, part, blockIdx.x, rng[sg.inst], &S.counter[4], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        S.relres = S.bnorm > 0 ? sqrt(sh[0]) / S.bnorm : 0.0;
+        S.reorth = 0;
+        mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    if (!cnn) {
+        k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st);
+        MD_CHECK_LAUNCH();
+        return MD_OK;
+    }
+    const size_t smem = (size_t)B->max_n1 * 20;
+    k_tree_lift<<<B->ninst, 256, smem, s>>>(B->d, B->off, vin, zout, B->st);
+    MD_CHECK_LAUNCH();
+    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, s));
+    OutIO io{zout, B->off, vin, B->off, B->st, B->d};
+    MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s));
+    return MD_OK;
+}
+
+static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    const long long tot = B->total;
+    const int gb = (B->ninst + 31) / 32;
+    for (int j = 0; j < B->k; ++j) {
+        const float* Vj = B->V + (long long)j * tot;
+        float* Zj = B->Z + (long long)j * tot;
+        float* W = B->V + (long long)(j + 1) * tot;
+        MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, s));
+        MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
+        for (int pass = 0; pass < 2; ++pass) {
+            k_dots<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, tot, j, pass, B->st, B->part);
+            k_update<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, tot, j, pass, B->st, B->part);
+        }
+        k_givens<<<gb, 32, 0, s>>>(B->st, B->ninst, j, B->k);
+        MD_CHECK_LAUNCH();
+    }
+    k_lsq<<<gb, 32, 0, s>>>(B->st, B->ninst);
+    k_xupd<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->Z, tot, B->x, B->st);
+    MD_CHECK_LAUNCH();
+    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
+    k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st, B->part,
+                                             B->ndone, B->res_iters, B->res_relres, B->res_time);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+#define CG_CHUNK 25
+static md_status launch_cycle_cg(md_batch* B, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    for (int it = 0; it < CG_CHUNK; ++it) {
+        MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->p64, B->off, B->y64, s, B->st, 1));
+        k_cg_alpha<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->p64, B->y64, B->st, B->part);
+        k_cg_xr<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->x, B->r64, B->p64, B->y64,
+                                                 B->st, B->part, B->ndone, B->res_iters, B->res_relres, B->res_time);
+        k_cg_p<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, B->r64, B->p64, B->st);
+        MD_CHECK_LAUNCH();
+    }
+    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
+    k_cg_final<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->b, B->y64, B->st, B->part, B->ndone,
+                                                B->res_iters, B->res_relres, B->res_time);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+static md_status build_graph(md_batch* B) {
+    if (B->graph && B->graph_cnn == B->cnn) return MD_OK;
+    if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+    cudaGraph_t g;
+    MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+    md_status st = (B->solver == MD_SOLVER_CG_JACOBI) ? launch_cycle_cg(B, B->cap) : launch_cycle_fgmres(B, B->cap);
+    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+    if (st != MD_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return st; }
+    MD_CUDA(e);
+    e = cudaGraphInstantiate(&B->graph, g, 0);
+    cudaGraphDestroy(g);
+    MD_CUDA(e);
+    B->graph_cnn = B->cnn;
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const md_cnn* cnn, md_solver solver,
+                                     int restart, md_batch** out) {
+    if (!out || n_ops < 1 || !ops) { md_set_error("md_batch_create: bad argument"); return MD_ERR_ARG; }
+    *out = nullptr;
+    if (solver != MD_SOLVER_CG_JACOBI && (restart < 1 || restart > MD_KMAX)) {
+        md_set_error("md_batch_create: restart %d outside [1, %d]", restart, MD_KMAX); return MD_ERR_ARG;
+    }
+    if (solver == MD_SOLVER_FGMRES_CNN && !cnn) { md_set_error("md_batch_create: network required"); return MD_ERR_ARG; }
+    md_batch* B = new md_batch();
+    B->ninst = n_ops;
+    B->solver = solver;
+    B->k = solver == MD_SOLVER_CG_JACOBI ? 1 : restart;
+    B->cnn = cnn;
+    std::vector<const InstDesc*> ptrs;
+    std::vector<int> Ns;
+    long long tot = 0;
+    for (int i = 0; i < n_ops; ++i) {
+        if (!ops[i]) { delete B; md_set_error("md_batch_create: op %d is NULL", i); return MD_ERR_ARG; }
+        for (int j2 = 0; j2 < i; ++j2)
+            if (ops[j2] == ops[i]) { delete B; md_set_error("md_batch_create: op %d repeated", i); return MD_ERR_ARG; }
+        B->ops.push_back(ops[i]);
+        B->hdesc.push_back(ops[i]->h);
+        B->hoff.push_back(tot);
+        tot += ops[i]->h.n;
+        B->max_n1 = std::max(B->max_n1, ops[i]->h.n1);
+        Ns.push_back(ops[i]->h.N);
+    }
+    B->hoff.push_back(tot);
+    B->total = tot;
+    for (auto& d : B->hdesc) ptrs.push_back(&d);
+    md_status st = MD_OK;
+    auto chk = [&](md_status s2) { if (st == MD_OK) st = s2; };
+    chk(dev_upload(&B->allocs, &B->d, B->hdesc.data(), B->hdesc.size()));
+    chk(build_tables(ptrs, &B->tabs, &B->allocs));
+    chk(dev_upload(&B->allocs, &B->off, B->hoff.data(), B->hoff.size()));
+    chk(dev_alloc(&B->allocs, &B->x, (size_t)tot));
+    chk(dev_alloc(&B->allocs, &B->b, (size_t)tot));
+    chk(dev_alloc(&B->allocs, &B->y64, (size_t)tot));
+    if (solver == MD_SOLVER_CG_JACOBI) {
+        chk(dev_alloc(&B->allocs, &B->r64, (size_t)tot));
+        chk(dev_alloc(&B->allocs, &B->p64, (size_t)tot));
+    } else {
+        chk(dev_alloc(&B->allocs, &B->V, (size_t)(B->k + 1) * tot));
+        chk(dev_alloc(&B->allocs, &B->Z, (size_t)B->k * tot));
+    }
+    chk(dev_alloc(&B->allocs, &B->st, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->part, (size_t)std::max(B->tabs.vec.nblocks, 1) * MD_MAXR));
+    chk(dev_alloc(&B->allocs, &B->ndone, 1));
+    chk(dev_alloc(&B->allocs, &B->res_iters, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->res_relres, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->res_time, (size_t)n_ops));
+    if (st == MD_OK && solver == MD_SOLVER_FGMRES_CNN) {
+        chk(cnn_work_create(Ns, &B->cw));
+        const size_t smem = (size_t)B->max_n1 * 20;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) chk(md_cuda_status(e, "tree smem", __FILE__, __LINE__));
+        }
+    }
+    if (st == MD_OK) {
+        cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) chk(md_cuda_status(e, "cudaStreamCreate", __FILE__, __LINE__));
+    }
+    if (st == MD_OK) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) chk(md_cuda_status(e, "md_batch_create", __FILE__, __LINE__));
+    }
+    if (st != MD_OK) { md_batch_destroy(B); return st; }
+    *out = B;
+    return MD_OK;
+}
+
+extern "C" void md_batch_destroy(md_batch* B) {
+    if (!B) return;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    cnn_work_destroy(B->cw);
+    dev_free_all(&B->allocs);
+    delete B;
+}
+
+extern "C" md_status md_batch_offsets(const md_batch* B, long long* offsets) {
+    if (!B || !offsets) { md_set_error("md_batch_offsets: NULL argument"); return MD_ERR_ARG; }
+    memcpy(offsets, B->hoff.data(), sizeof(long long) * B->hoff.size());
+    return MD_OK;
+}
+
+static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    const int gb = (B->ninst + 31) / 32;
+    k_init_state<<<gb, 32, 0, s>>>(B->st, B->ninst, tol, maxit, B->ndone);
+    k_norm_b<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->b, B->st, B->part);
+    MD_CHECK_LAUNCH();
+    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
+    if (B->solver == MD_SOLVER_CG_JACOBI) {
+        k_cg_init<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->r64, B->p64,
+                                                   B->st, B->part, B->ndone, B->res_iters, B->res_relres, B->res_time);
+    } else {
+        k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st,
+                                                 B->part, B->ndone, B->res_iters, B->res_relres, B->res_time);
+    }
+    MD_CHECK_LAUNCH();
+    MD_TRY(build_graph(B));
+    const int per_cycle = B->solver == MD_SOLVER_CG_JACOBI ? CG_CHUNK : B->k;
+    const long long max_cycles = (long long)maxit / per_cycle + 3;
+    int ndone = 0;
+    for (long long c = 0; c <= max_cycles; ++c) {
+        MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MD_CUDA(cudaStreamSynchronize(s));
+        if (ndone >= B->ninst) break;
+        MD_CUDA(cudaGraphLaunch(B->graph, s));
+    }
+    if (ndone < B->ninst) { md_set_error("batch solve did not terminate"); return MD_ERR_TIMEOUT; }
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_solve(md_batch* B, const double* b_all, double* x_all, double tol, int maxit,
+                                    int* iters, double* relres, md_stream stream) {
+    if (!B || !b_all || !x_all || !(tol > 0) || maxit < 1) { md_set_error("md_batch_solve: bad argument"); return MD_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    MD_CUDA(cudaMemcpyAsync(B->b, b_all, sizeof(double) * B->total, cudaMemcpyDeviceToDevice, s));
+    MD_CUDA(cudaMemcpyAsync(B->x, x_all, sizeof(double) * B->total, cudaMemcpyDeviceToDevice, s));
+    MD_TRY(batch_run(B, tol, maxit, s));
+    MD_CUDA(cudaMemcpyAsync(x_all, B->x, sizeof(double) * B->total, cudaMemcpyDeviceToDevice, s));
+    std::vector<int> it(B->ninst);
+    std::vector<double> rr(B->ninst);
+    B->last_times.resize(B->ninst);
+    MD_CUDA(cudaMemcpyAsync(it.data(), B->res_iters, sizeof(int) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(rr.data(), B->res_relres, sizeof(double) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(B->last_times.data(), B->res_time, sizeof(double) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int i = 0; i < B->ninst; ++i) {
+        if (iters) iters[i] = it[i];
+        if (relres) relres[i] = rr[i];
+        if (!(rr[i] <= tol)) all = false;
+    }
+    return all ? MD_OK : MD_NOT_CONVERGED;
+}
+
+extern "C" md_status md_batch_times(const md_batch* B, double* seconds) {
+    if (!B || !seconds) { md_set_error("md_batch_times: NULL argument"); return MD_ERR_ARG; }
+    for (int i = 0; i < B->ninst && i < (int)B->last_times.size(); ++i) seconds[i] = B->last_times[i];
+    return MD_OK;
+}
+
+static md_status op_batch(const md_op* op_c, md_solver solver, int restart, const md_cnn* cnn, md_batch** out) {
+    md_op* op = const_cast<md_op*>(op_c);
+    const int slot = (int)solver;
+    md_batch*& B = op->solver_cache[slot];
+    if (B && (op->solver_cache_restart[slot] != restart)) { md_batch_destroy(B); B = nullptr; }
+    if (!B) {
+        const md_op* ops[1] = {op};
+        MD_TRY(md_batch_create(1, ops, cnn, solver, restart, &B));
+        op->solver_cache_restart[slot] = restart;
+    }
+    B->cnn = cnn;
+    *out = B;
+    return MD_OK;
+}
+
+extern "C" md_status md_solve(const md_op* op, const md_cnn* cnn, const double* b, double* x, double tol, int restart,
+                              int maxit, int* iters, double* relres, md_stream s) {
+    if (!op || !b || !x) { md_set_error("md_solve: NULL argument"); return MD_ERR_ARG; }
+    md_batch* B = nullptr;
+    MD_TRY(op_batch(op, cnn ? MD_SOLVER_FGMRES_CNN : MD_SOLVER_CG_JACOBI, cnn ? restart : 1, cnn, &B));
+    return md_batch_solve(B, b, x, tol, maxit, iters, relres, s);
+}
+
+extern "C" md_status md_solve_batched(int n, const md_op* const* ops, const md_cnn* cnn, const double* const* b,
+                                      double* const* x, double tol, int restart, int maxit, int* iters,
+                                      double* relres, md_stream stream) {
+    if (n < 1 || !ops || !b || !x) { md_set_error("md_solve_batched: bad argument"); return MD_ERR_ARG; }
+    md_batch* B = nullptr;
+    MD_TRY(md_batch_create(n, ops, cnn, cnn ? MD_SOLVER_FGMRES_CNN : MD_SOLVER_CG_JACOBI, cnn ? restart : 1, &B));
+    cudaStream_t s = (cudaStream_t)stream;
+    md_status st = MD_OK;
+    for (int i = 0; i < n && st == MD_OK; ++i) {
+        cudaError_t e = cudaMemcpyAsync(B->b + B->hoff[i], b[i], sizeof(double) * ops[i]->h.n, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B->x + B->hoff[i], x[i], sizeof(double) * ops[i]->h.n, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) st = md_cuda_status(e, "md_solve_batched copy", __FILE__, __LINE__);
+    }
+    if (st == MD_OK) st = batch_run(B, tol, maxit, s);
+    if (st == MD_OK) {
+        for (int i = 0; i < n && st == MD_OK; ++i) {
+            cudaError_t e = cudaMemcpyAsync(x[i], B->x + B->hoff[i], sizeof(double) * ops[i]->h.n, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) st = md_cuda_status(e, "md_solve_batched copy", __FILE__, __LINE__);
+        }
+        std::vector<int> it(n);
+        std::vector<double> rr(n);
+        cudaMemcpyAsync(it.data(), B->res_iters, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(rr.data(), B->res_relres, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess && st == MD_OK) st = md_cuda_status(e, "md_solve_batched", __FILE__, __LINE__);
+        bool all = true;
+        for (int i = 0; i < n; ++i) {
+            if (iters) iters[i] = it[i];
+            if (relres) relres[i] = rr[i];
+            if (!(rr[i] <= tol)) all = false;
+        }
+        if (st == MD_OK && !all) st = MD_NOT_CONVERGED;
+    }
+    md_batch_destroy(B);
+    return st;
+}
+
+// Standalone preconditioner application (one instance).
+__global__ void k_prec_setup(KState* st) { st[0].active = 1; }
+
+extern "C" md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream stream) {
+    if (!op || !r || !z) { md_set_error("md_precondition: NULL argument"); return MD_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    md_batch* B = nullptr;
+    MD_TRY(op_batch(op, cnn ? MD_SOLVER_FGMRES_CNN : MD_SOLVER_FGMRES_JACOBI, 1, cnn, &B));
+    k_prec_setup<<<1, 1, 0, s>>>(B->st);
+    if (cnn) {
+        const Tables& T = B->tabs;
+        k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
+        MD_CHECK_LAUNCH();
+    }
+    return launch_precond(B, cnn, r, z, s);
+}

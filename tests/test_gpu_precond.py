@@ -1,0 +1,77 @@
+"""Parity of the network and the block preconditioner against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import instance_cases, rel_l2
+from oracle import cnn, fem, solvers
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_layers(flat):
+    from paper_2505_08491_gb300.weights import flat_to_layers
+    return flat_to_layers(flat)
+
+
+@pytest.mark.parametrize("n", [5, 9, 17, 33])
+def test_network_forward_matches_oracle(n):
+    from paper_2505_08491_gb300 import Network
+    from paper_2505_08491_gb300.weights import random_params
+    flat = random_params(5)
+    layers = [(cnn.round_bf16(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in oracle_layers(flat)]
+    net = Network(flat)
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((2, 3, n, n, n)).astype(np.float32)
+    Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    for s in range(2):
+        ref16 = cnn.forward(X[s].astype(np.float64), layers, bf16=True)
+        ref64 = cnn.forward(X[s].astype(np.float64), layers, bf16=False)
+        assert rel_l2(Y[s], ref16) <= 2e-3
+        assert rel_l2(Y[s], ref64) <= 3e-2
+
+
+def test_identity_pair_network_is_near_identity():
+    from paper_2505_08491_gb300 import Network
+    from paper_2505_08491_gb300.weights import identity_pair_params
+    net = Network(identity_pair_params())
+    X = np.random.default_rng(3).standard_normal((1, 3, 7, 7, 7)).astype(np.float32)
+    Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    assert rel_l2(Y[0, 0], X[0, 0] + X[0, 1]) <= 2e-2
+
+
+@pytest.mark.parametrize("case", instance_cases()[:3], ids=[c[0] for c in instance_cases()[:3]])
+def test_block_preconditioner_matches_oracle(case):
+    from paper_2505_08491_gb300 import Network, Operator
+    from paper_2505_08491_gb300.weights import random_params
+    name, N, g, beta, _ = case
+    p = fem.Problem(N, g, beta)
+    op = Operator(N, g, beta)
+    flat = random_params(9)
+    layers = [(cnn.round_bf16(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in oracle_layers(flat)]
+    net = Network(flat)
+    r = np.random.default_rng(4).standard_normal(p.n).astype(np.float32)
+    r[:p.n3][p.bd] = 0.0
+    z = op.precondition(torch.from_numpy(r).cuda(), net).cpu().numpy()
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True)
+    ref = Q(r.astype(np.float64))
+    # 1D part: exact tree solve in FP32
+    assert rel_l2(z[p.n3:], ref[p.n3:]) <= 1e-5
+    # 3D part: BF16 network
+    assert rel_l2(z[:p.n3], ref[:p.n3]) <= 5e-3
+    # Dirichlet rows copy the input
+    assert np.array_equal(z[:p.n3][p.bd], r[:p.n3][p.bd])
+
+
+def test_preconditioner_positive_homogeneity():
+    from paper_2505_08491_gb300 import Network, Operator
+    from paper_2505_08491_gb300.weights import random_params
+    name, N, g, beta, _ = instance_cases()[1]
+    op = Operator(N, g, beta)
+    net = Network(random_params(2))
+    p = fem.Problem(N, g, beta)
+    r = np.random.default_rng(5).standard_normal(p.n).astype(np.float32)
+    r[:p.n3][p.bd] = 0
+    z1 = op.precondition(torch.from_numpy(r).cuda(), net).cpu().numpy()
+    z2 = op.precondition(torch.from_numpy(4.0 * r).cuda(), net).cpu().numpy()
+    assert rel_l2(z2, 4.0 * z1) <= 1e-5
