@@ -197,6 +197,28 @@ md_status md_batch_solve(md_batch* b, const double* b_all, double* x_all, double
  * last md_batch_solve, relative to its start; host array of n_ops. */
 md_status md_batch_times(const md_batch* b, double* seconds);
 
+/* Instrumentation.  With profiling on, every captured restart cycle records
+ * CUDA events around each preconditioner application, around its four
+ * hidden 32->32 convolutions, around the operator apply and around the
+ * Arnoldi/Givens kernels; md_batch_stats returns totals since the last
+ * reset (device time, ms, summed over launches) and the number of kernel
+ * launches the batch issued.  Timing events add no work to the kernels. */
+typedef struct {
+    long long kernel_launches;   /* kernels launched by md_batch_solve calls */
+    long long cycles;            /* restart cycles (CG: chunks of 25 iterations) */
+    long long iterations;        /* sum over instances of Krylov iterations */
+    long long precond_nodes;     /* sum over instances of iterations x grid nodes */
+    double prec_ms;              /* preconditioner applications (iteration slots) */
+    double conv_hidden_ms;       /* the 4 hidden convolution launches per application */
+    long long conv_hidden_launches;
+    double apply_ms;             /* A z in FP32 */
+    double arnoldi_ms;           /* dots, updates, Givens */
+    double restart_ms;           /* least squares, x update, FP64 residual */
+} md_batch_stats_t;
+md_status md_batch_set_profiling(md_batch* b, int enable);
+md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
+md_status md_batch_reset_stats(md_batch* b);
+
 /* md_solve_batched -- one-shot form: create, solve (per-instance device
  * pointers given as host arrays), destroy. */
 md_status md_solve_batched(int n, const md_op* const* ops, const md_cnn* cnn, const double* const* b,

@@ -124,6 +124,18 @@ def normal_vector(base_seed: int, instance: int, n: int, stream: int = 0) -> np.
     return rng.standard_normal(n)
 
 
+def interior_source(N: int, seed: int | None) -> np.ndarray | None:
+    """Nodal source f ~ N(0, 1) on the interior nodes of the (N+1)^3 grid
+    (x fastest), 0 on the cube boundary; None when seed is None (f = 0)."""
+    if seed is None:
+        return None
+    f = normal_vector(seed, 0, (N + 1) ** 3)
+    idx = np.arange(N + 1)
+    b = (idx == 0) | (idx == N)
+    f[(b[:, None, None] | b[None, :, None] | b[None, None, :]).ravel()] = 0.0
+    return f
+
+
 # Workload recipes.  Sizes are Q1 elements per cube edge (N); nodes (N+1)^3.
 WORKLOADS = {
     # one straight segment, f = 0, g = 1, Jacobi-CG to 1e-10 in FP64

@@ -291,12 +291,8 @@ class Problem:
 
     def source(self, seed: int | None) -> np.ndarray | None:
         """Nodal f ~ N(0,1) on interior nodes, 0 on the boundary."""
-        if seed is None:
-            return None
-        from mdgen import normal_vector
-        f = normal_vector(seed, 0, self.n3)
-        f[self.bd] = 0.0
-        return f
+        from mdgen import interior_source
+        return interior_source(self.N, seed)
 
     def apply(self, u: np.ndarray) -> np.ndarray:
         return self.A @ u

@@ -29,6 +29,13 @@ class MdOpInfo(C.Structure):
                 ("n", C.c_longlong), ("alpha", C.c_double), ("beta", C.c_double)]
 
 
+class MdBatchStats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_longlong), ("cycles", C.c_longlong), ("iterations", C.c_longlong),
+                ("precond_nodes", C.c_longlong), ("prec_ms", C.c_double), ("conv_hidden_ms", C.c_double),
+                ("conv_hidden_launches", C.c_longlong), ("apply_ms", C.c_double), ("arnoldi_ms", C.c_double),
+                ("restart_ms", C.c_double)]
+
+
 class MdTrainCfg(C.Structure):
     _fields_ = [("n_ops", C.c_int), ("ops", C.POINTER(C.c_void_p)), ("n_samples", C.c_int),
                 ("sample_op", C.POINTER(C.c_int)), ("sample_r", C.POINTER(C.c_void_p)),
@@ -66,6 +73,9 @@ SIGNATURES = {
     "md_batch_offsets": (st, [vp, C.POINTER(i64)]),
     "md_batch_solve": (st, [vp, vp, vp, f64, i32, C.POINTER(i32), C.POINTER(f64), vp]),
     "md_batch_times": (st, [vp, C.POINTER(f64)]),
+    "md_batch_set_profiling": (st, [vp, i32]),
+    "md_batch_stats": (st, [vp, C.POINTER(MdBatchStats)]),
+    "md_batch_reset_stats": (st, [vp]),
     "md_solve_batched": (st, [i32, C.POINTER(vp), vp, C.POINTER(vp), C.POINTER(vp), f64, i32, i32,
                               C.POINTER(i32), C.POINTER(f64), vp]),
     "md_train": (st, [vp, C.POINTER(MdTrainCfg)]),

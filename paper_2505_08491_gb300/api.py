@@ -202,6 +202,17 @@ class Batch:
                     "md_batch_solve", allow=(L.MD_OK, L.MD_NOT_CONVERGED))
         return list(it), list(rr), s == L.MD_OK
 
+    def set_profiling(self, enable: bool):
+        L.check(L.load().md_batch_set_profiling(self._h, 1 if enable else 0), "md_batch_set_profiling")
+
+    def stats(self) -> dict:
+        st = L.MdBatchStats()
+        L.check(L.load().md_batch_stats(self._h, C.byref(st)), "md_batch_stats")
+        return {k: getattr(st, k) for k, _ in L.MdBatchStats._fields_}
+
+    def reset_stats(self):
+        L.check(L.load().md_batch_reset_stats(self._h), "md_batch_reset_stats")
+
     def times(self):
         n = len(self.ops)
         t = (C.c_double * n)()

@@ -40,7 +40,8 @@ struct OutIO {
     const InstDesc* D;         // CONV_PREC: D[i].alpha
 };
 
-md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s);
+md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
+                             cudaEvent_t e_hidden0 = nullptr, cudaEvent_t e_hidden1 = nullptr);
 // X0 = [v0 / s, l / s, d] from a preconditioner input (instance 3D part at v + voff[i])
 md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
                         cudaStream_t s);

@@ -51,8 +51,28 @@ struct md_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     const md_cnn* graph_cnn = nullptr;
+    bool graph_prof = false;
+    long long graph_kernels = 0;
     std::vector<double> last_times;
+    // instrumentation
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;   // per iteration slot j: 6 events, then 2 for the restart
+    md_batch_stats_t stats{};
 };
+
+enum { EV_PRE0 = 0, EV_CONV0, EV_CONV1, EV_APPLY0, EV_APPLY1, EV_ARN1, EV_PER_J };
+
+static cudaEvent_t ev_at(md_batch* B, int j, int which) {
+    if (!B->profiling) return nullptr;
+    return B->ev[(size_t)j * EV_PER_J + which];
+}
+static cudaEvent_t ev_restart(md_batch* B, int which) {
+    if (!B->profiling) return nullptr;
+    return B->ev[(size_t)B->k * EV_PER_J + which];
+}
+static void rec(cudaEvent_t e, cudaStream_t s) {
+    if (e) cudaEventRecord(e, s);
+}
 
 // ---------------------------------------------------------------------------
 // reduction helper: each block writes R partials; the last block of the
@@ -543,11 +563,14 @@ __global__ void __launch_bounds__(MD_TB) k_cg_final(const Seg* __restrict__ seg,
 
 // ---------------------------------------------------------------------------
 // host side
-static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, cudaStream_t s) {
+static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, cudaStream_t s,
+                                cudaEvent_t e_conv0 = nullptr, cudaEvent_t e_conv1 = nullptr) {
     const Tables& T = B->tabs;
     if (!cnn) {
         k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st);
         MD_CHECK_LAUNCH();
+        rec(e_conv0, s);
+        rec(e_conv1, s);
         return MD_OK;
     }
     const size_t smem = (size_t)B->max_n1 * 20;
@@ -555,7 +578,7 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     MD_CHECK_LAUNCH();
     MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, s));
     OutIO io{zout, B->off, vin, B->off, B->st, B->d};
-    MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s));
+    MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
     return MD_OK;
 }
 
@@ -567,14 +590,19 @@ static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
         const float* Vj = B->V + (long long)j * tot;
         float* Zj = B->Z + (long long)j * tot;
         float* W = B->V + (long long)(j + 1) * tot;
-        MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, s));
+        rec(ev_at(B, j, EV_PRE0), s);
+        MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, s,
+                              ev_at(B, j, EV_CONV0), ev_at(B, j, EV_CONV1)));
+        rec(ev_at(B, j, EV_APPLY0), s);
         MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
+        rec(ev_at(B, j, EV_APPLY1), s);
         for (int pass = 0; pass < 2; ++pass) {
             k_dots<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, tot, j, pass, B->st, B->part);
             k_update<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, tot, j, pass, B->st, B->part);
         }
         k_givens<<<gb, 32, 0, s>>>(B->st, B->ninst, j, B->k);
         MD_CHECK_LAUNCH();
+        rec(ev_at(B, j, EV_ARN1), s);
     }
     k_lsq<<<gb, 32, 0, s>>>(B->st, B->ninst);
     k_xupd<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->Z, tot, B->x, B->st);
@@ -583,6 +611,7 @@ static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
     k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st, B->part,
                                              B->ndone, B->res_iters, B->res_relres, B->res_time);
     MD_CHECK_LAUNCH();
+    rec(ev_restart(B, 1), s);
     return MD_OK;
 }
 
@@ -605,19 +634,49 @@ static md_status launch_cycle_cg(md_batch* B, cudaStream_t s) {
 }
 
 static md_status build_graph(md_batch* B) {
-    if (B->graph && B->graph_cnn == B->cnn) return MD_OK;
+    if (B->graph && B->graph_cnn == B->cnn && B->graph_prof == B->profiling) return MD_OK;
     if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+    if (B->profiling && B->ev.empty()) {
+        B->ev.resize((size_t)B->k * EV_PER_J + 2);
+        for (auto& e : B->ev) MD_CUDA(cudaEventCreate(&e));
+    }
     cudaGraph_t g;
     MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
     md_status st = (B->solver == MD_SOLVER_CG_JACOBI) ? launch_cycle_cg(B, B->cap) : launch_cycle_fgmres(B, B->cap);
     cudaError_t e = cudaStreamEndCapture(B->cap, &g);
     if (st != MD_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return st; }
     MD_CUDA(e);
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    B->graph_kernels = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) B->graph_kernels++;
+    }
     e = cudaGraphInstantiate(&B->graph, g, 0);
     cudaGraphDestroy(g);
     MD_CUDA(e);
     B->graph_cnn = B->cnn;
+    B->graph_prof = B->profiling;
     return MD_OK;
+}
+
+static void accumulate_events(md_batch* B) {
+    if (!B->profiling || B->solver == MD_SOLVER_CG_JACOBI) return;
+    auto el = [](cudaEvent_t a, cudaEvent_t b) {
+        float ms = 0.f;
+        return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : 0.0;
+    };
+    for (int j = 0; j < B->k; ++j) {
+        B->stats.prec_ms += el(ev_at(B, j, EV_PRE0), ev_at(B, j, EV_APPLY0));
+        B->stats.conv_hidden_ms += el(ev_at(B, j, EV_CONV0), ev_at(B, j, EV_CONV1));
+        B->stats.apply_ms += el(ev_at(B, j, EV_APPLY0), ev_at(B, j, EV_APPLY1));
+        B->stats.arnoldi_ms += el(ev_at(B, j, EV_APPLY1), ev_at(B, j, EV_ARN1));
+        if (B->solver == MD_SOLVER_FGMRES_CNN) B->stats.conv_hidden_launches += 4;
+    }
+    B->stats.restart_ms += el(ev_at(B, B->k - 1, EV_ARN1), ev_restart(B, 1));
 }
 
 extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const md_cnn* cnn, md_solver solver,
@@ -694,6 +753,7 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
 
 extern "C" void md_batch_destroy(md_batch* B) {
     if (!B) return;
+    for (auto e : B->ev) cudaEventDestroy(e);
     if (B->graph) cudaGraphExecDestroy(B->graph);
     if (B->cap) cudaStreamDestroy(B->cap);
     cnn_work_destroy(B->cw);
@@ -726,11 +786,15 @@ static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
     const int per_cycle = B->solver == MD_SOLVER_CG_JACOBI ? CG_CHUNK : B->k;
     const long long max_cycles = (long long)maxit / per_cycle + 3;
     int ndone = 0;
+    B->stats.kernel_launches += 5;
     for (long long c = 0; c <= max_cycles; ++c) {
         MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
         MD_CUDA(cudaStreamSynchronize(s));
+        if (c > 0) accumulate_events(B);
         if (ndone >= B->ninst) break;
         MD_CUDA(cudaGraphLaunch(B->graph, s));
+        B->stats.cycles += 1;
+        B->stats.kernel_launches += B->graph_kernels;
     }
     if (ndone < B->ninst) { md_set_error("batch solve did not terminate"); return MD_ERR_TIMEOUT; }
     return MD_OK;
@@ -756,8 +820,28 @@ extern "C" md_status md_batch_solve(md_batch* B, const double* b_all, double* x_
         if (iters) iters[i] = it[i];
         if (relres) relres[i] = rr[i];
         if (!(rr[i] <= tol)) all = false;
+        B->stats.iterations += it[i];
+        B->stats.precond_nodes += (long long)it[i] * B->hdesc[i].n3;
     }
     return all ? MD_OK : MD_NOT_CONVERGED;
+}
+
+extern "C" md_status md_batch_set_profiling(md_batch* B, int enable) {
+    if (!B) { md_set_error("md_batch_set_profiling: NULL batch"); return MD_ERR_ARG; }
+    B->profiling = enable != 0;
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_stats(const md_batch* B, md_batch_stats_t* out) {
+    if (!B || !out) { md_set_error("md_batch_stats: NULL argument"); return MD_ERR_ARG; }
+    *out = B->stats;
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_reset_stats(md_batch* B) {
+    if (!B) { md_set_error("md_batch_reset_stats: NULL batch"); return MD_ERR_ARG; }
+    B->stats = md_batch_stats_t{};
+    return MD_OK;
 }
 
 extern "C" md_status md_batch_times(const md_batch* B, double* seconds) {
