@@ -301,12 +301,12 @@ md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvO
     MD_TRY((launch_conv<1, 32, false>(w->x0, w->off_x0, w->a, w->off_ab, W + c->w_off[0], B + c->b_off[0], w, io, 0, s)));
     __nv_bfloat16* src = w->a;
     __nv_bfloat16* dst = w->b;
-    if (e_hidden0) cudaEventRecord(e_hidden0, s);
+    if (e_hidden0) cudaEventRecordWithFlags(e_hidden0, s, cudaEventRecordExternal);
     for (int l = 1; l <= 4; ++l) {
         MD_TRY((launch_conv<4, 32, false>(src, w->off_ab, dst, w->off_ab, W + c->w_off[l], B + c->b_off[l], w, io, 0, s)));
         std::swap(src, dst);
     }
-    if (e_hidden1) cudaEventRecord(e_hidden1, s);
+    if (e_hidden1) cudaEventRecordWithFlags(e_hidden1, s, cudaEventRecordExternal);
     MD_TRY((launch_conv<4, 1, true>(src, w->off_ab, nullptr, nullptr, W + c->w_off[5], B + c->b_off[5], w, io, (int)last, s)));
     return MD_OK;
 }

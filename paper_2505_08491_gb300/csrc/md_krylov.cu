@@ -70,8 +70,10 @@ static cudaEvent_t ev_restart(md_batch* B, int which) {
     if (!B->profiling) return nullptr;
     return B->ev[(size_t)B->k * EV_PER_J + which];
 }
+// Inside stream capture an event must be recorded as an external event node
+// to be readable after the graph runs.
 static void rec(cudaEvent_t e, cudaStream_t s) {
-    if (e) cudaEventRecord(e, s);
+    if (e) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
 }
 
 // ---------------------------------------------------------------------------
@@ -667,7 +669,11 @@ static void accumulate_events(md_batch* B) {
     if (!B->profiling || B->solver == MD_SOLVER_CG_JACOBI) return;
     auto el = [](cudaEvent_t a, cudaEvent_t b) {
         float ms = 0.f;
-        return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : 0.0;
+        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+            (void)cudaGetLastError();  // a failed read must not surface as a later launch error
+            return 0.0;
+        }
+        return (double)ms;
     };
     for (int j = 0; j < B->k; ++j) {
         B->stats.prec_ms += el(ev_at(B, j, EV_PRE0), ev_at(B, j, EV_APPLY0));
