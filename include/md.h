@@ -132,6 +132,11 @@ md_status md_apply(const md_op* op, md_prec prec, const void* u, void* y, md_str
 #define MD_CNN_LAYERS 6
 #define MD_CNN_NPARAMS 114209
 md_status md_cnn_create(const float* host_params, long long n_params, md_cnn** out);
+/* Engine of the convolutions: 0 = 5th-gen tensor cores (tcgen05 implicit
+ * GEMM, the default), 1 = CUDA cores (same arithmetic: BF16 operands, FP32
+ * accumulation; kept as the cross-check of the tensor-core path).
+ * Takes effect at the next launch that builds its work (a new md_batch). */
+md_status md_cnn_set_engine(md_cnn* c, int engine);
 md_status md_cnn_get_params(const md_cnn* c, float* host_params, long long n_params);
 void md_cnn_destroy(md_cnn* c);
 /* File: magic "MDCNN001", int64 count, count FP32 values, uint64 FNV-1a

@@ -61,6 +61,7 @@ SIGNATURES = {
     "md_apply": (st, [vp, i32, vp, vp, vp]),
     "md_cnn_create": (st, [C.POINTER(C.c_float), i64, C.POINTER(vp)]),
     "md_cnn_get_params": (st, [vp, C.POINTER(C.c_float), i64]),
+    "md_cnn_set_engine": (st, [vp, i32]),
     "md_cnn_destroy": (None, [vp]),
     "md_cnn_save": (st, [vp, C.c_char_p]),
     "md_cnn_load": (st, [C.c_char_p, C.POINTER(vp)]),

@@ -140,6 +140,11 @@ class Network:
     def handle(self):
         return self._h
 
+    def set_engine(self, engine: str):
+        """'tensor' (tcgen05, default) or 'cuda_cores' (the cross-check path)."""
+        code = {"tensor": 0, "cuda_cores": 1}[engine]
+        L.check(L.load().md_cnn_set_engine(self._h, code), "md_cnn_set_engine")
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             L.load().md_cnn_destroy(self._h)

@@ -12,6 +12,7 @@
 
 #include "md_cnn.h"
 #include "md_common.cuh"
+#include "md_conv_tc.h"
 
 namespace {
 const int kCin[MD_CNN_LAYERS] = {3, 32, 32, 32, 32, 32};
@@ -52,11 +53,28 @@ static md_status cnn_upload(md_cnn* c) {
     }
     c->w_off[MD_CNN_LAYERS] = w.size();
     c->b_off[MD_CNN_LAYERS] = b.size();
+    // tensor-core operand images: first layer kind 1, hidden kind 0, last kind 2
+    std::vector<__nv_bfloat16> img, all;
+    for (int l = 0; l < MD_CNN_LAYERS; ++l) {
+        const int kind = l == 0 ? 1 : (l == MD_CNN_LAYERS - 1 ? 2 : 0);
+        tc_weight_image(kind, c->host.data() + host_w_off(l), kCin[l], kCout[l], img);
+        c->wmma_off[l] = all.size();
+        all.insert(all.end(), img.begin(), img.end());
+    }
+    c->wmma_off[MD_CNN_LAYERS] = all.size();
     std::vector<void*> tmp;
     if (c->w) { cudaFree(c->w); c->w = nullptr; }
     if (c->b) { cudaFree(c->b); c->b = nullptr; }
+    if (c->wmma) { cudaFree(c->wmma); c->wmma = nullptr; }
     MD_TRY(dev_upload(&tmp, &c->w, w.data(), w.size()));
     MD_TRY(dev_upload(&tmp, &c->b, b.data(), b.size()));
+    MD_TRY(dev_upload(&tmp, &c->wmma, all.data(), all.size()));
+    return MD_OK;
+}
+
+extern "C" md_status md_cnn_set_engine(md_cnn* c, int engine) {
+    if (!c || (engine != 0 && engine != 1)) { md_set_error("md_cnn_set_engine: bad argument"); return MD_ERR_ARG; }
+    c->engine = engine;
     return MD_OK;
 }
 
@@ -150,12 +168,18 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     CnnWork* w = new CnnWork();
     w->ninst = (int)Ns.size();
     w->hN = Ns;
-    long long rx = 0, rab = 0, nodes = 0;
+    long long rx = CNN_MARGIN_ROWS, rab = CNN_MARGIN_ROWS, nodes = 0;
     std::vector<Seg> segs;
     std::vector<InstRange> ranges;
+    std::vector<TcItem> items;
+    int pd_max = 0;
+    for (int n : Ns) pd_max = std::max(pd_max, n + 3);
+    w->tps = tc_smem_bytes(0, tc_window_rows(2, pd_max)) <= 227 * 1024 ? 2 : 1;
+    w->W = tc_window_rows(w->tps, pd_max);
     const int CH = 512;
     for (int i = 0; i < w->ninst; ++i) {
         long long Pd = Ns[i] + 3, P = Pd * Pd * Pd;
+        if (Pd + 1 + 256 + 8 > CNN_MARGIN_ROWS) { delete w; md_set_error("grid too large for the network workspace"); return MD_ERR_ARG; }
         w->h_off_x0.push_back(rx * 8);
         w->h_off_ab.push_back(rab * 8);
         rx += P;
@@ -165,11 +189,24 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
         ranges.push_back({(int)segs.size(), 0});
         for (int b = 0; b < n3; b += CH) segs.push_back({i, 0, b, std::min(n3, b + CH)});
         ranges.back().count = (int)segs.size() - ranges.back().first;
+        // rows of the planes that hold grid nodes: [Pd^2, (N+2) Pd^2)
+        for (long long p = Pd * Pd; p < (Ns[i] + 2) * Pd * Pd; p += 128 * w->tps) items.push_back({i, (int)p});
     }
+    rx += CNN_MARGIN_ROWS;
+    rab += CNN_MARGIN_ROWS;
     w->total_nodes = nodes;
+    w->nitems = (int)items.size();
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            w->nsm = nsm;
+    }
     md_status st = MD_OK;
     auto chk = [&](md_status s) { if (st == MD_OK) st = s; };
+    chk(tc_prepare(w->W, w->tps));
     chk(dev_upload(&w->allocs, &w->N, Ns.data(), Ns.size()));
+    chk(dev_upload(&w->allocs, &w->items, items.data(), items.size()));
+    chk(dev_alloc(&w->allocs, &w->err, 1));
     chk(dev_upload(&w->allocs, &w->off_x0, w->h_off_x0.data(), w->h_off_x0.size()));
     chk(dev_upload(&w->allocs, &w->off_ab, w->h_off_ab.data(), w->h_off_ab.size()));
     chk(dev_alloc(&w->allocs, &w->x0, (size_t)rx * 8));
@@ -294,8 +331,40 @@ static md_status launch_conv(const __nv_bfloat16* in, const long long* in_off, _
     return MD_OK;
 }
 
+static md_status tc_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
+                                   cudaEvent_t e_hidden0, cudaEvent_t e_hidden1) {
+    const int grid = std::max(1, std::min(w->nitems, w->nsm));
+    TcArgs a{};
+    a.Ns = w->N;
+    a.items = w->items;
+    a.nitems = w->nitems;
+    a.W = w->W;
+    a.io = io;
+    a.mode = (int)last;
+    a.err = w->err;
+    // layer 0: x0 (one chunk) -> a
+    a.in = w->x0; a.in_off = w->off_x0; a.out = w->a; a.out_off = w->off_ab;
+    a.wimg = c->wmma + c->wmma_off[0]; a.bias = c->b + c->b_off[0]; a.cout = 32;
+    MD_TRY(tc_launch(1, w->tps, a, grid, s));
+    __nv_bfloat16* src = w->a;
+    __nv_bfloat16* dst = w->b;
+    if (e_hidden0) cudaEventRecordWithFlags(e_hidden0, s, cudaEventRecordExternal);
+    for (int l = 1; l <= 4; ++l) {
+        a.in = src; a.in_off = w->off_ab; a.out = dst; a.out_off = w->off_ab;
+        a.wimg = c->wmma + c->wmma_off[l]; a.bias = c->b + c->b_off[l]; a.cout = 32;
+        MD_TRY(tc_launch(0, w->tps, a, grid, s));
+        std::swap(src, dst);
+    }
+    if (e_hidden1) cudaEventRecordWithFlags(e_hidden1, s, cudaEventRecordExternal);
+    a.in = src; a.in_off = w->off_ab; a.out = nullptr; a.out_off = nullptr;
+    a.wimg = c->wmma + c->wmma_off[5]; a.bias = c->b + c->b_off[5]; a.cout = 1;
+    MD_TRY(tc_launch(2, w->tps, a, grid, s));
+    return MD_OK;
+}
+
 md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
                              cudaEvent_t e_hidden0, cudaEvent_t e_hidden1) {
+    if (c->engine == 0) return tc_forward_layers(c, w, io, last, s, e_hidden0, e_hidden1);
     const __nv_bfloat16* W = c->w;
     const float* B = c->b;
     MD_TRY((launch_conv<1, 32, false>(w->x0, w->off_x0, w->a, w->off_ab, W + c->w_off[0], B + c->b_off[0], w, io, 0, s)));
@@ -380,7 +449,10 @@ extern "C" md_status md_cnn_forward(const md_cnn* c, int n_nodes_edge, int batch
     if (st == MD_OK) st = cnn_pack_raw(w, X, (cudaStream_t)s);
     if (st == MD_OK) st = cnn_forward_layers(c, w, io, CONV_RAW, (cudaStream_t)s);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)s);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, w->err, sizeof(int), cudaMemcpyDeviceToHost);
     cnn_work_destroy(w);
     if (st == MD_OK && e != cudaSuccess) st = md_cuda_status(e, "md_cnn_forward", __FILE__, __LINE__);
+    if (st == MD_OK && err) { md_set_error("md_cnn_forward: a convolution timed out"); st = MD_ERR_TIMEOUT; }
     return st;
 }

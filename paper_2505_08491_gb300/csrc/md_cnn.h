@@ -6,12 +6,20 @@
 // Pd = N + 3, row p = (i+1) + Pd((j+1) + Pd(k+1)) for grid node (i,j,k);
 // channels in chunks of 8: element (chunk c, row p, lane l) at
 // (c * P + p) * 8 + l.  Halo rows are never written and stay zero, which is
-// the zero 'same' padding of every layer.
+// the zero 'same' padding of every layer.  Each buffer has a zero margin of
+// CNN_MARGIN_ROWS rows before the first and after the last instance, which
+// the tensor-core windows of halo-only tiles may read.
+#define CNN_MARGIN_ROWS 8192
+struct TcItem;
 struct CnnWork {
     int ninst = 0;
     std::vector<void*> allocs;
     std::vector<int> hN;
     int* N = nullptr;              // device, per instance
+    // tensor-core path: work items of tps*128 padded rows, window rows W
+    TcItem* items = nullptr;
+    int nitems = 0, tps = 2, W = 0, nsm = 148;
+    int* err = nullptr;            // set by a timed-out wait in a conv kernel
     __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
     __nv_bfloat16* a = nullptr;    // 4 chunks
     __nv_bfloat16* b = nullptr;    // 4 chunks

@@ -1,0 +1,430 @@
+// 3x3x3 'same' convolutions of the preconditioner network on the 5th-gen
+// tensor cores (tcgen05, sm_103a): implicit GEMM, BF16 operands, FP32
+// accumulators in tensor memory.
+//
+// GEMM view of one layer: D[M = grid rows][N = c_out] =
+//   sum over taps t and input chunks of A_t[rows][c_in] * W_t[c_in][c_out],
+// where A_t is the activation tensor shifted by the tap's row offset.
+//
+// Layout.  Activations live in a zero-haloed padded grid (Pd = N+3 per
+// axis, row p = x + Pd (y + Pd z)) with channels in chunks of 8 BF16
+// (16 bytes): element (chunk c, row p, lane l) at (c P + p) 8 + l.  Copied
+// to shared memory unchanged, any 8 consecutive rows of one chunk are a
+// 128-byte core matrix of the no-swizzle K-major operand layout, so the A
+// operand of every tap is the same tile with its start address moved by the
+// tap's row offset dx + Pd dy (+ a z-window for dz): no im2col, no re-layout.
+//
+// Pipeline (one CTA per SM, persistent over work items of TPS x 128 rows):
+//   warp 0      producer: for the three z-windows (dz = -1, 0, 1) and every
+//               chunk, one bulk async copy (TMA, cp.async.bulk) of the
+//               TPS*128 + 2(Pd+1) contiguous rows the taps read; stages are
+//               double-buffered on mbarriers with transaction counts;
+//   warp 1      one thread issues tcgen05.mma (M=128, N=32 (16 for the last
+//               layer), K=16) for 27 taps x 2 K-halves per tile into a
+//               double-buffered TMEM accumulator and commits to mbarriers;
+//   warps 2..5  epilogue: tcgen05.ld of their 32-lane quarter, bias, GELU,
+//               BF16 pack, 16-byte stores of the grid rows (halo rows of
+//               the tile are computed but never stored, so zero padding is
+//               preserved).
+// The first layer (3 input channels in one 8-channel chunk) pairs two taps
+// per K=16 step (14 MMAs per tile); the last (1 output channel) runs N=16
+// with zero weights in the extra columns.
+//
+// Every mbarrier wait is bounded (2 s of globaltimer); on timeout the kernel
+// sets an error flag, waits (bounded) for its own work in flight, frees its
+// tensor memory and returns.
+#include <cstdio>
+
+#include "md_cnn.h"
+#include "md_common.cuh"
+#include "md_conv_tc.h"
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and the error flag set) after ~2 s.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*(volatile int*)err) return false;
+        if (globaltimer() - t0 > 2000000000ULL) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major:
+// start >> 4 [0,14), LBO >> 4 [16,30) (next 16-byte chunk along K),
+// SBO >> 4 [32,46) (next 8-row group along M/N), version 1 at bit 46,
+// layout type 0 (no swizzle) in [61,64).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ULL << 46);
+}
+
+// Instruction descriptor of kind::f16: D F32 (bit 4), A BF16 (bits 7-9 = 1),
+// B BF16 (bits 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int NC>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NC]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ inline float gelu_exact(float x) { return x * normcdff(x); }
+
+__device__ inline uint4 pack8(const float* v) {
+    uint4 r;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&r);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    return r;
+}
+
+}  // namespace
+
+// KIND 0: hidden 32 -> 32; KIND 1: first 3(8) -> 32 with paired taps;
+// KIND 2: last 32 -> 1 (N = 16).
+template <int KIND, int TPS>
+__global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
+    constexpr int CIN8 = (KIND == 1) ? 1 : 4;
+    constexpr int NCOL = (KIND == 2) ? 16 : 32;
+    constexpr int WIMG = tc_wimg_bytes(KIND);
+    constexpr uint32_t IDESC = idesc_bf16(128, NCOL);
+    constexpr int TMEM_COLS = 128;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int W = a.W;
+    unsigned char* wsm = sm;
+    unsigned char* stg = sm + tc_align(WIMG);
+    const int stage_bytes = 3 * CIN8 * W * 16;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 2 * stage_bytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + 2;
+    uint64_t* tfull = bars + 4;
+    uint64_t* tempty = bars + 6;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int i = threadIdx.x; i < WIMG / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(a.wimg)[i];
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------- producer
+        if (lane == 0) {
+            int it = 0;
+            for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+                const TcItem w = a.items[item];
+                if (a.io.st && !a.io.st[w.inst].active) continue;
+                const int s = it & 1, r = it >> 1;
+                if (!mbar_wait(&empty[s], (r & 1) ^ 1, a.err)) break;
+                const long long Pd = a.Ns[w.inst] + 3, P = Pd * Pd * Pd;
+                // rows the taps read, plus 8 so the first layer's zero-weight
+                // dummy tap (one row further) reads copied, finite data
+                const int wl = TPS * 128 + 2 * (int)(Pd + 1) + 8;
+                mbar_arrive_expect_tx(&full[s], (uint32_t)(3 * CIN8 * wl * 16));
+                const __nv_bfloat16* base = a.in + a.in_off[w.inst];
+                unsigned char* dst = stg + s * stage_bytes;
+                for (int dz = 0; dz < 3; ++dz)
+                    for (int c = 0; c < CIN8; ++c) {
+                        const long long row = (long long)c * P + w.p0 + (long long)(dz - 1) * Pd * Pd - (Pd + 1);
+                        bulk_g2s(dst + (size_t)(dz * CIN8 + c) * W * 16, base + row * 8, (uint32_t)(wl * 16), &full[s]);
+                    }
+                ++it;
+            }
+            // copies still in flight complete before the CTA leaves
+            for (int k = (it >= 2 ? it - 2 : 0); k < it; ++k) mbar_wait(&full[k & 1], (k >> 1) & 1, a.err);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int it = 0;
+            const uint32_t wbase = smem_u32(wsm);
+            for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+                const TcItem w = a.items[item];
+                if (a.io.st && !a.io.st[w.inst].active) continue;
+                const int s = it & 1, r = it >> 1;
+                if (!mbar_wait(&full[s], r & 1, a.err)) break;
+                if (!mbar_wait(&tempty[s], (r & 1) ^ 1, a.err)) break;
+                tc_fence_after();
+                const int Pd = a.Ns[w.inst] + 3;
+                const uint32_t sbase = smem_u32(stg + s * stage_bytes);
+                const uint32_t region = (uint32_t)W * 16;  // bytes per (dz, chunk) region
+#pragma unroll 1
+                for (int u = 0; u < TPS; ++u) {
+                    const uint32_t d = tmem + (uint32_t)((s * TPS + u) * NCOL);
+                    if (KIND == 1) {
+                        // 27 taps of one 8-channel chunk, two per K=16 step
+#pragma unroll 1
+                        for (int pr = 0; pr < 14; ++pr) {
+                            const int t1 = 2 * pr, t2 = 2 * pr + 1;
+                            const int dz1 = t1 / 9, dy1 = (t1 / 3) % 3 - 1, dx1 = t1 % 3 - 1;
+                            const uint32_t a1 = sbase + dz1 * region + (uint32_t)(Pd + 1 + u * 128 + dy1 * Pd + dx1) * 16;
+                            uint32_t a2;
+                            if (t2 < 27) {
+                                const int dz2 = t2 / 9, dy2 = (t2 / 3) % 3 - 1, dx2 = t2 % 3 - 1;
+                                a2 = sbase + dz2 * region + (uint32_t)(Pd + 1 + u * 128 + dy2 * Pd + dx2) * 16;
+                            } else {
+                                a2 = a1 + 16;  // zero weights: any finite rows
+                            }
+                            const uint64_t ad = sdesc(a1, a2 - a1, 128);
+                            const uint64_t bd = sdesc(wbase + pr * 1024, 512, 128);
+                            mma_bf16(d, ad, bd, IDESC, pr > 0 ? 1u : 0u);
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int t = 0; t < 27; ++t) {
+                            const int dz = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                            const uint32_t arow = (uint32_t)(Pd + 1 + u * 128 + dy * Pd + dx) * 16;
+#pragma unroll
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const uint64_t ad = sdesc(sbase + (dz * 4 + 2 * hh) * region + arow, region, 128);
+                                const uint64_t bd = sdesc(wbase + (t * 4 + 2 * hh) * NCOL * 16, NCOL * 16, 128);
+                                mma_bf16(d, ad, bd, IDESC, (t > 0 || hh > 0) ? 1u : 0u);
+                            }
+                        }
+                    }
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&tfull[s]);
+                ++it;
+            }
+            // MMAs in flight complete before the tensor memory is freed
+            if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+        const int q = warp & 3;
+        float bias[NCOL];
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c) bias[c] = (c < a.cout) ? a.bias[c] : 0.f;
+        int it = 0;
+        for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+            const TcItem w = a.items[item];
+            if (a.io.st && !a.io.st[w.inst].active) continue;
+            const int s = it & 1, r = it >> 1;
+            if (!mbar_wait(&tfull[s], r & 1, a.err)) break;
+            tc_fence_after();
+            const int N = a.Ns[w.inst], M = N + 1;
+            const long long Pd = N + 3, P = Pd * Pd * Pd;
+#pragma unroll 1
+            for (int u = 0; u < TPS; ++u) {
+                float v[NCOL];
+                tmem_ld<NCOL>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * TPS + u) * NCOL), v);
+                const long long p = (long long)w.p0 + u * 128 + q * 32 + lane;
+                const int xp = (int)(p % Pd), yp = (int)((p / Pd) % Pd), zp = (int)(p / (Pd * Pd));
+                const bool valid = xp >= 1 && xp <= M && yp >= 1 && yp <= M && zp >= 1 && zp <= M;
+                if (!valid) continue;
+                if (KIND != 2) {
+                    __nv_bfloat16* o = a.out + a.out_off[w.inst];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        float g[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) g[e] = gelu_exact(v[c * 8 + e] + bias[c * 8 + e]);
+                        *reinterpret_cast<uint4*>(o + ((long long)c * P + p) * 8) = pack8(g);
+                    }
+                } else {
+                    const int i = xp - 1, j = yp - 1, k = zp - 1;
+                    const int n = i + M * (j + M * k);
+                    const float y = v[0] + bias[0];
+                    float* o = a.io.out + a.io.off[w.inst];
+                    if (a.mode == CONV_PREC) {
+                        const bool bd = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
+                        const float scale = (float)(a.io.st[w.inst].s / a.io.D[w.inst].alpha);
+                        o[n] = bd ? a.io.vin[a.io.vin_off[w.inst] + n] : scale * y;
+                    } else {
+                        o[n] = y;
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[s]);
+            ++it;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+int tc_smem_bytes(int kind, int W) {
+    const int cin8 = kind == 1 ? 1 : 4;
+    return tc_align(tc_wimg_bytes(kind)) + 2 * 3 * cin8 * W * 16 + 8 * 8 + 16;
+}
+
+template <int KIND, int TPS>
+static md_status launch_one(const TcArgs& a, int grid, cudaStream_t s) {
+    const int smem = tc_smem_bytes(KIND, a.W);
+    k_conv_tc<KIND, TPS><<<grid, 192, smem, s>>>(a);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+// Largest window region (rows) per stage size TPS for grids of padded edge Pd.
+int tc_window_rows(int tps, int pd_max) { return (tps * 128 + 2 * (pd_max + 1) + 8 + 7) & ~7; }
+
+// Kernel attributes are set once per window size, outside stream capture.
+md_status tc_prepare(int W, int tps) {
+    static int done[3] = {-1, -1, -1};
+    if (done[tps] == W) return MD_OK;
+    const int s0 = tc_smem_bytes(0, W), s1 = tc_smem_bytes(1, W), s2 = tc_smem_bytes(2, W);
+    if (s0 > 227 * 1024) { md_set_error("conv tile window too large for shared memory"); return MD_ERR_ARG; }
+    if (tps == 2) {
+        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
+        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
+    } else {
+        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
+        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
+        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
+    }
+    done[tps] = W;
+    return MD_OK;
+}
+
+md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s) {
+    if (tps == 2) {
+        if (kind == 0) return launch_one<0, 2>(a, grid, s);
+        if (kind == 1) return launch_one<1, 2>(a, grid, s);
+        return launch_one<2, 2>(a, grid, s);
+    }
+    if (kind == 0) return launch_one<0, 1>(a, grid, s);
+    if (kind == 1) return launch_one<1, 1>(a, grid, s);
+    return launch_one<2, 1>(a, grid, s);
+}
+
+// Weight images in the operand layout the MMAs read:
+//   kind 0: [tap 27][k-chunk 4][n 32][8]
+//   kind 1: [pair 14][k-chunk 2 (= the pair's two taps)][n 32][8]
+//   kind 2: [tap 27][k-chunk 4][n 16][8], columns 1..15 zero
+void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img) {
+    const int ncol = kind == 2 ? 16 : 32;
+    img.assign(tc_wimg_bytes(kind) / 2, __float2bfloat16_rn(0.0f));
+    auto w_at = [&](int co, int ci, int tap) -> float {
+        if (co >= cout || ci >= cin) return 0.0f;
+        return W[((size_t)co * cin + ci) * 27 + tap];
+    };
+    if (kind == 1) {
+        for (int pr = 0; pr < 14; ++pr)
+            for (int half = 0; half < 2; ++half) {
+                const int tap = 2 * pr + half;
+                for (int n = 0; n < 32; ++n)
+                    for (int l = 0; l < 8; ++l)
+                        img[((size_t)(pr * 2 + half) * 32 + n) * 8 + l] =
+                            __float2bfloat16_rn(tap < 27 ? w_at(n, l, tap) : 0.0f);
+            }
+    } else {
+        for (int tap = 0; tap < 27; ++tap)
+            for (int kc = 0; kc < 4; ++kc)
+                for (int n = 0; n < ncol; ++n)
+                    for (int l = 0; l < 8; ++l)
+                        img[((size_t)(tap * 4 + kc) * ncol + n) * 8 + l] = __float2bfloat16_rn(w_at(n, kc * 8 + l, tap));
+    }
+}

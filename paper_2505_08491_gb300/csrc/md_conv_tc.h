@@ -1,0 +1,38 @@
+// Tensor-core (tcgen05) convolution launches (internal).
+#pragma once
+#include <vector>
+
+#include "md_cnn.h"
+
+// One work item: TPS * 128 consecutive padded rows of one instance
+// (TPS = 128-row tiles per pipeline stage, 2, or 1 when the window of a
+// large grid would not fit shared memory twice).
+struct TcItem { int inst, p0; };
+
+struct TcArgs {
+    const __nv_bfloat16* in;     // activation buffer (chunk-major padded layout)
+    const long long* in_off;     // per instance element offset
+    __nv_bfloat16* out;          // next activation buffer (hidden layers)
+    const long long* out_off;
+    const int* Ns;               // per instance grid size N
+    const TcItem* items;
+    int nitems;
+    int W;                       // rows per (dz, chunk) window region in shared memory
+    const __nv_bfloat16* wimg;   // weight image in operand layout
+    const float* bias;
+    int cout;                    // real output channels
+    OutIO io;                    // last layer output / instance gating
+    int mode;                    // ConvOut of the last layer
+    int* err;                    // set on a timed-out wait
+};
+
+__host__ __device__ constexpr int tc_wimg_bytes(int kind) {
+    return kind == 1 ? 14 * 2 * 32 * 16 : 27 * 4 * (kind == 2 ? 16 : 32) * 16;
+}
+__host__ __device__ constexpr int tc_align(int b) { return (b + 1023) & ~1023; }
+
+int tc_smem_bytes(int kind, int W);
+int tc_window_rows(int tps, int pd_max);
+md_status tc_prepare(int W, int tps);
+md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s);
+void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img);

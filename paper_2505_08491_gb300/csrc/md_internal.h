@@ -108,9 +108,10 @@ struct md_cnn {
     float* b = nullptr;          // device biases, per layer [cout]
     size_t w_off[MD_CNN_LAYERS + 1];
     size_t b_off[MD_CNN_LAYERS + 1];
-    // tcgen05 operand images of the weights (see md_conv)
+    // tcgen05 operand images of the weights (md_conv_tc.cu)
     __nv_bfloat16* wmma = nullptr;
     size_t wmma_off[MD_CNN_LAYERS + 1];
+    int engine = 0;              // 0: tensor cores (tcgen05), 1: CUDA cores
 };
 
 // Per-instance Krylov state (device).

@@ -52,6 +52,7 @@ struct md_batch {
     cudaGraphExec_t graph = nullptr;
     const md_cnn* graph_cnn = nullptr;
     bool graph_prof = false;
+    int graph_engine = -1;
     long long graph_kernels = 0;
     std::vector<double> last_times;
     // instrumentation
@@ -636,7 +637,8 @@ static md_status launch_cycle_cg(md_batch* B, cudaStream_t s) {
 }
 
 static md_status build_graph(md_batch* B) {
-    if (B->graph && B->graph_cnn == B->cnn && B->graph_prof == B->profiling) return MD_OK;
+    const int engine = B->cnn ? B->cnn->engine : 0;
+    if (B->graph && B->graph_cnn == B->cnn && B->graph_prof == B->profiling && B->graph_engine == engine) return MD_OK;
     if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
     if (B->profiling && B->ev.empty()) {
         B->ev.resize((size_t)B->k * EV_PER_J + 2);
@@ -662,6 +664,7 @@ static md_status build_graph(md_batch* B) {
     MD_CUDA(e);
     B->graph_cnn = B->cnn;
     B->graph_prof = B->profiling;
+    B->graph_engine = engine;
     return MD_OK;
 }
 
@@ -801,6 +804,11 @@ static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
         MD_CUDA(cudaGraphLaunch(B->graph, s));
         B->stats.cycles += 1;
         B->stats.kernel_launches += B->graph_kernels;
+    }
+    if (B->cw) {
+        int err = 0;
+        MD_CUDA(cudaMemcpy(&err, B->cw->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) { md_set_error("a network convolution timed out waiting on its pipeline"); return MD_ERR_TIMEOUT; }
     }
     if (ndone < B->ninst) { md_set_error("batch solve did not terminate"); return MD_ERR_TIMEOUT; }
     return MD_OK;

@@ -1,0 +1,58 @@
+"""The tensor-core (tcgen05) convolutions against the CUDA-core path and the
+oracle: same BF16 operands and FP32 accumulation, so both engines agree to
+accumulation-order rounding, and both match the oracle's BF16 emulation."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import rel_l2
+from oracle import cnn
+
+pytestmark = pytest.mark.gpu
+
+
+def _net(seed, engine):
+    from paper_2505_08491_gb300 import Network
+    from paper_2505_08491_gb300.weights import random_params
+    flat = random_params(seed)
+    net = Network(flat)
+    net.set_engine(engine)
+    return net, flat
+
+
+@pytest.mark.parametrize("n,batch", [(5, 1), (9, 2), (17, 1), (33, 2)])
+def test_tensor_engine_matches_cuda_cores_and_oracle(n, batch):
+    from paper_2505_08491_gb300.weights import flat_to_layers
+    t_net, flat = _net(21, "tensor")
+    c_net, _ = _net(21, "cuda_cores")
+    X = np.random.default_rng(n).standard_normal((batch, 3, n, n, n)).astype(np.float32)
+    Xt = torch.from_numpy(X).cuda()
+    Yt = t_net.forward(Xt).cpu().numpy()
+    Yc = c_net.forward(Xt).cpu().numpy()
+    assert np.all(np.isfinite(Yt))
+    assert rel_l2(Yt, Yc) <= 2e-3
+    layers = [(cnn.round_bf16(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in flat_to_layers(flat)]
+    for s in range(batch):
+        ref = cnn.forward(X[s].astype(np.float64), layers, bf16=True)
+        assert rel_l2(Yt[s], ref) <= 2e-3
+
+
+def test_tensor_engine_single_tap_kernels():
+    """A network with one non-zero tap per layer (an exact shift chain):
+    every tap position is exercised in turn against the oracle."""
+    from paper_2505_08491_gb300 import Network
+    from paper_2505_08491_gb300.weights import layers_to_flat
+    rng = np.random.default_rng(3)
+    n = 11
+    X = rng.standard_normal((1, 3, n, n, n)).astype(np.float32)
+    for tap in (0, 4, 13, 17, 26):
+        kz, ky, kx = tap // 9, (tap // 3) % 3, tap % 3
+        layers = []
+        for ci, co in zip(cnn.CHANNELS[:-1], cnn.CHANNELS[1:]):
+            W = np.zeros((co, ci, 3, 3, 3))
+            W[:, :, kz, ky, kx] = cnn.round_bf16(rng.standard_normal((co, ci)) * 0.3)
+            layers.append((W, np.zeros(co)))
+        net = Network(layers_to_flat(layers))
+        Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()[0]
+        ref = cnn.forward(X[0].astype(np.float64), layers, bf16=True)
+        assert rel_l2(Y, ref) <= 2e-3, tap
