@@ -171,11 +171,13 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     long long rx = CNN_MARGIN_ROWS, rab = CNN_MARGIN_ROWS, nodes = 0;
     std::vector<Seg> segs;
     std::vector<InstRange> ranges;
-    std::vector<TcItem> items;
+    std::vector<TcUnit> units;
     int pd_max = 0;
     for (int n : Ns) pd_max = std::max(pd_max, n + 3);
-    w->tps = tc_smem_bytes(0, tc_window_rows(2, pd_max)) <= 227 * 1024 ? 2 : 1;
+    w->tps = 2;
     w->W = tc_window_rows(w->tps, pd_max);
+    w->NS = tc_ring_slots(w->W);
+    if (w->NS == 0) { delete w; md_set_error("grid too large for the tensor-core convolution windows"); return MD_ERR_ARG; }
     const int CH = 512;
     for (int i = 0; i < w->ninst; ++i) {
         long long Pd = Ns[i] + 3, P = Pd * Pd * Pd;
@@ -189,13 +191,19 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
         ranges.push_back({(int)segs.size(), 0});
         for (int b = 0; b < n3; b += CH) segs.push_back({i, 0, b, std::min(n3, b + CH)});
         ranges.back().count = (int)segs.size() - ranges.back().first;
-        // rows of the planes that hold grid nodes: [Pd^2, (N+2) Pd^2)
-        for (long long p = Pd * Pd; p < (Ns[i] + 2) * Pd * Pd; p += 128 * w->tps) items.push_back({i, (int)p});
+        // columns of tps*128 in-plane rows, walked over the planes holding grid
+        // nodes (padded z in [1, N+2)) in chunks of at most 17 planes
+        const int nz = Ns[i] + 1, nch = (nz + 16) / 17;
+        for (long long s0 = 0; s0 < Pd * Pd; s0 += 128 * w->tps)
+            for (int c = 0; c < nch; ++c) {
+                const int z0 = 1 + (int)((long long)nz * c / nch), z1 = 1 + (int)((long long)nz * (c + 1) / nch);
+                units.push_back({i, (int)s0, z0, z1});
+            }
     }
     rx += CNN_MARGIN_ROWS;
     rab += CNN_MARGIN_ROWS;
     w->total_nodes = nodes;
-    w->nitems = (int)items.size();
+    w->nunits = (int)units.size();
     {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
@@ -205,7 +213,7 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     auto chk = [&](md_status s) { if (st == MD_OK) st = s; };
     chk(tc_prepare(w->W, w->tps));
     chk(dev_upload(&w->allocs, &w->N, Ns.data(), Ns.size()));
-    chk(dev_upload(&w->allocs, &w->items, items.data(), items.size()));
+    chk(dev_upload(&w->allocs, &w->units, units.data(), units.size()));
     chk(dev_alloc(&w->allocs, &w->err, 1));
     chk(dev_upload(&w->allocs, &w->off_x0, w->h_off_x0.data(), w->h_off_x0.size()));
     chk(dev_upload(&w->allocs, &w->off_ab, w->h_off_ab.data(), w->h_off_ab.size()));
@@ -333,12 +341,13 @@ static md_status launch_conv(const __nv_bfloat16* in, const long long* in_off, _
 
 static md_status tc_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
                                    cudaEvent_t e_hidden0, cudaEvent_t e_hidden1) {
-    const int grid = std::max(1, std::min(w->nitems, w->nsm));
+    const int grid = std::max(1, std::min(w->nunits, w->nsm));
     TcArgs a{};
     a.Ns = w->N;
-    a.items = w->items;
-    a.nitems = w->nitems;
+    a.units = w->units;
+    a.nunits = w->nunits;
     a.W = w->W;
+    a.NS = w->NS;
     a.io = io;
     a.mode = (int)last;
     a.err = w->err;

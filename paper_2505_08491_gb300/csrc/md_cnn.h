@@ -10,15 +10,16 @@
 // CNN_MARGIN_ROWS rows before the first and after the last instance, which
 // the tensor-core windows of halo-only tiles may read.
 #define CNN_MARGIN_ROWS 8192
-struct TcItem;
+struct TcUnit;
 struct CnnWork {
     int ninst = 0;
     std::vector<void*> allocs;
     std::vector<int> hN;
     int* N = nullptr;              // device, per instance
-    // tensor-core path: work items of tps*128 padded rows, window rows W
-    TcItem* items = nullptr;
-    int nitems = 0, tps = 2, W = 0, nsm = 148;
+    // tensor-core path: z-walking work units of tps*128 in-plane rows,
+    // window rows W, NS ring slots
+    TcUnit* units = nullptr;
+    int nunits = 0, tps = 2, W = 0, NS = 0, nsm = 148;
     int* err = nullptr;            // set by a timed-out wait in a conv kernel
     __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
     __nv_bfloat16* a = nullptr;    // 4 chunks

@@ -14,21 +14,26 @@
 // operand of every tap is the same tile with its start address moved by the
 // tap's row offset dx + Pd dy (+ a z-window for dz): no im2col, no re-layout.
 //
-// Pipeline (one CTA per SM, persistent over work items of TPS x 128 rows):
-//   warp 0      producer: for the three z-windows (dz = -1, 0, 1) and every
-//               chunk, one bulk async copy (TMA, cp.async.bulk) of the
-//               TPS*128 + 2(Pd+1) contiguous rows the taps read; stages are
-//               double-buffered on mbarriers with transaction counts;
+// Pipeline (one CTA per SM, persistent over work units; a unit is a column
+// of TPS x 128 in-plane rows walked along z, so the window copied for plane
+// z serves planes z-1, z and z+1):
+//   warp 0      producer: per plane window and chunk one bulk async copy
+//               (TMA, cp.async.bulk) of the TPS*128 + 2(Pd+1) + 8 contiguous
+//               rows the taps read, into a ring of NS shared-memory slots,
+//               completion counted on mbarriers (transaction bytes);
 //   warp 1      one thread issues tcgen05.mma (M=128, N=32 (16 for the last
-//               layer), K=16) for 27 taps x 2 K-halves per tile into a
-//               double-buffered TMEM accumulator and commits to mbarriers;
+//               layer), K=16): 27 taps x 2 K-halves per tile, fully unrolled
+//               from per-unit row offsets, into a double-buffered TMEM
+//               accumulator; commits free the accumulator for the epilogue
+//               and the oldest window for the producer;
 //   warps 2..5  epilogue: tcgen05.ld of their 32-lane quarter, bias, GELU,
-//               BF16 pack, 16-byte stores of the grid rows (halo rows of
-//               the tile are computed but never stored, so zero padding is
-//               preserved).
+//               BF16 pack, 16-byte stores of the grid rows of the plane
+//               (halo rows are computed but never stored, so the zero padding
+//               is preserved).
 // The first layer (3 input channels in one 8-channel chunk) pairs two taps
-// per K=16 step (14 MMAs per tile); the last (1 output channel) runs N=16
-// with zero weights in the extra columns.
+// of one z-window per K=16 step (5 MMAs per window, the ninth tap with a
+// zero-weight partner); the last (1 output channel) runs N=16 with zero
+// weights in the extra columns.
 //
 // Every mbarrier wait is bounded (2 s of globaltimer); on timeout the kernel
 // sets an error flag, waits (bounded) for its own work in flight, frees its
@@ -164,6 +169,12 @@ __device__ inline uint4 pack8(const float* v) {
 
 // KIND 0: hidden 32 -> 32; KIND 1: first 3(8) -> 32 with paired taps;
 // KIND 2: last 32 -> 1 (N = 16).
+//
+// A work unit is a column of TPS*128 in-plane rows starting at s0, walked
+// over planes z in [z0, z1).  Window w holds, for plane w, the rows
+// [w Pd^2 + s0 - (Pd+1), + TPS*128 + 2(Pd+1) + 8) of every input chunk; plane
+// z reads windows z-1, z, z+1, so each copied window serves three planes.
+// Windows go round a ring of NS shared-memory slots.
 template <int KIND, int TPS>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
     constexpr int CIN8 = (KIND == 1) ? 1 : 4;
@@ -172,24 +183,26 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
     constexpr uint32_t IDESC = idesc_bf16(128, NCOL);
     constexpr int TMEM_COLS = 128;
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int W = a.W;
+    const int W = a.W, NS = a.NS;
+    const int slot_bytes = CIN8 * W * 16;
     unsigned char* wsm = sm;
-    unsigned char* stg = sm + tc_align(WIMG);
-    const int stage_bytes = 3 * CIN8 * W * 16;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stg + 2 * stage_bytes);
-    uint64_t* full = bars;
-    uint64_t* empty = bars + 2;
-    uint64_t* tfull = bars + 4;
-    uint64_t* tempty = bars + 6;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+    unsigned char* ring = sm + tc_align(WIMG);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)NS * slot_bytes);
+    uint64_t* full = bars;             // [NS]
+    uint64_t* empty = bars + NS;       // [NS]
+    uint64_t* tfull = bars + 2 * NS;   // [2]
+    uint64_t* tempty = bars + 2 * NS + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     for (int i = threadIdx.x; i < WIMG / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(a.wimg)[i];
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], 4);
         }
@@ -209,84 +222,100 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ---------------- producer
+        // ---------------- producer: one bulk copy per window and chunk
         if (lane == 0) {
-            int it = 0;
-            for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-                const TcItem w = a.items[item];
-                if (a.io.st && !a.io.st[w.inst].active) continue;
-                const int s = it & 1, r = it >> 1;
-                if (!mbar_wait(&empty[s], (r & 1) ^ 1, a.err)) break;
-                const long long Pd = a.Ns[w.inst] + 3, P = Pd * Pd * Pd;
-                // rows the taps read, plus 8 so the first layer's zero-weight
-                // dummy tap (one row further) reads copied, finite data
+            int g = 0;
+            bool ok = true;
+            for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
+                const TcUnit U = a.units[un];
+                if (a.io.st && !a.io.st[U.inst].active) continue;
+                const long long Pd = a.Ns[U.inst] + 3, P = Pd * Pd * Pd;
                 const int wl = TPS * 128 + 2 * (int)(Pd + 1) + 8;
-                mbar_arrive_expect_tx(&full[s], (uint32_t)(3 * CIN8 * wl * 16));
-                const __nv_bfloat16* base = a.in + a.in_off[w.inst];
-                unsigned char* dst = stg + s * stage_bytes;
-                for (int dz = 0; dz < 3; ++dz)
+                const __nv_bfloat16* base = a.in + a.in_off[U.inst];
+                for (int w = U.z0 - 1; w <= U.z1; ++w, ++g) {
+                    const int slot = g % NS, r = g / NS;
+                    if (!mbar_wait(&empty[slot], (r & 1) ^ 1, a.err)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&full[slot], (uint32_t)(CIN8 * wl * 16));
+                    unsigned char* dst = ring + (size_t)slot * slot_bytes;
                     for (int c = 0; c < CIN8; ++c) {
-                        const long long row = (long long)c * P + w.p0 + (long long)(dz - 1) * Pd * Pd - (Pd + 1);
-                        bulk_g2s(dst + (size_t)(dz * CIN8 + c) * W * 16, base + row * 8, (uint32_t)(wl * 16), &full[s]);
+                        const long long row = (long long)c * P + (long long)w * Pd * Pd + U.s0 - (Pd + 1);
+                        bulk_g2s(dst + (size_t)c * W * 16, base + row * 8, (uint32_t)(wl * 16), &full[slot]);
                     }
-                ++it;
+                }
             }
             // copies still in flight complete before the CTA leaves
-            for (int k = (it >= 2 ? it - 2 : 0); k < it; ++k) mbar_wait(&full[k & 1], (k >> 1) & 1, a.err);
+            for (int k = (g > NS ? g - NS : 0); k < g; ++k) mbar_wait(&full[k % NS], (k / NS) & 1, a.err);
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int it = 0;
-            const uint32_t wbase = smem_u32(wsm);
-            for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-                const TcItem w = a.items[item];
-                if (a.io.st && !a.io.st[w.inst].active) continue;
-                const int s = it & 1, r = it >> 1;
-                if (!mbar_wait(&full[s], r & 1, a.err)) break;
-                if (!mbar_wait(&tempty[s], (r & 1) ^ 1, a.err)) break;
-                tc_fence_after();
-                const int Pd = a.Ns[w.inst] + 3;
-                const uint32_t sbase = smem_u32(stg + s * stage_bytes);
-                const uint32_t region = (uint32_t)W * 16;  // bytes per (dz, chunk) region
-#pragma unroll 1
-                for (int u = 0; u < TPS; ++u) {
-                    const uint32_t d = tmem + (uint32_t)((s * TPS + u) * NCOL);
-                    if (KIND == 1) {
-                        // 27 taps of one 8-channel chunk, two per K=16 step
-#pragma unroll 1
-                        for (int pr = 0; pr < 14; ++pr) {
-                            const int t1 = 2 * pr, t2 = 2 * pr + 1;
-                            const int dz1 = t1 / 9, dy1 = (t1 / 3) % 3 - 1, dx1 = t1 % 3 - 1;
-                            const uint32_t a1 = sbase + dz1 * region + (uint32_t)(Pd + 1 + u * 128 + dy1 * Pd + dx1) * 16;
-                            uint32_t a2;
-                            if (t2 < 27) {
-                                const int dz2 = t2 / 9, dy2 = (t2 / 3) % 3 - 1, dx2 = t2 % 3 - 1;
-                                a2 = sbase + dz2 * region + (uint32_t)(Pd + 1 + u * 128 + dy2 * Pd + dx2) * 16;
-                            } else {
-                                a2 = a1 + 16;  // zero weights: any finite rows
-                            }
-                            const uint64_t ad = sdesc(a1, a2 - a1, 128);
-                            const uint64_t bd = sdesc(wbase + pr * 1024, 512, 128);
-                            mma_bf16(d, ad, bd, IDESC, pr > 0 ? 1u : 0u);
-                        }
-                    } else {
-#pragma unroll 1
-                        for (int t = 0; t < 27; ++t) {
-                            const int dz = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                            const uint32_t arow = (uint32_t)(Pd + 1 + u * 128 + dy * Pd + dx) * 16;
+            int g = 0, it = 0;
+            bool ok = true;
+            const uint32_t wb = smem_u32(wsm);
+            const uint32_t rb0 = smem_u32(ring);
+            const uint64_t a_hi = (1ULL << 46) | ((uint64_t)((128 >> 4) & 0x3FFF) << 32);  // version, SBO = 128
+            for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
+                const TcUnit U = a.units[un];
+                if (a.io.st && !a.io.st[U.inst].active) continue;
+                const int Pd = a.Ns[U.inst] + 3;
+                const int nwin = U.z1 - U.z0 + 2;
+                uint32_t rowoff[9];
 #pragma unroll
-                            for (int hh = 0; hh < 2; ++hh) {
-                                const uint64_t ad = sdesc(sbase + (dz * 4 + 2 * hh) * region + arow, region, 128);
-                                const uint64_t bd = sdesc(wbase + (t * 4 + 2 * hh) * NCOL * 16, NCOL * 16, 128);
-                                mma_bf16(d, ad, bd, IDESC, (t > 0 || hh > 0) ? 1u : 0u);
-                            }
+                for (int q9 = 0; q9 < 9; ++q9) rowoff[q9] = (uint32_t)(Pd + 1 + (q9 / 3 - 1) * Pd + (q9 % 3 - 1)) * 16;
+                for (int k = 0; k < nwin - 2 && ok; ++k) {
+                    // windows k, k+1, k+2 of this unit (planes z-1, z, z+1)
+                    const int g0 = g + k;
+                    if (k == 0) {
+                        if (!mbar_wait(&full[g0 % NS], (g0 / NS) & 1, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&full[(g0 + 1) % NS], ((g0 + 1) / NS) & 1, a.err)) { ok = false; break; }
+                    }
+                    if (!mbar_wait(&full[(g0 + 2) % NS], ((g0 + 2) / NS) & 1, a.err)) { ok = false; break; }
+                    const int bsel = it & 1;
+                    if (!mbar_wait(&tempty[bsel], ((it >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+                    tc_fence_after();
+                    uint32_t sb[3];
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) sb[dz] = rb0 + (uint32_t)(((g0 + dz) % NS) * slot_bytes);
+#pragma unroll
+                    for (int ut = 0; ut < TPS; ++ut) {
+                        const uint32_t d = tmem + (uint32_t)((bsel * TPS + ut) * NCOL);
+                        if (KIND == 1) {
+                            // per z-window: taps (0,1) (2,3) (4,5) (6,7) (8, zero-weight row + 1)
+#pragma unroll
+                            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                                for (int pr = 0; pr < 5; ++pr) {
+                                    const uint32_t a1 = sb[dz] + rowoff[2 * pr] + ut * 2048;
+                                    const uint32_t a2 = (pr < 4) ? sb[dz] + rowoff[2 * pr + 1] + ut * 2048 : a1 + 16;
+                                    const uint64_t ad = a_hi | ((uint64_t)(((a2 - a1) >> 4) & 0x3FFF) << 16) | ((a1 >> 4) & 0x3FFF);
+                                    const uint64_t bd = sdesc(wb + (uint32_t)((dz * 5 + pr) * 1024), 512, 128);
+                                    mma_bf16(d, ad, bd, IDESC, (dz > 0 || pr > 0) ? 1u : 0u);
+                                }
+                        } else {
+                            const uint64_t a_lbo = (uint64_t)(((W * 16) >> 4) & 0x3FFF) << 16;
+#pragma unroll
+                            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+                                for (int q9 = 0; q9 < 9; ++q9)
+#pragma unroll
+                                    for (int hh = 0; hh < 2; ++hh) {
+                                        const int t = dz * 9 + q9;
+                                        const uint32_t aa = sb[dz] + (uint32_t)(2 * hh * W * 16) + rowoff[q9] + ut * 2048;
+                                        const uint64_t ad = a_hi | a_lbo | ((aa >> 4) & 0x3FFF);
+                                        const uint64_t bd = sdesc(wb + (uint32_t)((t * 4 + 2 * hh) * NCOL * 16), NCOL * 16, 128);
+                                        mma_bf16(d, ad, bd, IDESC, (t > 0 || hh > 0) ? 1u : 0u);
+                                    }
                         }
                     }
+                    mma_commit(&tfull[bsel]);
+                    mma_commit(&empty[g0 % NS]);  // window k is not read by later planes
+                    if (k == nwin - 3) {
+                        mma_commit(&empty[(g0 + 1) % NS]);
+                        mma_commit(&empty[(g0 + 2) % NS]);
+                    }
+                    ++it;
                 }
-                mma_commit(&empty[s]);
-                mma_commit(&tfull[s]);
-                ++it;
+                g += nwin;
             }
             // MMAs in flight complete before the tensor memory is freed
             if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
@@ -298,49 +327,52 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
         for (int c = 0; c < NCOL; ++c) bias[c] = (c < a.cout) ? a.bias[c] : 0.f;
         int it = 0;
-        for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-            const TcItem w = a.items[item];
-            if (a.io.st && !a.io.st[w.inst].active) continue;
-            const int s = it & 1, r = it >> 1;
-            if (!mbar_wait(&tfull[s], r & 1, a.err)) break;
-            tc_fence_after();
-            const int N = a.Ns[w.inst], M = N + 1;
+        bool ok = true;
+        for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
+            const TcUnit U = a.units[un];
+            if (a.io.st && !a.io.st[U.inst].active) continue;
+            const int N = a.Ns[U.inst], M = N + 1;
             const long long Pd = N + 3, P = Pd * Pd * Pd;
+            for (int z = U.z0; z < U.z1; ++z, ++it) {
+                const int bsel = it & 1;
+                if (!mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err)) { ok = false; break; }
+                tc_fence_after();
 #pragma unroll 1
-            for (int u = 0; u < TPS; ++u) {
-                float v[NCOL];
-                tmem_ld<NCOL>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((s * TPS + u) * NCOL), v);
-                const long long p = (long long)w.p0 + u * 128 + q * 32 + lane;
-                const int xp = (int)(p % Pd), yp = (int)((p / Pd) % Pd), zp = (int)(p / (Pd * Pd));
-                const bool valid = xp >= 1 && xp <= M && yp >= 1 && yp <= M && zp >= 1 && zp <= M;
-                if (!valid) continue;
-                if (KIND != 2) {
-                    __nv_bfloat16* o = a.out + a.out_off[w.inst];
+                for (int ut = 0; ut < TPS; ++ut) {
+                    float v[NCOL];
+                    tmem_ld<NCOL>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL), v);
+                    const long long r = (long long)U.s0 + ut * 128 + q * 32 + lane;  // in-plane row
+                    if (r >= Pd * Pd) continue;
+                    const int xp = (int)(r % Pd), yp = (int)(r / Pd);
+                    if (xp < 1 || xp > M || yp < 1 || yp > M) continue;
+                    const long long p = (long long)z * Pd * Pd + r;
+                    if (KIND != 2) {
+                        __nv_bfloat16* o = a.out + a.out_off[U.inst];
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        float g[8];
+                        for (int c = 0; c < 4; ++c) {
+                            float gl[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) g[e] = gelu_exact(v[c * 8 + e] + bias[c * 8 + e]);
-                        *reinterpret_cast<uint4*>(o + ((long long)c * P + p) * 8) = pack8(g);
-                    }
-                } else {
-                    const int i = xp - 1, j = yp - 1, k = zp - 1;
-                    const int n = i + M * (j + M * k);
-                    const float y = v[0] + bias[0];
-                    float* o = a.io.out + a.io.off[w.inst];
-                    if (a.mode == CONV_PREC) {
-                        const bool bd = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
-                        const float scale = (float)(a.io.st[w.inst].s / a.io.D[w.inst].alpha);
-                        o[n] = bd ? a.io.vin[a.io.vin_off[w.inst] + n] : scale * y;
+                            for (int e = 0; e < 8; ++e) gl[e] = gelu_exact(v[c * 8 + e] + bias[c * 8 + e]);
+                            *reinterpret_cast<uint4*>(o + ((long long)c * P + p) * 8) = pack8(gl);
+                        }
                     } else {
-                        o[n] = y;
+                        const int i = xp - 1, j = yp - 1, kk = z - 1;
+                        const int n = i + M * (j + M * kk);
+                        const float y = v[0] + bias[0];
+                        float* o = a.io.out + a.io.off[U.inst];
+                        if (a.mode == CONV_PREC) {
+                            const bool bd = (i == 0 || i == N || j == 0 || j == N || kk == 0 || kk == N);
+                            const float scale = (float)(a.io.st[U.inst].s / a.io.D[U.inst].alpha);
+                            o[n] = bd ? a.io.vin[a.io.vin_off[U.inst] + n] : scale * y;
+                        } else {
+                            o[n] = y;
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[bsel]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[s]);
-            ++it;
         }
     }
 
@@ -354,14 +386,21 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
 
 // ---------------------------------------------------------------------------
 // host side
-int tc_smem_bytes(int kind, int W) {
+int tc_smem_bytes(int kind, int W, int ns) {
     const int cin8 = kind == 1 ? 1 : 4;
-    return tc_align(tc_wimg_bytes(kind)) + 2 * 3 * cin8 * W * 16 + 8 * 8 + 16;
+    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 4) * 8 + 16;
+}
+
+// Ring slots that fit next to the hidden-layer weights (at most 8).
+int tc_ring_slots(int W) {
+    for (int ns = 8; ns >= 4; --ns)
+        if (tc_smem_bytes(0, W, ns) <= 227 * 1024) return ns;
+    return 0;
 }
 
 template <int KIND, int TPS>
 static md_status launch_one(const TcArgs& a, int grid, cudaStream_t s) {
-    const int smem = tc_smem_bytes(KIND, a.W);
+    const int smem = tc_smem_bytes(KIND, a.W, a.NS);
     k_conv_tc<KIND, TPS><<<grid, 192, smem, s>>>(a);
     MD_CHECK_LAUNCH();
     return MD_OK;
@@ -374,8 +413,9 @@ int tc_window_rows(int tps, int pd_max) { return (tps * 128 + 2 * (pd_max + 1) +
 md_status tc_prepare(int W, int tps) {
     static int done[3] = {-1, -1, -1};
     if (done[tps] == W) return MD_OK;
-    const int s0 = tc_smem_bytes(0, W), s1 = tc_smem_bytes(1, W), s2 = tc_smem_bytes(2, W);
-    if (s0 > 227 * 1024) { md_set_error("conv tile window too large for shared memory"); return MD_ERR_ARG; }
+    const int ns = tc_ring_slots(W);
+    if (ns == 0) { md_set_error("conv tile window too large for shared memory"); return MD_ERR_ARG; }
+    const int s0 = tc_smem_bytes(0, W, ns), s1 = tc_smem_bytes(1, W, ns), s2 = tc_smem_bytes(2, W, ns);
     if (tps == 2) {
         MD_CUDA(cudaFuncSetAttribute(k_conv_tc<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
         MD_CUDA(cudaFuncSetAttribute(k_conv_tc<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
@@ -402,7 +442,7 @@ md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s
 
 // Weight images in the operand layout the MMAs read:
 //   kind 0: [tap 27][k-chunk 4][n 32][8]
-//   kind 1: [pair 14][k-chunk 2 (= the pair's two taps)][n 32][8]
+//   kind 1: [dz 3][pair 5][k-chunk 2 (= the pair's two taps)][n 32][8], tap 9 of a pair zero
 //   kind 2: [tap 27][k-chunk 4][n 16][8], columns 1..15 zero
 void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img) {
     const int ncol = kind == 2 ? 16 : 32;
@@ -412,14 +452,16 @@ void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__
         return W[((size_t)co * cin + ci) * 27 + tap];
     };
     if (kind == 1) {
-        for (int pr = 0; pr < 14; ++pr)
-            for (int half = 0; half < 2; ++half) {
-                const int tap = 2 * pr + half;
-                for (int n = 0; n < 32; ++n)
-                    for (int l = 0; l < 8; ++l)
-                        img[((size_t)(pr * 2 + half) * 32 + n) * 8 + l] =
-                            __float2bfloat16_rn(tap < 27 ? w_at(n, l, tap) : 0.0f);
-            }
+        for (int dz = 0; dz < 3; ++dz)
+            for (int pr = 0; pr < 5; ++pr)
+                for (int half = 0; half < 2; ++half) {
+                    const int q9 = 2 * pr + half;
+                    const int tap = dz * 9 + q9;
+                    for (int n = 0; n < 32; ++n)
+                        for (int l = 0; l < 8; ++l)
+                            img[((size_t)((dz * 5 + pr) * 2 + half) * 32 + n) * 8 + l] =
+                                __float2bfloat16_rn(q9 < 9 ? w_at(n, l, tap) : 0.0f);
+                }
     } else {
         for (int tap = 0; tap < 27; ++tap)
             for (int kc = 0; kc < 4; ++kc)

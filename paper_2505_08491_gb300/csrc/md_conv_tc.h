@@ -4,10 +4,9 @@
 
 #include "md_cnn.h"
 
-// One work item: TPS * 128 consecutive padded rows of one instance
-// (TPS = 128-row tiles per pipeline stage, 2, or 1 when the window of a
-// large grid would not fit shared memory twice).
-struct TcItem { int inst, p0; };
+// One work unit: in-plane rows [s0, s0 + TPS*128) of one instance, walked
+// over padded planes [z0, z1) (TPS = 128-row tiles per plane step).
+struct TcUnit { int inst, s0, z0, z1; };
 
 struct TcArgs {
     const __nv_bfloat16* in;     // activation buffer (chunk-major padded layout)
@@ -15,9 +14,10 @@ struct TcArgs {
     __nv_bfloat16* out;          // next activation buffer (hidden layers)
     const long long* out_off;
     const int* Ns;               // per instance grid size N
-    const TcItem* items;
-    int nitems;
-    int W;                       // rows per (dz, chunk) window region in shared memory
+    const TcUnit* units;
+    int nunits;
+    int W;                       // rows per (window, chunk) region in shared memory
+    int NS;                      // ring slots
     const __nv_bfloat16* wimg;   // weight image in operand layout
     const float* bias;
     int cout;                    // real output channels
@@ -27,11 +27,12 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_wimg_bytes(int kind) {
-    return kind == 1 ? 14 * 2 * 32 * 16 : 27 * 4 * (kind == 2 ? 16 : 32) * 16;
+    return kind == 1 ? 15 * 2 * 32 * 16 : 27 * 4 * (kind == 2 ? 16 : 32) * 16;
 }
 __host__ __device__ constexpr int tc_align(int b) { return (b + 1023) & ~1023; }
 
-int tc_smem_bytes(int kind, int W);
+int tc_smem_bytes(int kind, int W, int ns);
+int tc_ring_slots(int W);
 int tc_window_rows(int tps, int pd_max);
 md_status tc_prepare(int W, int tps);
 md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s);
