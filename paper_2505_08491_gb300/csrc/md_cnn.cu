@@ -236,7 +236,6 @@ void cnn_work_destroy(CnnWork* w) {
 }
 
 // ---- kernels ---------------------------------------------------------------------
-__device__ inline float gelu_exact(float x) { return x * normcdff(x); }
 
 __device__ inline void unpack8(const uint4& r, float (&x)[8]) {
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&r);
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restri
             for (int c = 0; c < COUT / 8; ++c) {
                 float v[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = gelu_exact(acc[c * 8 + e]);
+                for (int e = 0; e < 8; ++e) v[e] = gelu_fast(acc[c * 8 + e]);
                 *reinterpret_cast<uint4*>(o + (c * P + p) * 8) = pack8(v);
             }
         } else {

@@ -26,7 +26,7 @@
 //               from per-unit row offsets, into a double-buffered TMEM
 //               accumulator; commits free the accumulator for the epilogue
 //               and the oldest window for the producer;
-//   warps 2..5  epilogue: tcgen05.ld of their 32-lane quarter, bias, GELU,
+//   warps 2..9  epilogue: tcgen05.ld of their 32-lane quarter and column half, bias, GELU,
 //               BF16 pack, 16-byte stores of the grid rows of the plane
 //               (halo rows are computed but never stored, so the zero padding
 //               is preserved).
@@ -142,6 +142,17 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
 }
 
 template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
 __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -155,7 +166,6 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ inline float gelu_exact(float x) { return x * normcdff(x); }
 
 __device__ inline uint4 pack8(const float* v) {
     uint4 r;
@@ -176,7 +186,7 @@ __device__ inline uint4 pack8(const float* v) {
 // z reads windows z-1, z, z+1, so each copied window serves three planes.
 // Windows go round a ring of NS shared-memory slots.
 template <int KIND, int TPS>
-__global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     constexpr int CIN8 = (KIND == 1) ? 1 : 4;
     constexpr int NCOL = (KIND == 2) ? 16 : 32;
     constexpr int WIMG = tc_wimg_bytes(KIND);
@@ -204,7 +214,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
-            mbar_init(&tempty[i], 4);
+            mbar_init(&tempty[i], TC_EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -321,11 +331,15 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
             if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
         }
     } else {
-        // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
-        const int q = warp & 3;
-        float bias[NCOL];
+        // ---------------- epilogue: warps 2..9; TMEM lane quarter = warp % 4,
+        // column half = (warp - 2) / 4 (16 of the 32 accumulator columns)
+        constexpr int HC = NCOL / 2;
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int c0 = half * HC;
+        float bias[HC];
 #pragma unroll
-        for (int c = 0; c < NCOL; ++c) bias[c] = (c < a.cout) ? a.bias[c] : 0.f;
+        for (int c = 0; c < HC; ++c) bias[c] = (c0 + c < a.cout) ? a.bias[c0 + c] : 0.f;
+        const bool idle = (KIND == 2 && half == 1);  // the last layer's one channel is in half 0
         int it = 0;
         bool ok = true;
         for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
@@ -338,9 +352,9 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
                 if (!mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
-                for (int ut = 0; ut < TPS; ++ut) {
-                    float v[NCOL];
-                    tmem_ld<NCOL>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL), v);
+                for (int ut = 0; ut < TPS && !idle; ++ut) {
+                    float v[HC];
+                    tmem_ld<HC>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL + c0), v);
                     const long long r = (long long)U.s0 + ut * 128 + q * 32 + lane;  // in-plane row
                     if (r >= Pd * Pd) continue;
                     const int xp = (int)(r % Pd), yp = (int)(r / Pd);
@@ -349,11 +363,11 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(TcArgs a) {
                     if (KIND != 2) {
                         __nv_bfloat16* o = a.out + a.out_off[U.inst];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
+                        for (int c = 0; c < HC / 8; ++c) {
                             float gl[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) gl[e] = gelu_exact(v[c * 8 + e] + bias[c * 8 + e]);
-                            *reinterpret_cast<uint4*>(o + ((long long)c * P + p) * 8) = pack8(gl);
+                            for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(v[c * 8 + e] + bias[c * 8 + e]);
+                            *reinterpret_cast<uint4*>(o + ((long long)(half * (HC / 8) + c) * P + p) * 8) = pack8(gl);
                         }
                     } else {
                         const int i = xp - 1, j = yp - 1, kk = z - 1;
@@ -401,7 +415,7 @@ int tc_ring_slots(int W) {
 template <int KIND, int TPS>
 static md_status launch_one(const TcArgs& a, int grid, cudaStream_t s) {
     const int smem = tc_smem_bytes(KIND, a.W, a.NS);
-    k_conv_tc<KIND, TPS><<<grid, 192, smem, s>>>(a);
+    k_conv_tc<KIND, TPS><<<grid, TC_THREADS, smem, s>>>(a);
     MD_CHECK_LAUNCH();
     return MD_OK;
 }

@@ -8,6 +8,9 @@
 // over padded planes [z0, z1) (TPS = 128-row tiles per plane step).
 struct TcUnit { int inst, s0, z0, z1; };
 
+#define TC_EPI_WARPS 8                       // epilogue warps: 4 lane quarters x 2 column halves
+#define TC_THREADS (32 * (2 + TC_EPI_WARPS))  // + producer and MMA warps
+
 struct TcArgs {
     const __nv_bfloat16* in;     // activation buffer (chunk-major padded layout)
     const long long* in_off;     // per instance element offset
