@@ -167,6 +167,68 @@ class Network:
         return Y
 
 
+    def backward(self, X: torch.Tensor, dY: torch.Tensor, need_dx: bool = False):
+        """Gradients of sum(dY * N(X)): (dparams (MD_CNN_NPARAMS,), dX or None)."""
+        X = X.contiguous()
+        dY = dY.contiguous()
+        n = X.shape[2]
+        dp = torch.empty(L.MD_CNN_NPARAMS, dtype=torch.float32, device="cuda")
+        dX = torch.empty_like(X) if need_dx else None
+        L.check(L.load().md_cnn_backward(self._h, n, X.shape[0], _ptr(X, torch.float32), _ptr(dY, torch.float32),
+                                         _ptr(dp), _ptr(dX) if need_dx else None, _stream()), "md_cnn_backward")
+        return dp, dX
+
+
+class NetworkFunction(torch.autograd.Function):
+    """Y = N(X) with the library's forward and backward kernels, for use
+    inside torch autograd graphs.  The parameters are those held by `net`;
+    their gradient is returned for a `params` tensor the caller passes
+    (e.g. a flat FP32 copy of the weights it optimises)."""
+
+    @staticmethod
+    def forward(ctx, X, params, net):
+        ctx.net = net
+        ctx.save_for_backward(X)
+        return net.forward(X)
+
+    @staticmethod
+    def backward(ctx, dY):
+        (X,) = ctx.saved_tensors
+        dp, dX = ctx.net.backward(X, dY, need_dx=ctx.needs_input_grad[0])
+        return dX, dp, None
+
+
+def _op_array(ops):
+    return (C.c_void_p * len(ops))(*[o.handle.value for o in ops])
+
+
+def train_loss(net: Network, ops: list, residuals: list, with_grad: bool = True):
+    """Mean training loss ||C z0 - b0||^2 / ||b0||^2 over the samples
+    (operator ops[i], residual residuals[i] float32 of length ops[i].n), and
+    its gradient with respect to the flat parameters."""
+    loss = C.c_double()
+    grad = torch.empty(L.MD_CNN_NPARAMS, dtype=torch.float32, device="cuda") if with_grad else None
+    rs = (C.c_void_p * len(residuals))(*[r.data_ptr() for r in residuals])
+    L.check(L.load().md_train_loss(net.handle, len(ops), _op_array(ops), rs, C.byref(loss),
+                                   _ptr(grad) if with_grad else None, _stream()), "md_train_loss")
+    return loss.value, grad
+
+
+def train(net: Network, ops: list, sample_op: list, residuals: list, *, epochs: int, batch: int = 32,
+          lr: float = 1e-3, lr_min: float = 1e-5, betas=(0.9, 0.999), weight_decay: float = 1e-4,
+          eps: float = 1e-8, seed: int = 0):
+    """Unsupervised training (md_train) in place; returns the mean loss per epoch."""
+    hist = (C.c_double * epochs)()
+    so = (C.c_int * len(sample_op))(*sample_op)
+    rs = (C.c_void_p * len(residuals))(*[r.data_ptr() for r in residuals])
+    cfg = L.MdTrainCfg(len(ops), C.cast(_op_array(ops), C.POINTER(C.c_void_p)), len(sample_op),
+                       C.cast(so, C.POINTER(C.c_int)), C.cast(rs, C.POINTER(C.c_void_p)), int(epochs), int(batch),
+                       float(lr), float(lr_min), float(betas[0]), float(betas[1]), float(weight_decay), float(eps),
+                       int(seed), C.cast(hist, C.POINTER(C.c_double)))
+    L.check(L.load().md_train(net.handle, C.byref(cfg)), "md_train")
+    return list(hist)
+
+
 class Batch:
     """Many instances solved together (md_batch_*)."""
 

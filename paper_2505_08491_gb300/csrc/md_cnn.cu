@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "md_cnn.h"
 #include "md_common.cuh"
@@ -34,7 +35,7 @@ uint64_t fnv1a(const void* p, size_t n) {
 }  // namespace
 
 // ---- parameters --------------------------------------------------------------
-static md_status cnn_upload(md_cnn* c) {
+md_status cnn_upload(md_cnn* c) {
     // packed weights per layer: [tap][cin_pad][cout] BF16 (RN), biases FP32
     std::vector<__nv_bfloat16> w;
     std::vector<float> b;
@@ -62,13 +63,36 @@ static md_status cnn_upload(md_cnn* c) {
         all.insert(all.end(), img.begin(), img.end());
     }
     c->wmma_off[MD_CNN_LAYERS] = all.size();
-    std::vector<void*> tmp;
-    if (c->w) { cudaFree(c->w); c->w = nullptr; }
-    if (c->b) { cudaFree(c->b); c->b = nullptr; }
-    if (c->wmma) { cudaFree(c->wmma); c->wmma = nullptr; }
-    MD_TRY(dev_upload(&tmp, &c->w, w.data(), w.size()));
-    MD_TRY(dev_upload(&tmp, &c->b, b.data(), b.size()));
-    MD_TRY(dev_upload(&tmp, &c->wmma, all.data(), all.size()));
+    // input-gradient (transposed, flipped) weights of every layer:
+    // Wt[tap'][c_out padded to >= 8][c_in padded to >= 8] = W[c_out][c_in][26 - tap']
+    std::vector<__nv_bfloat16> wt;
+    for (int l = 0; l < MD_CNN_LAYERS; ++l) {
+        c->wt_off[l] = wt.size();
+        const float* W = c->host.data() + host_w_off(l);
+        const int cop = kCout[l] < 8 ? 8 : kCout[l], cip = kCin[l] < 8 ? 8 : kCin[l];
+        for (int tp = 0; tp < 27; ++tp)
+            for (int co = 0; co < cop; ++co)
+                for (int ci = 0; ci < cip; ++ci) {
+                    float v = (co < kCout[l] && ci < kCin[l]) ? W[((size_t)co * kCin[l] + ci) * 27 + (26 - tp)] : 0.0f;
+                    wt.push_back(__float2bfloat16_rn(v));
+                }
+    }
+    c->wt_off[MD_CNN_LAYERS] = wt.size();
+    // device buffers keep their size, so a network updated in place (training)
+    // reuses its allocations
+    auto put = [](auto** dst, const auto& v) -> md_status {
+        using T = typename std::remove_reference<decltype(v)>::type::value_type;
+        if (!*dst) {
+            std::vector<void*> tmp;
+            return dev_upload(&tmp, (T**)dst, v.data(), v.size());
+        }
+        MD_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+        return MD_OK;
+    };
+    MD_TRY(put(&c->w, w));
+    MD_TRY(put(&c->b, b));
+    MD_TRY(put(&c->wmma, all));
+    MD_TRY(put(&c->wt, wt));
     return MD_OK;
 }
 
@@ -108,6 +132,7 @@ extern "C" void md_cnn_destroy(md_cnn* c) {
     if (c->w) cudaFree(c->w);
     if (c->b) cudaFree(c->b);
     if (c->wmma) cudaFree(c->wmma);
+    if (c->wt) cudaFree(c->wt);
     delete c;
 }
 
@@ -150,7 +175,7 @@ extern "C" md_status md_cnn_load(const char* path, md_cnn** out) {
 template <int CIN8, int COUT, bool LAST>
 __global__ void k_conv_simt(const __nv_bfloat16* __restrict__, const long long* __restrict__, __nv_bfloat16* __restrict__,
                             const long long* __restrict__, const __nv_bfloat16* __restrict__, const float* __restrict__,
-                            const Seg* __restrict__, const int* __restrict__, OutIO, int);
+                            const Seg* __restrict__, const int* __restrict__, OutIO, int, __nv_bfloat16* __restrict__);
 
 // Kernel attributes are set once, outside any stream capture.
 static md_status cnn_prepare() {
@@ -260,7 +285,8 @@ template <int CIN8, int COUT, bool LAST>
 __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restrict__ in, const long long* __restrict__ in_off,
                                                    __nv_bfloat16* __restrict__ outb, const long long* __restrict__ out_off,
                                                    const __nv_bfloat16* __restrict__ W, const float* __restrict__ Bias,
-                                                   const Seg* __restrict__ seg, const int* __restrict__ Ns, OutIO io, int mode) {
+                                                   const Seg* __restrict__ seg, const int* __restrict__ Ns, OutIO io, int mode,
+                                                   __nv_bfloat16* __restrict__ zsave) {
     constexpr int CIN = CIN8 * 8;
     constexpr int NW = 27 * CIN * COUT;
     if (io.st && !io.st[seg[blockIdx.x].inst].active) return;
@@ -312,6 +338,7 @@ __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restri
 #pragma unroll
                 for (int e = 0; e < 8; ++e) v[e] = gelu_fast(acc[c * 8 + e]);
                 *reinterpret_cast<uint4*>(o + (c * P + p) * 8) = pack8(v);
+                if (zsave) *reinterpret_cast<uint4*>(zsave + out_off[sg.inst] + (c * P + p) * 8) = pack8(acc + c * 8);
             }
         } else {
             float* o = io.out + io.off[sg.inst];
@@ -330,10 +357,10 @@ __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restri
 template <int CIN8, int COUT, bool LAST>
 static md_status launch_conv(const __nv_bfloat16* in, const long long* in_off, __nv_bfloat16* outb,
                              const long long* out_off, const __nv_bfloat16* W, const float* B, const CnnWork* w,
-                             const OutIO& io, int mode, cudaStream_t s) {
+                             const OutIO& io, int mode, cudaStream_t s, __nv_bfloat16* zsave = nullptr) {
     const size_t smem = (size_t)27 * CIN8 * 8 * COUT * sizeof(__nv_bfloat16);
     auto kern = k_conv_simt<CIN8, COUT, LAST>;
-    kern<<<w->nodes.nblocks, 128, smem, s>>>(in, in_off, outb, out_off, W, B, w->nodes.seg, w->N, io, mode);
+    kern<<<w->nodes.nblocks, 128, smem, s>>>(in, in_off, outb, out_off, W, B, w->nodes.seg, w->N, io, mode, zsave);
     MD_CHECK_LAUNCH();
     return MD_OK;
 }
@@ -367,6 +394,41 @@ static md_status tc_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io,
     a.in = src; a.in_off = w->off_ab; a.out = nullptr; a.out_off = nullptr;
     a.wimg = c->wmma + c->wmma_off[5]; a.bias = c->b + c->b_off[5]; a.cout = 1;
     MD_TRY(tc_launch(2, w->tps, a, grid, s));
+    return MD_OK;
+}
+
+// Forward pass keeping every activation: A[l] (l = 1..5) the GELU outputs,
+// Z[l] the pre-activations (BF16, 4 chunks, layout of w->a), x0 the input;
+// the last layer writes y (FP32 grid, + io.off) as CONV_RAW.
+md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A, __nv_bfloat16* const* Z,
+                            const OutIO& io, cudaStream_t s) {
+    const __nv_bfloat16* src = w->x0;
+    const long long* src_off = w->off_x0;
+    for (int l = 0; l < MD_CNN_LAYERS; ++l) {
+        const bool last = l == MD_CNN_LAYERS - 1;
+        if (c->engine == 0) {
+            TcArgs a{};
+            a.Ns = w->N; a.units = w->units; a.nunits = w->nunits; a.W = w->W; a.NS = w->NS; a.err = w->err;
+            a.io = io; a.mode = CONV_RAW;
+            a.in = src; a.in_off = src_off;
+            a.out = last ? nullptr : A[l + 1]; a.out_off = w->off_ab;
+            a.zsave = last ? nullptr : Z[l + 1];
+            a.wimg = c->wmma + c->wmma_off[l]; a.bias = c->b + c->b_off[l]; a.cout = last ? 1 : 32;
+            const int grid = std::max(1, std::min(w->nunits, w->nsm));
+            MD_TRY(tc_launch(l == 0 ? 1 : (last ? 2 : 0), w->tps, a, grid, s));
+        } else {
+            const __nv_bfloat16* W = c->w + c->w_off[l];
+            const float* B = c->b + c->b_off[l];
+            if (l == 0) {
+                MD_TRY((launch_conv<1, 32, false>(src, src_off, A[1], w->off_ab, W, B, w, io, 0, s, Z[1])));
+            } else if (!last) {
+                MD_TRY((launch_conv<4, 32, false>(src, src_off, A[l + 1], w->off_ab, W, B, w, io, 0, s, Z[l + 1])));
+            } else {
+                MD_TRY((launch_conv<4, 1, true>(src, src_off, nullptr, nullptr, W, B, w, io, CONV_RAW, s)));
+            }
+        }
+        if (!last) { src = A[l + 1]; src_off = w->off_ab; }
+    }
     return MD_OK;
 }
 

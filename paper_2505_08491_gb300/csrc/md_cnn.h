@@ -51,6 +51,9 @@ struct OutIO {
 
 md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
                              cudaEvent_t e_hidden0 = nullptr, cudaEvent_t e_hidden1 = nullptr);
+md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A, __nv_bfloat16* const* Z,
+                            const OutIO& io, cudaStream_t s);
+md_status cnn_upload(md_cnn* c);
 // X0 = [v0 / s, l / s, d] from a preconditioner input (instance 3D part at v + voff[i])
 md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
                         cudaStream_t s);

@@ -97,6 +97,23 @@ __device__ __forceinline__ float gelu_fast(float x) {
     return x * phi;
 }
 
+// GELU'(x) = Phi(x) + x phi(x), phi(x) = exp(-x^2/2) / sqrt(2 pi); Phi from
+// the same rational approximation as gelu_fast (e^{-z^2} with z^2 = x^2/2 is
+// also the Gaussian factor of phi).
+__device__ __forceinline__ float gelu_grad_fast(float x) {
+    const float z = fabsf(x) * 0.70710678118654752f;
+    const float t = __frcp_rn(fmaf(0.3275911f, z, 1.0f));
+    float poly = fmaf(1.061405429f, t, -1.453152027f);
+    poly = fmaf(poly, t, 1.421413741f);
+    poly = fmaf(poly, t, -0.284496736f);
+    poly = fmaf(poly, t, 0.254829592f);
+    poly *= t;
+    const float e = __expf(-z * z);
+    const float h = 0.5f * poly * e;
+    const float cdf = x < 0.0f ? h : 1.0f - h;
+    return cdf + x * (0.3989422804014327f * e);
+}
+
 __device__ inline unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

@@ -366,8 +366,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         for (int c = 0; c < HC / 8; ++c) {
                             float gl[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(v[c * 8 + e] + bias[c * 8 + e]);
-                            *reinterpret_cast<uint4*>(o + ((long long)(half * (HC / 8) + c) * P + p) * 8) = pack8(gl);
+                            for (int e = 0; e < 8; ++e) gl[e] = v[c * 8 + e] + bias[c * 8 + e];
+                            const long long at = ((long long)(half * (HC / 8) + c) * P + p) * 8;
+                            if (a.zsave) *reinterpret_cast<uint4*>(a.zsave + a.out_off[U.inst] + at) = pack8(gl);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(gl[e]);
+                            *reinterpret_cast<uint4*>(o + at) = pack8(gl);
                         }
                     } else {
                         const int i = xp - 1, j = yp - 1, kk = z - 1;

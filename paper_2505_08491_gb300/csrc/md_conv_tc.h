@@ -27,6 +27,7 @@ struct TcArgs {
     OutIO io;                    // last layer output / instance gating
     int mode;                    // ConvOut of the last layer
     int* err;                    // set on a timed-out wait
+    __nv_bfloat16* zsave;        // optional pre-activation copy (hidden layers, layout of out)
 };
 
 __host__ __device__ constexpr int tc_wimg_bytes(int kind) {

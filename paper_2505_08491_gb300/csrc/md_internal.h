@@ -112,6 +112,9 @@ struct md_cnn {
     __nv_bfloat16* wmma = nullptr;
     size_t wmma_off[MD_CNN_LAYERS + 1];
     int engine = 0;              // 0: tensor cores (tcgen05), 1: CUDA cores
+    // input-gradient weights (training): per layer [tap'][c_out pad][c_in]
+    __nv_bfloat16* wt = nullptr;
+    size_t wt_off[MD_CNN_LAYERS + 1];
 };
 
 // Per-instance Krylov state (device).

@@ -924,6 +924,19 @@ extern "C" md_status md_solve_batched(int n, const md_op* const* ops, const md_c
     return st;
 }
 
+// Preconditioner input pieces for ninst instances given from outside a solve
+// (training): ||v0||^2, then the 1D solve into z's 1D part, the lift and s.
+md_status launch_prec_input(const Tables& T, const InstDesc* d, const long long* off, const float* v, float* z,
+                            KState* st, int ninst, int max_n1, double* part, cudaStream_t s) {
+    k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, off, v, st, part);
+    MD_CHECK_LAUNCH();
+    const size_t smem = (size_t)max_n1 * 20;
+    if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_tree_lift<<<ninst, 256, smem, s>>>(d, off, v, z, st);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
 // Standalone preconditioner application (one instance).
 __global__ void k_prec_setup(KState* st) { st[0].active = 1; }
 
