@@ -1,0 +1,101 @@
+"""Train the preconditioner network and save it (weights/cnn_trained.bin).
+
+Training set (the unsupervised residual set of Section 4.1, on seeded random
+trees): graphs of 3-31 segments (binary trees of depth 2-5) on grids N = 16
+and 32, beta = 1.  Per graph 8 right-hand sides of the block preconditioner:
+4 random vectors (N(0,1) on every unknown, zero on Dirichlet nodes; the
+high-frequency augmentation of Section 4.1.2) and the residuals of the
+Jacobi-preconditioned FGMRES(30) solve of the graph's own problem after 5,
+10, 20 and 30 iterations (residuals the solver actually meets).  Loss, AdamW
+and the cosine schedule run in md_train.
+
+Usage: python -m paper_2505_08491_gb300.train_net --graphs 1024 --epochs 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+import mdgen  # noqa: E402
+from paper_2505_08491_gb300 import Batch, Network, Operator, train  # noqa: E402
+from paper_2505_08491_gb300.weights import TRAINED, random_params  # noqa: E402
+
+HARVEST = (5, 10, 20, 30)
+
+
+def interior_mask(N):
+    idx = np.arange(N + 1)
+    b = (idx == 0) | (idx == N)
+    return ~(b[:, None, None] | b[None, :, None] | b[None, None, :]).ravel()
+
+
+def build_set(n_graphs: int, first: int = 0):
+    insts = [mdgen.workload_instance("train_trees", first + i) for i in range(n_graphs)]
+    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    samples, sample_op = [], []
+    by_N = {}
+    for i, (w, op) in enumerate(zip(insts, ops)):
+        by_N.setdefault(w["N"], []).append(i)
+        mask = torch.from_numpy(np.concatenate([interior_mask(w["N"]), np.ones(op.n1, bool)])).cuda()
+        for k in range(4):
+            v = torch.from_numpy(mdgen.normal_vector(w["f_seed"] or 0, first + i, op.n, stream=k).astype(np.float32)).cuda()
+            samples.append(v * mask)
+            sample_op.append(i)
+    # harvested residuals, batched per grid size
+    for N, idx in by_N.items():
+        sub = [ops[i] for i in idx]
+        bs = []
+        for i in idx:
+            w = insts[i]
+            f = mdgen.interior_source(w["N"], w["f_seed"])
+            bs.append(ops[i].rhs(torch.from_numpy(f).cuda() if f is not None else None, w["g"]))
+        b_all = torch.cat(bs)
+        B = Batch(sub, "fgmres_jacobi", restart=30)
+        for k in HARVEST:
+            x_all = torch.zeros_like(b_all)
+            B.solve(b_all, x_all, tol=1e-14, maxit=k)
+            for j, i in enumerate(idx):
+                o0, o1 = B.offsets[j], B.offsets[j + 1]
+                r = bs[j] - ops[i].apply(x_all[o0:o1].contiguous())
+                samples.append(r.float())
+                sample_op.append(i)
+        B.close()
+    return ops, samples, sample_op
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--graphs", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-min", type=float, default=1e-5)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=TRAINED)
+    ap.add_argument("--init", default=None, help="start from this network file")
+    args = ap.parse_args()
+    t0 = time.time()
+    ops, samples, sample_op = build_set(args.graphs)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    net = Network.load(args.init) if args.init else Network(random_params(args.seed))
+    hist = train(net, ops, sample_op, samples, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                 lr_min=args.lr_min, seed=args.seed)
+    t2 = time.time()
+    os.makedirs(os.path.dirname(args.out), exist_ok=True)
+    net.save(args.out)
+    print(json.dumps({"graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
+                      "set_seconds": t1 - t0, "train_seconds": t2 - t1, "loss": hist}))
+
+
+if __name__ == "__main__":
+    main()
