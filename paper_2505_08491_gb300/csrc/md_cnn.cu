@@ -216,10 +216,10 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
         ranges.push_back({(int)segs.size(), 0});
         for (int b = 0; b < n3; b += CH) segs.push_back({i, 0, b, std::min(n3, b + CH)});
         ranges.back().count = (int)segs.size() - ranges.back().first;
-        // columns of tps*128 in-plane rows, walked over the planes holding grid
+        // columns of tps*126 in-plane rows, walked over the planes holding grid
         // nodes (padded z in [1, N+2)) in chunks of at most 17 planes
         const int nz = Ns[i] + 1, nch = (nz + 16) / 17;
-        for (long long s0 = 0; s0 < Pd * Pd; s0 += 128 * w->tps)
+        for (long long s0 = 0; s0 < Pd * Pd; s0 += 126 * w->tps)
             for (int c = 0; c < nch; ++c) {
                 const int z0 = 1 + (int)((long long)nz * c / nch), z1 = 1 + (int)((long long)nz * (c + 1) / nch);
                 units.push_back({i, (int)s0, z0, z1});
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restri
                                                    __nv_bfloat16* __restrict__ zsave) {
     constexpr int CIN = CIN8 * 8;
     constexpr int NW = 27 * CIN * COUT;
-    if (io.st && !io.st[seg[blockIdx.x].inst].active) return;
+    if (!cnn_runs(io.st, seg[blockIdx.x].inst)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem_raw);
     for (int i = threadIdx.x; i < NW; i += blockDim.x) sw[i] = W[i];
@@ -455,7 +455,7 @@ __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__
                             const float* __restrict__ v, const long long* __restrict__ voff, const KState* __restrict__ st,
                             __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off) {
     const Seg sg = seg[blockIdx.x];
-    if (!st[sg.inst].active) return;
+    if (!cnn_runs(st, sg.inst)) return;
     const InstDesc& d = D[sg.inst];
     const int N = Ns[sg.inst], M = N + 1;
     const long long Pd = N + 3;

@@ -177,21 +177,31 @@ __device__ inline uint4 pack8(const float* v) {
 
 }  // namespace
 
-// KIND 0: hidden 32 -> 32; KIND 1: first 3(8) -> 32 with paired taps;
-// KIND 2: last 32 -> 1 (N = 16).
+// KIND 0: hidden 32 -> 32; KIND 1: first 3(8) -> 32; KIND 2: last 32 -> 1.
 //
-// A work unit is a column of TPS*128 in-plane rows starting at s0, walked
+// dx folding.  For every (dy, dz) the MMA multiplies the A tile (128 rows a_i
+// shifted by dy Pd + dz Pd^2) by the weights of the three dx taps side by
+// side (N = 3 x 32 = 96 columns; 16 for the last layer):
+//   D[i][g*32 + o] = sum_{dy,dz,c} X[a_i + dy Pd + dz Pd^2][c] W[o][c][dz,dy,dx=g-1],
+// and the output of row a_i is O[i] = D[i-1][g=0] + D[i][g=1] + D[i+1][g=2]
+// (the dx = -1, 0, +1 taps read rows a_i - 1, a_i, a_i + 1).  Row i-1 / i+1
+// of the tile live in the neighbouring TMEM lanes: the epilogue moves them
+// with warp shuffles, and across the 32-lane warp boundaries through shared
+// memory.  A tile of 128 lanes therefore yields 126 outputs (lanes 1..126);
+// tiles are spaced 126 rows apart.
+//
+// A work unit is a column of TPS*126 in-plane rows starting at s0, walked
 // over planes z in [z0, z1).  Window w holds, for plane w, the rows
-// [w Pd^2 + s0 - (Pd+1), + TPS*128 + 2(Pd+1) + 8) of every input chunk; plane
-// z reads windows z-1, z, z+1, so each copied window serves three planes.
+// [w Pd^2 + s0 - 1 - Pd, + TPS*126 + 2 Pd + 10) of every input chunk; plane z
+// reads windows z-1, z, z+1, so each copied window serves three planes.
 // Windows go round a ring of NS shared-memory slots.
 template <int KIND, int TPS>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     constexpr int CIN8 = (KIND == 1) ? 1 : 4;
-    constexpr int NCOL = (KIND == 2) ? 16 : 32;
+    constexpr int NCOL = (KIND == 2) ? 16 : 96;   // MMA N (accumulator columns per tile)
     constexpr int WIMG = tc_wimg_bytes(KIND);
     constexpr uint32_t IDESC = idesc_bf16(128, NCOL);
-    constexpr int TMEM_COLS = 128;
+    constexpr int TMEM_COLS = (2 * TPS * NCOL <= 128) ? 128 : ((2 * TPS * NCOL <= 256) ? 256 : 512);
     extern __shared__ __align__(1024) unsigned char sm[];
     const int W = a.W, NS = a.NS;
     const int slot_bytes = CIN8 * W * 16;
@@ -202,7 +212,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     uint64_t* empty = bars + NS;       // [NS]
     uint64_t* tfull = bars + 2 * NS;   // [2]
     uint64_t* tempty = bars + 2 * NS + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+    uint64_t* xbar = bars + 2 * NS + 4;  // [2] epilogue exchange, double-buffered
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6);
+    // warp-boundary exchange of the epilogue: [buffer][quarter][half][2 x 16]
+    float* xch = reinterpret_cast<float*>(bars + 2 * NS + 8);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     for (int i = threadIdx.x; i < WIMG / 16; i += blockDim.x)
@@ -215,6 +228,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], TC_EPI_WARPS);
+            mbar_init(&xbar[i], TC_EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -238,9 +252,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             bool ok = true;
             for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
                 const TcUnit U = a.units[un];
-                if (a.io.st && !a.io.st[U.inst].active) continue;
+                if (!cnn_runs(a.io.st, U.inst)) continue;
                 const long long Pd = a.Ns[U.inst] + 3, P = Pd * Pd * Pd;
-                const int wl = TPS * 128 + 2 * (int)(Pd + 1) + 8;
+                const int wl = tc_window_load_rows(TPS, (int)Pd);
                 const __nv_bfloat16* base = a.in + a.in_off[U.inst];
                 for (int w = U.z0 - 1; w <= U.z1; ++w, ++g) {
                     const int slot = g % NS, r = g / NS;
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     mbar_arrive_expect_tx(&full[slot], (uint32_t)(CIN8 * wl * 16));
                     unsigned char* dst = ring + (size_t)slot * slot_bytes;
                     for (int c = 0; c < CIN8; ++c) {
-                        const long long row = (long long)c * P + (long long)w * Pd * Pd + U.s0 - (Pd + 1);
+                        const long long row = (long long)c * P + (long long)w * Pd * Pd + U.s0 - 1 - Pd;
                         bulk_g2s(dst + (size_t)c * W * 16, base + row * 8, (uint32_t)(wl * 16), &full[slot]);
                     }
                 }
@@ -266,12 +280,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             const uint64_t a_hi = (1ULL << 46) | ((uint64_t)((128 >> 4) & 0x3FFF) << 32);  // version, SBO = 128
             for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
                 const TcUnit U = a.units[un];
-                if (a.io.st && !a.io.st[U.inst].active) continue;
-                const int Pd = a.Ns[U.inst] + 3;
+                if (!cnn_runs(a.io.st, U.inst)) continue;
+                const uint32_t pd16 = (uint32_t)(a.Ns[U.inst] + 3) * 16;
                 const int nwin = U.z1 - U.z0 + 2;
-                uint32_t rowoff[9];
-#pragma unroll
-                for (int q9 = 0; q9 < 9; ++q9) rowoff[q9] = (uint32_t)(Pd + 1 + (q9 / 3 - 1) * Pd + (q9 % 3 - 1)) * 16;
                 for (int k = 0; k < nwin - 2 && ok; ++k) {
                     // windows k, k+1, k+2 of this unit (planes z-1, z, z+1)
                     const int g0 = g + k;
@@ -289,16 +300,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                     for (int ut = 0; ut < TPS; ++ut) {
                         const uint32_t d = tmem + (uint32_t)((bsel * TPS + ut) * NCOL);
+                        const uint32_t ub = (uint32_t)(ut * 126 * 16);
                         if (KIND == 1) {
-                            // per z-window: taps (0,1) (2,3) (4,5) (6,7) (8, zero-weight row + 1)
+                            // one 8-channel chunk: per z-window the (dy=-1, dy=0) rows in
+                            // one K=16 step, (dy=+1, zero-weight row + 1) in a second
 #pragma unroll
                             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                                for (int pr = 0; pr < 5; ++pr) {
-                                    const uint32_t a1 = sb[dz] + rowoff[2 * pr] + ut * 2048;
-                                    const uint32_t a2 = (pr < 4) ? sb[dz] + rowoff[2 * pr + 1] + ut * 2048 : a1 + 16;
+                                for (int pr = 0; pr < 2; ++pr) {
+                                    const uint32_t a1 = sb[dz] + ub + (uint32_t)(2 * pr) * pd16;
+                                    const uint32_t a2 = pr == 0 ? a1 + pd16 : a1 + 16;
                                     const uint64_t ad = a_hi | ((uint64_t)(((a2 - a1) >> 4) & 0x3FFF) << 16) | ((a1 >> 4) & 0x3FFF);
-                                    const uint64_t bd = sdesc(wb + (uint32_t)((dz * 5 + pr) * 1024), 512, 128);
+                                    const uint64_t bd = sdesc(wb + (uint32_t)((dz * 2 + pr) * 2 * NCOL * 16), NCOL * 16, 128);
                                     mma_bf16(d, ad, bd, IDESC, (dz > 0 || pr > 0) ? 1u : 0u);
                                 }
                         } else {
@@ -306,14 +319,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                                for (int q9 = 0; q9 < 9; ++q9)
+                                for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                                     for (int hh = 0; hh < 2; ++hh) {
-                                        const int t = dz * 9 + q9;
-                                        const uint32_t aa = sb[dz] + (uint32_t)(2 * hh * W * 16) + rowoff[q9] + ut * 2048;
+                                        const int combo = dz * 3 + dy;
+                                        const uint32_t aa = sb[dz] + (uint32_t)(2 * hh * W * 16) + ub + (uint32_t)dy * pd16;
                                         const uint64_t ad = a_hi | a_lbo | ((aa >> 4) & 0x3FFF);
-                                        const uint64_t bd = sdesc(wb + (uint32_t)((t * 4 + 2 * hh) * NCOL * 16), NCOL * 16, 128);
-                                        mma_bf16(d, ad, bd, IDESC, (t > 0 || hh > 0) ? 1u : 0u);
+                                        const uint64_t bd = sdesc(wb + (uint32_t)((combo * 4 + 2 * hh) * NCOL * 16), NCOL * 16, 128);
+                                        mma_bf16(d, ad, bd, IDESC, (combo > 0 || hh > 0) ? 1u : 0u);
                                     }
                         }
                     }
@@ -331,20 +344,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
         }
     } else {
-        // ---------------- epilogue: warps 2..9; TMEM lane quarter = warp % 4,
-        // column half = (warp - 2) / 4 (16 of the 32 accumulator columns)
-        constexpr int HC = NCOL / 2;
-        const int q = warp & 3, half = (warp - 2) >> 2;
-        const int c0 = half * HC;
+        // ---------------- epilogue: warps 2..9; TMEM lane quarter q = warp % 4,
+        // output-channel half h = (warp - 2) / 4
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        constexpr int HC = (KIND == 2) ? 1 : 16;   // output channels per thread
         float bias[HC];
 #pragma unroll
-        for (int c = 0; c < HC; ++c) bias[c] = (c0 + c < a.cout) ? a.bias[c0 + c] : 0.f;
-        const bool idle = (KIND == 2 && half == 1);  // the last layer's one channel is in half 0
-        int it = 0;
+        for (int c = 0; c < HC; ++c) bias[c] = (KIND == 2) ? a.bias[0] : a.bias[h * 16 + c];
+        int it = 0, xcnt = 0;
         bool ok = true;
         for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
             const TcUnit U = a.units[un];
-            if (a.io.st && !a.io.st[U.inst].active) continue;
+            if (!cnn_runs(a.io.st, U.inst)) continue;
             const int N = a.Ns[U.inst], M = N + 1;
             const long long Pd = N + 3, P = Pd * Pd * Pd;
             for (int z = U.z0; z < U.z1; ++z, ++it) {
@@ -352,38 +363,81 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 if (!mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err)) { ok = false; break; }
                 tc_fence_after();
 #pragma unroll 1
-                for (int ut = 0; ut < TPS && !idle; ++ut) {
-                    float v[HC];
-                    tmem_ld<HC>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL + c0), v);
-                    const long long r = (long long)U.s0 + ut * 128 + q * 32 + lane;  // in-plane row
+                for (int ut = 0; ut < TPS; ++ut) {
+                    // this lane's three column groups (dx = -1, 0, +1)
+                    float dm[HC], dc[HC], dp[HC];
+                    const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
+                    if (KIND == 2) {
+                        float v[16];
+                        tmem_ld<16>(tb, v);
+                        dm[0] = v[0];
+                        dc[0] = v[1];
+                        dp[0] = v[2];
+                    } else {
+                        float v[16];
+                        tmem_ld<16>(tb + 0 * 32 + h * 16, v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) dm[c] = v[c];
+                        tmem_ld<16>(tb + 1 * 32 + h * 16, v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) dc[c] = v[c];
+                        tmem_ld<16>(tb + 2 * 32 + h * 16, v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) dp[c] = v[c];
+                    }
+                    // warp-boundary values: lane 31's dx=-1 group and lane 0's dx=+1 group
+                    // (bounded mbarrier handshake among the epilogue warps; buffer
+                    // xcnt & 1 is rewritten only after every warp passed the next one)
+                    const int xbuf = xcnt & 1;
+                    float* xb = xch + (size_t)xbuf * (4 * 2 * 32);
+                    if (lane == 31)
+#pragma unroll
+                        for (int c = 0; c < HC; ++c) xb[(q * 2 + h) * 32 + c] = dm[c];
+                    if (lane == 0)
+#pragma unroll
+                        for (int c = 0; c < HC; ++c) xb[(q * 2 + h) * 32 + 16 + c] = dp[c];
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&xbar[xbuf]);
+                    if (!mbar_wait(&xbar[xbuf], (xcnt >> 1) & 1, a.err)) { ok = false; break; }
+                    ++xcnt;
+                    float o[HC];
+#pragma unroll
+                    for (int c = 0; c < HC; ++c) {
+                        float up = __shfl_up_sync(0xffffffffu, dm[c], 1);    // D[i-1][dx=-1]
+                        float dn = __shfl_down_sync(0xffffffffu, dp[c], 1);  // D[i+1][dx=+1]
+                        if (lane == 0) up = q > 0 ? xb[((q - 1) * 2 + h) * 32 + c] : 0.f;
+                        if (lane == 31) dn = q < 3 ? xb[((q + 1) * 2 + h) * 32 + 16 + c] : 0.f;
+                        o[c] = up + dc[c] + dn + bias[c];
+                    }
+                    const int i = q * 32 + lane;  // tile lane; outputs for lanes 1..126
+                    if (i < 1 || i > 126) continue;
+                    if (KIND == 2 && h == 1) continue;
+                    const long long r = (long long)U.s0 - 1 + ut * 126 + i;  // in-plane row
                     if (r >= Pd * Pd) continue;
                     const int xp = (int)(r % Pd), yp = (int)(r / Pd);
                     if (xp < 1 || xp > M || yp < 1 || yp > M) continue;
                     const long long p = (long long)z * Pd * Pd + r;
                     if (KIND != 2) {
-                        __nv_bfloat16* o = a.out + a.out_off[U.inst];
+                        __nv_bfloat16* out = a.out + a.out_off[U.inst];
 #pragma unroll
-                        for (int c = 0; c < HC / 8; ++c) {
+                        for (int c8 = 0; c8 < 2; ++c8) {
+                            const long long at = ((long long)(h * 2 + c8) * P + p) * 8;
+                            if (a.zsave) *reinterpret_cast<uint4*>(a.zsave + a.out_off[U.inst] + at) = pack8(o + c8 * 8);
                             float gl[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) gl[e] = v[c * 8 + e] + bias[c * 8 + e];
-                            const long long at = ((long long)(half * (HC / 8) + c) * P + p) * 8;
-                            if (a.zsave) *reinterpret_cast<uint4*>(a.zsave + a.out_off[U.inst] + at) = pack8(gl);
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(gl[e]);
-                            *reinterpret_cast<uint4*>(o + at) = pack8(gl);
+                            for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(o[c8 * 8 + e]);
+                            *reinterpret_cast<uint4*>(out + at) = pack8(gl);
                         }
                     } else {
-                        const int i = xp - 1, j = yp - 1, kk = z - 1;
-                        const int n = i + M * (j + M * kk);
-                        const float y = v[0] + bias[0];
-                        float* o = a.io.out + a.io.off[U.inst];
+                        const int ii = xp - 1, jj = yp - 1, kk = z - 1;
+                        const int n = ii + M * (jj + M * kk);
+                        float* ov = a.io.out + a.io.off[U.inst];
                         if (a.mode == CONV_PREC) {
-                            const bool bd = (i == 0 || i == N || j == 0 || j == N || kk == 0 || kk == N);
+                            const bool bd = (ii == 0 || ii == N || jj == 0 || jj == N || kk == 0 || kk == N);
                             const float scale = (float)(a.io.st[U.inst].s / a.io.D[U.inst].alpha);
-                            o[n] = bd ? a.io.vin[a.io.vin_off[U.inst] + n] : scale * y;
+                            ov[n] = bd ? a.io.vin[a.io.vin_off[U.inst] + n] : scale * o[0];
                         } else {
-                            o[n] = y;
+                            ov[n] = o[0];
                         }
                     }
                 }
@@ -406,7 +460,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 // host side
 int tc_smem_bytes(int kind, int W, int ns) {
     const int cin8 = kind == 1 ? 1 : 4;
-    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 4) * 8 + 16;
+    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 8) * 8 + 2 * 4 * 2 * 32 * 4 + 16;
 }
 
 // Ring slots that fit next to the hidden-layer weights (at most 8).
@@ -425,7 +479,7 @@ static md_status launch_one(const TcArgs& a, int grid, cudaStream_t s) {
 }
 
 // Largest window region (rows) per stage size TPS for grids of padded edge Pd.
-int tc_window_rows(int tps, int pd_max) { return (tps * 128 + 2 * (pd_max + 1) + 8 + 7) & ~7; }
+int tc_window_rows(int tps, int pd_max) { return (tc_window_load_rows(tps, pd_max) + 7) & ~7; }
 
 // Kernel attributes are set once per window size, outside stream capture.
 md_status tc_prepare(int W, int tps) {
@@ -458,33 +512,44 @@ md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s
     return launch_one<2, 1>(a, grid, s);
 }
 
-// Weight images in the operand layout the MMAs read:
-//   kind 0: [tap 27][k-chunk 4][n 32][8]
-//   kind 1: [dz 3][pair 5][k-chunk 2 (= the pair's two taps)][n 32][8], tap 9 of a pair zero
-//   kind 2: [tap 27][k-chunk 4][n 16][8], columns 1..15 zero
+// Weight images in the operand layout the MMAs read (n = dx index * 32 + o,
+// i.e. the three dx taps of one (dy, dz) side by side):
+//   kind 0: [combo = dz*3+dy (9)][k-chunk 4][n 96][8]
+//   kind 1: [dz 3][pair 2][k-chunk 2][n 96][8]; pair 0 = (dy -1, dy 0),
+//           pair 1 = (dy +1, zero)
+//   kind 2: [combo 9][k-chunk 4][n 16][8]; n = dx index for o = 0, rest zero
 void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img) {
-    const int ncol = kind == 2 ? 16 : 32;
     img.assign(tc_wimg_bytes(kind) / 2, __float2bfloat16_rn(0.0f));
-    auto w_at = [&](int co, int ci, int tap) -> float {
-        if (co >= cout || ci >= cin) return 0.0f;
-        return W[((size_t)co * cin + ci) * 27 + tap];
+    auto w_at = [&](int o, int c, int tap) -> float {
+        if (o >= cout || c >= cin) return 0.0f;
+        return W[((size_t)o * cin + c) * 27 + tap];
     };
     if (kind == 1) {
         for (int dz = 0; dz < 3; ++dz)
-            for (int pr = 0; pr < 5; ++pr)
+            for (int pr = 0; pr < 2; ++pr)
                 for (int half = 0; half < 2; ++half) {
-                    const int q9 = 2 * pr + half;
-                    const int tap = dz * 9 + q9;
-                    for (int n = 0; n < 32; ++n)
-                        for (int l = 0; l < 8; ++l)
-                            img[((size_t)((dz * 5 + pr) * 2 + half) * 32 + n) * 8 + l] =
-                                __float2bfloat16_rn(q9 < 9 ? w_at(n, l, tap) : 0.0f);
+                    const int dy = 2 * pr + half;  // 3 = zero partner
+                    for (int n = 0; n < 96; ++n)
+                        for (int l = 0; l < 8; ++l) {
+                            const int g = n / 32, o = n % 32;
+                            const float v = dy < 3 ? w_at(o, l, dz * 9 + dy * 3 + g) : 0.0f;
+                            img[((size_t)((dz * 2 + pr) * 2 + half) * 96 + n) * 8 + l] = __float2bfloat16_rn(v);
+                        }
                 }
-    } else {
-        for (int tap = 0; tap < 27; ++tap)
+    } else if (kind == 0) {
+        for (int combo = 0; combo < 9; ++combo)
             for (int kc = 0; kc < 4; ++kc)
-                for (int n = 0; n < ncol; ++n)
+                for (int n = 0; n < 96; ++n)
+                    for (int l = 0; l < 8; ++l) {
+                        const int g = n / 32, o = n % 32;
+                        img[((size_t)(combo * 4 + kc) * 96 + n) * 8 + l] =
+                            __float2bfloat16_rn(w_at(o, kc * 8 + l, combo * 3 + g));
+                    }
+    } else {
+        for (int combo = 0; combo < 9; ++combo)
+            for (int kc = 0; kc < 4; ++kc)
+                for (int n = 0; n < 3; ++n)
                     for (int l = 0; l < 8; ++l)
-                        img[((size_t)(tap * 4 + kc) * ncol + n) * 8 + l] = __float2bfloat16_rn(w_at(n, kc * 8 + l, tap));
+                        img[((size_t)(combo * 4 + kc) * 16 + n) * 8 + l] = __float2bfloat16_rn(w_at(0, kc * 8 + l, combo * 3 + n));
     }
 }

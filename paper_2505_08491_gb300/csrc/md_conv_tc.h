@@ -4,8 +4,9 @@
 
 #include "md_cnn.h"
 
-// One work unit: in-plane rows [s0, s0 + TPS*128) of one instance, walked
-// over padded planes [z0, z1) (TPS = 128-row tiles per plane step).
+// One work unit: in-plane rows [s0, s0 + TPS*126) of one instance, walked
+// over padded planes [z0, z1) (TPS = 128-lane tiles per plane step, each
+// yielding 126 rows).
 struct TcUnit { int inst, s0, z0, z1; };
 
 #define TC_EPI_WARPS 8                       // epilogue warps: 4 lane quarters x 2 column halves
@@ -31,8 +32,11 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_wimg_bytes(int kind) {
-    return kind == 1 ? 15 * 2 * 32 * 16 : 27 * 4 * (kind == 2 ? 16 : 32) * 16;
+    return kind == 1 ? 3 * 2 * 2 * 96 * 16 : 9 * 4 * (kind == 2 ? 16 : 96) * 16;
 }
+// rows one window copy holds: TPS tiles 126 rows apart, 128 rows each, read
+// at dy offsets 0..2 Pd from the window start, plus 8 rows of slack
+__host__ __device__ constexpr int tc_window_load_rows(int tps, int pd) { return (tps - 1) * 126 + 128 + 2 * pd + 8; }
 __host__ __device__ constexpr int tc_align(int b) { return (b + 1023) & ~1023; }
 
 int tc_smem_bytes(int kind, int W, int ns);

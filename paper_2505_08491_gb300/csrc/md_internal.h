@@ -131,9 +131,15 @@ struct KState {
     double tol, inner_tol;
     double rho, alpha_cg, pq;            // CG scalars
     unsigned long long t_start, t_done;  // globaltimer stamps
-    int j, m, active, converged, iters, reorth, nan_seen, fallback, maxit, cycle_iters;
+    int j, m, active, converged, iters, reorth, nan_seen, fallback, maxit, cycle_iters, stalls;
     unsigned int counter[8];             // last-block counters per reduction kernel
 };
+
+// An instance runs the network in this launch: inside its cycle and not
+// switched to the Jacobi fallback.
+__host__ __device__ inline bool cnn_runs(const KState* st, int inst) {
+    return !st || (st[inst].active && !st[inst].fallback);
+}
 
 // Problem-size independent kernel launches (md_apply.cu)
 struct KState;

@@ -114,7 +114,7 @@ __global__ void k_init_state(KState* st, int ninst, double tol, int maxit, int* 
     if (i >= ninst) return;
     KState& S = st[i];
     S.tol = tol; S.maxit = maxit; S.iters = 0; S.converged = 0; S.active = 0; S.j = 0; S.m = 0;
-    S.reorth = 0; S.nan_seen = 0; S.fallback = 0; S.bnorm = 0; S.relres = 1; S.cycle_iters = 0;
+    S.reorth = 0; S.nan_seen = 0; S.fallback = 0; S.bnorm = 0; S.relres = 1; S.cycle_iters = -1; S.stalls = 0;
     S.inner_tol = INNER_REL;
     S.t_start = globaltimer();
     S.t_done = 0;
@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(MD_TB) k_resid(const Seg* __restrict__ seg, co
         S.relres = S.bnorm > 0 ? S.beta / S.bnorm : 0.0;
         S.m = 0;
         S.j = 0;
-        if (S.relres <= S.tol || S.iters >= S.maxit) {
+        // a cycle that made no iteration (breakdown) counts as a stall; three
+        // stalls in a row, or a non-finite residual, end the instance unconverged
+        if (S.cycle_iters == 0) S.stalls += 1;
+        else if (S.cycle_iters > 0) S.stalls = 0;
+        if (S.relres <= S.tol || S.iters >= S.maxit || S.stalls >= 3 || !isfinite(S.relres)) {
             mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
         } else {
             S.active = 1;
@@ -292,8 +296,12 @@ __global__ void k_givens(KState* st, int ninst, int j, int k) {
     }
     const double den = hypot(H[j], H[j + 1]);
     if (den == 0.0 || !isfinite(den)) {
-        S.active = 0;  // breakdown: keep the columns before j
+        // breakdown: keep the columns before j; a preconditioner that gave no
+        // usable direction (or a non-finite one) is replaced by Jacobi for the
+        // rest of this instance's solve
+        S.active = 0;
         S.nan_seen |= !isfinite(den);
+        if (j == 0 || !isfinite(den)) S.fallback = 1;
         return;
     }
     S.cs[j] = H[j] / den;
@@ -316,6 +324,7 @@ __global__ void k_lsq(KState* st, int ninst) {
     if (i >= ninst) return;
     KState& S = st[i];
     S.active = 0;
+    S.cycle_iters = S.t_done ? 0 : S.m;
     if (S.t_done || S.m == 0) return;
     const int m = S.m;
     for (int r = m - 1; r >= 0; --r) {
@@ -348,9 +357,9 @@ __global__ void __launch_bounds__(MD_TB) k_xupd(const Seg* __restrict__ seg, con
 // Jacobi: Z = diag(A)^{-1} V
 __global__ void __launch_bounds__(MD_TB) k_jacobi(const Seg* __restrict__ seg, const long long* __restrict__ off,
                                                   const InstDesc* __restrict__ D, const float* __restrict__ v, float* z,
-                                                  const KState* st) {
+                                                  const KState* st, int only_fallback) {
     const Seg sg = seg[blockIdx.x];
-    if (st && !st[sg.inst].active) return;
+    if (st && (!st[sg.inst].active || (only_fallback && !st[sg.inst].fallback))) return;
     const long long o = off[sg.inst];
     const float* dinv = D[sg.inst].dinv32;
     for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) z[o + e] = dinv[e] * v[o + e];
@@ -365,7 +374,7 @@ __global__ void __launch_bounds__(256) k_tree_lift(const InstDesc* __restrict__ 
     __shared__ double sh[32];
     const int inst = blockIdx.x;
     KState& S = st[inst];
-    if (!S.active) return;
+    if (!S.active || S.fallback) return;
     const InstDesc& d = D[inst];
     const int n1 = d.n1;
     float* y = reinterpret_cast<float*>(smraw);
@@ -570,12 +579,15 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
                                 cudaEvent_t e_conv0 = nullptr, cudaEvent_t e_conv1 = nullptr) {
     const Tables& T = B->tabs;
     if (!cnn) {
-        k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st);
+        k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 0);
         MD_CHECK_LAUNCH();
         rec(e_conv0, s);
         rec(e_conv1, s);
         return MD_OK;
     }
+    // instances whose network application broke down continue with Jacobi
+    k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 1);
+    MD_CHECK_LAUNCH();
     const size_t smem = (size_t)B->max_n1 * 20;
     k_tree_lift<<<B->ninst, 256, smem, s>>>(B->d, B->off, vin, zout, B->st);
     MD_CHECK_LAUNCH();

@@ -1,0 +1,47 @@
+"""Failure handling on the GPU with failures made on the host: a network
+whose activations overflow (non-finite preconditioner output) switches the
+affected instances to the Jacobi fallback, and a useless network does not
+keep a batch from terminating."""
+import numpy as np
+import pytest
+import torch
+
+import mdgen
+from helpers import instance_cases
+from oracle import fem
+
+pytestmark = pytest.mark.gpu
+
+
+def test_non_finite_network_falls_back_to_jacobi():
+    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300.weights import NPARAMS
+    cases = instance_cases()[:3]
+    probs = [fem.Problem(N, g, beta) for _, N, g, beta, _ in cases]
+    ops = [Operator(N, g, beta) for _, N, g, beta, _ in cases]
+    b_all = torch.from_numpy(np.concatenate([p.rhs(p.source(c[4]), 1.0) for p, c in zip(probs, cases)])).cuda()
+    bad = Network(np.full(NPARAMS, 1e30, dtype=np.float32))
+    B = Batch(ops, "fgmres_cnn", bad, restart=30)
+    x = torch.zeros_like(b_all)
+    its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=5000)
+    assert ok, (its, rels)
+    xs = x.cpu().numpy()
+    for i, p in enumerate(probs):
+        xi = xs[B.offsets[i]:B.offsets[i + 1]]
+        assert np.linalg.norm(p.rhs(p.source(cases[i][4]), 1.0) - p.A @ xi) <= 1.01e-8 * np.linalg.norm(b_all[B.offsets[i]:B.offsets[i + 1]].cpu().numpy())
+
+
+def test_useless_network_terminates_on_mixed_batch():
+    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300.weights import random_params
+    insts = [mdgen.workload_instance("batch256_mixed", i) for i in range(6)]
+    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    bs = []
+    for w, op in zip(insts, ops):
+        f = mdgen.interior_source(w["N"], w["f_seed"])
+        bs.append(op.rhs(torch.from_numpy(f).cuda(), w["g"]))
+    b_all = torch.cat(bs)
+    B = Batch(ops, "fgmres_cnn", Network(random_params(0)), restart=30)
+    x = torch.zeros_like(b_all)
+    its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=120)
+    assert len(its) == 6 and all(i <= 120 for i in its)
