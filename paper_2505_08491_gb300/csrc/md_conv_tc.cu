@@ -26,7 +26,7 @@
 //               from per-unit row offsets, into a double-buffered TMEM
 //               accumulator; commits free the accumulator for the epilogue
 //               and the oldest window for the producer;
-//   warps 2..9  epilogue: tcgen05.ld of their 32-lane quarter and column half, bias, GELU,
+//   warps 2..17 epilogue: tcgen05.ld of their 32-lane quarter and 8-channel group, bias, GELU,
 //               BF16 pack, 16-byte stores of the grid rows of the plane
 //               (halo rows are computed but never stored, so the zero padding
 //               is preserved).
@@ -121,51 +121,22 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// loads without the wait (several loads, then one tmem_wait_ld)
 template <int NC>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[NC]);
+__device__ __forceinline__ void tmem_ld_nowait(uint32_t taddr, float (&v)[NC]);
 
 template <>
-__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-template <>
-__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8]) {
+__device__ __forceinline__ void tmem_ld_nowait<8>(uint32_t taddr, float (&v)[8]) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                 : "r"(taddr)
+                 : "memory");
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-template <>
-__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 
 __device__ inline uint4 pack8(const float* v) {
     uint4 r;
@@ -344,91 +315,99 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
         }
     } else {
-        // ---------------- epilogue: warps 2..9; TMEM lane quarter q = warp % 4,
-        // output-channel half h = (warp - 2) / 4
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        constexpr int HC = (KIND == 2) ? 1 : 16;   // output channels per thread
-        float bias[HC];
+        // ---------------- epilogue: warps 2 .. 2+TC_EPI_WARPS-1; TMEM lane
+        // quarter q = warp % 4, output-channel group cg = (warp - 2) / 4 of
+        // TC_EPI_CH channels
+        constexpr int CH = (KIND == 2) ? 1 : TC_EPI_CH;
+        const int q = warp & 3, cg = (warp - 2) >> 2;
+        const int i = q * 32 + lane;  // tile lane; outputs for lanes 1..126
+        float bias[CH];
 #pragma unroll
-        for (int c = 0; c < HC; ++c) bias[c] = (KIND == 2) ? a.bias[0] : a.bias[h * 16 + c];
+        for (int c = 0; c < CH; ++c) bias[c] = (KIND == 2) ? a.bias[0] : a.bias[cg * CH + c];
+        const bool writer = KIND != 2 || cg == 0;
         int it = 0, xcnt = 0;
         bool ok = true;
         for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
             const TcUnit U = a.units[un];
             if (!cnn_runs(a.io.st, U.inst)) continue;
             const int N = a.Ns[U.inst], M = N + 1;
-            const long long Pd = N + 3, P = Pd * Pd * Pd;
+            const int Pd = N + 3, P2 = Pd * Pd, P = P2 * Pd;
+            // in-plane row of this lane in each tile, and whether it is a grid row
+            // (the same for every plane of the unit)
+            int rr[TPS];
+            bool val[TPS];
+#pragma unroll
+            for (int ut = 0; ut < TPS; ++ut) {
+                const int r = U.s0 - 1 + ut * 126 + i;
+                const int yp = r / Pd, xp = r - yp * Pd;
+                rr[ut] = r;
+                val[ut] = writer && i >= 1 && i <= 126 && r < P2 && xp >= 1 && xp <= M && yp >= 1 && yp <= M;
+            }
+            __nv_bfloat16* outU = (KIND != 2) ? a.out + a.out_off[U.inst] : nullptr;
+            __nv_bfloat16* zsU = (KIND != 2 && a.zsave) ? a.zsave + a.out_off[U.inst] : nullptr;
             for (int z = U.z0; z < U.z1; ++z, ++it) {
                 const int bsel = it & 1;
                 if (!mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err)) { ok = false; break; }
                 tc_fence_after();
-#pragma unroll 1
+#pragma unroll
                 for (int ut = 0; ut < TPS; ++ut) {
                     // this lane's three column groups (dx = -1, 0, +1)
-                    float dm[HC], dc[HC], dp[HC];
+                    float dm[CH], dc[CH], dp[CH];
                     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
-                    if (KIND == 2) {
-                        float v[16];
-                        tmem_ld<16>(tb, v);
+                    if constexpr (KIND == 2) {
+                        float v[8];
+                        tmem_ld_nowait<8>(tb, v);
+                        tmem_wait_ld();
                         dm[0] = v[0];
                         dc[0] = v[1];
                         dp[0] = v[2];
                     } else {
-                        float v[16];
-                        tmem_ld<16>(tb + 0 * 32 + h * 16, v);
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) dm[c] = v[c];
-                        tmem_ld<16>(tb + 1 * 32 + h * 16, v);
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) dc[c] = v[c];
-                        tmem_ld<16>(tb + 2 * 32 + h * 16, v);
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) dp[c] = v[c];
+                        tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm);
+                        tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc);
+                        tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp);
+                        tmem_wait_ld();
                     }
-                    // warp-boundary values: lane 31's dx=-1 group and lane 0's dx=+1 group
+                    // warp-boundary values: lane 31's dx=-1 group, lane 0's dx=+1 group
                     // (bounded mbarrier handshake among the epilogue warps; buffer
                     // xcnt & 1 is rewritten only after every warp passed the next one)
                     const int xbuf = xcnt & 1;
-                    float* xb = xch + (size_t)xbuf * (4 * 2 * 32);
+                    float* xb = xch + (size_t)xbuf * (4 * TC_EPI_GROUPS * 2 * TC_EPI_CH);
+                    float* mine = xb + (q * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
                     if (lane == 31)
 #pragma unroll
-                        for (int c = 0; c < HC; ++c) xb[(q * 2 + h) * 32 + c] = dm[c];
+                        for (int c = 0; c < CH; ++c) mine[c] = dm[c];
                     if (lane == 0)
 #pragma unroll
-                        for (int c = 0; c < HC; ++c) xb[(q * 2 + h) * 32 + 16 + c] = dp[c];
+                        for (int c = 0; c < CH; ++c) mine[TC_EPI_CH + c] = dp[c];
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&xbar[xbuf]);
                     if (!mbar_wait(&xbar[xbuf], (xcnt >> 1) & 1, a.err)) { ok = false; break; }
                     ++xcnt;
-                    float o[HC];
+                    const float* prev = xb + (((q + 3) & 3) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
+                    const float* next = xb + (((q + 1) & 3) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
+                    float o[CH];
 #pragma unroll
-                    for (int c = 0; c < HC; ++c) {
+                    for (int c = 0; c < CH; ++c) {
                         float up = __shfl_up_sync(0xffffffffu, dm[c], 1);    // D[i-1][dx=-1]
                         float dn = __shfl_down_sync(0xffffffffu, dp[c], 1);  // D[i+1][dx=+1]
-                        if (lane == 0) up = q > 0 ? xb[((q - 1) * 2 + h) * 32 + c] : 0.f;
-                        if (lane == 31) dn = q < 3 ? xb[((q + 1) * 2 + h) * 32 + 16 + c] : 0.f;
+                        if (lane == 0) up = prev[c];
+                        if (lane == 31) dn = next[c];
                         o[c] = up + dc[c] + dn + bias[c];
                     }
-                    const int i = q * 32 + lane;  // tile lane; outputs for lanes 1..126
-                    if (i < 1 || i > 126) continue;
-                    if (KIND == 2 && h == 1) continue;
-                    const long long r = (long long)U.s0 - 1 + ut * 126 + i;  // in-plane row
-                    if (r >= Pd * Pd) continue;
-                    const int xp = (int)(r % Pd), yp = (int)(r / Pd);
-                    if (xp < 1 || xp > M || yp < 1 || yp > M) continue;
-                    const long long p = (long long)z * Pd * Pd + r;
-                    if (KIND != 2) {
-                        __nv_bfloat16* out = a.out + a.out_off[U.inst];
+                    if (!val[ut]) continue;
+                    const int p = z * P2 + rr[ut];
+                    if constexpr (KIND != 2) {
 #pragma unroll
-                        for (int c8 = 0; c8 < 2; ++c8) {
-                            const long long at = ((long long)(h * 2 + c8) * P + p) * 8;
-                            if (a.zsave) *reinterpret_cast<uint4*>(a.zsave + a.out_off[U.inst] + at) = pack8(o + c8 * 8);
+                        for (int c8 = 0; c8 < CH / 8; ++c8) {
+                            const int at = ((cg * (CH / 8) + c8) * P + p) * 8;
+                            if (zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
                             float gl[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(o[c8 * 8 + e]);
-                            *reinterpret_cast<uint4*>(out + at) = pack8(gl);
+                            *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
                         }
                     } else {
+                        const int xp = rr[ut] % Pd, yp = rr[ut] / Pd;
                         const int ii = xp - 1, jj = yp - 1, kk = z - 1;
                         const int n = ii + M * (jj + M * kk);
                         float* ov = a.io.out + a.io.off[U.inst];
@@ -441,6 +420,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         }
                     }
                 }
+                if (!ok) break;
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[bsel]);
@@ -460,7 +440,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 // host side
 int tc_smem_bytes(int kind, int W, int ns) {
     const int cin8 = kind == 1 ? 1 : 4;
-    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 8) * 8 + 2 * 4 * 2 * 32 * 4 + 16;
+    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 8) * 8 + 2 * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH * 4 + 16;
 }
 
 // Ring slots that fit next to the hidden-layer weights (at most 8).

@@ -9,7 +9,9 @@
 // yielding 126 rows).
 struct TcUnit { int inst, s0, z0, z1; };
 
-#define TC_EPI_WARPS 8                       // epilogue warps: 4 lane quarters x 2 column halves
+#define TC_EPI_CH 8                          // output channels per epilogue thread
+#define TC_EPI_GROUPS (32 / TC_EPI_CH)       // channel groups
+#define TC_EPI_WARPS (4 * TC_EPI_GROUPS)     // epilogue warps: 4 TMEM lane quarters x channel groups
 #define TC_THREADS (32 * (2 + TC_EPI_WARPS))  // + producer and MMA warps
 
 struct TcArgs {
