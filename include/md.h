@@ -120,6 +120,23 @@ md_status md_rhs(const md_op* op, const double* f, double g, double* b, md_strea
  * float*) or FP64 (double*).  u and y must not alias.  Asynchronous. */
 md_status md_apply(const md_op* op, md_prec prec, const void* u, void* y, md_stream s);
 
+/* md_apply_noalloc -- the same y = A u as md_apply, for callers that must not
+ * allocate device memory or write the operator's own scratch (an application
+ * that reserves all device memory at start-up, or several users sharing one
+ * read-only operator handle).  The paper has no counterpart: this is a
+ * deployment variant of md_apply.  Its scratch (the quadrature-point values
+ * and a copy of the instance descriptor) is one static device array of the
+ * library, sized for MD_NOALLOC_MAX_NQ quadrature points (about 129 KB),
+ * which every GPU that loads the library keeps until the process exits.
+ * Operators with more quadrature points are rejected with MD_ERR_ARG.
+ * Nothing is allocated: the first call on a device (made with that device
+ * current) looks up the array's address once; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents, so calls that overlap on the GPU race with each other: order them
+ * on one stream or synchronise.  Asynchronous on s. */
+#define MD_NOALLOC_MAX_NQ 16384
+md_status md_apply_noalloc(const md_op* op, md_prec prec, const void* u, void* y, md_stream s);
+
 /* ---- the network -----------------------------------------------------------
  * Six 3x3x3 'same' convolutions 3->32->32->32->32->32->1 with bias, GELU
  * (x Phi(x)) after layers 1-5 (the fully convolutional hypothesis space of

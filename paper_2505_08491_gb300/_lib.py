@@ -59,6 +59,7 @@ SIGNATURES = {
     "md_op_distance": (st, [vp, vp, vp]),
     "md_rhs": (st, [vp, vp, f64, vp, vp]),
     "md_apply": (st, [vp, i32, vp, vp, vp]),
+    "md_apply_noalloc": (st, [vp, i32, vp, vp, vp]),
     "md_cnn_create": (st, [C.POINTER(C.c_float), i64, C.POINTER(vp)]),
     "md_cnn_get_params": (st, [vp, C.POINTER(C.c_float), i64]),
     "md_cnn_set_engine": (st, [vp, i32]),

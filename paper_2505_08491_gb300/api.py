@@ -87,6 +87,15 @@ class Operator:
                                   _stream()), "md_apply")
         return y
 
+    def apply_noalloc(self, u: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        """y = A u without any device allocation (md_apply_noalloc): the
+        scratch is a static array of the library, shared by all calls, so
+        overlapping calls must be ordered; `out` must be given."""
+        prec = L.MD_FP32 if u.dtype == torch.float32 else L.MD_FP64
+        L.check(L.load().md_apply_noalloc(self._h, prec, _ptr(u, u.dtype, self.n, "u"),
+                                          _ptr(out, u.dtype, self.n, "out"), _stream()), "md_apply_noalloc")
+        return out
+
     def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None) -> torch.Tensor:
         z = torch.empty_like(r) if out is None else out
         L.check(L.load().md_precondition(self._h, net.handle if net is not None else None,
