@@ -13,7 +13,7 @@ the circle, Section 2) evaluated at the 1D quadrature points, Psi evaluates
 the 1D P1 field at the same points and W holds the quadrature weights, so that
 (T u0 - u1, T v0 - v1)_Lambda is integrated by 2-point Gauss per 1D element.
 
-Readings of points the paper leaves open (listed in the design doc as well):
+Readings of points the paper leaves open:
   * boundary: homogeneous Dirichlet on every cube-boundary node, imposed by
     zeroing the node's row and column and putting 1 on the diagonal;
   * beta stands for the coupling factor 2*pi*eps and M uses unit line weight;
