@@ -49,8 +49,15 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def instances(rank: int, count: int):
-    return [mdgen.workload_instance(WORKLOAD, rank * count + i) for i in range(count)]
+WORKLOAD_TEXT = {
+    "tree15_32": "seeded binary trees (15 segments, 8 el/seg), N=32, beta=1, f~N(0,1), g=1",
+    "batch256_mixed": "seeded binary trees (7-255 segments), N in {32,48,64}, beta log-uniform [1,100], "
+                      "R~U(.01,.03), f~N(0,1), g=1",
+}
+
+
+def instances(workload: str, rank: int, count: int):
+    return [mdgen.workload_instance(workload, rank * count + i) for i in range(count)]
 
 
 class ClockSampler:
@@ -123,12 +130,12 @@ def reference_arm(args):
         return
     from paper_2505_08491_gb300.weights import default_network_params
     params = default_network_params()
-    insts = instances(0, COUNT)
+    insts = instances(args.workload, 0, args.count)
     for w in range(args.warmup):
-        oracle_solve_seconds(insts[w % COUNT], params)
+        oracle_solve_seconds(insts[w % len(insts)], params)
     ts, its = [], []
     for k in range(args.steps):
-        t, it, rel, done = oracle_solve_seconds(insts[(args.warmup + k) % COUNT], params)
+        t, it, rel, done = oracle_solve_seconds(insts[(args.warmup + k) % len(insts)], params)
         ts.append(t)
         its.append(it)
     total = sum(ts)
@@ -138,7 +145,8 @@ def reference_arm(args):
             "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: one instance per step (N=32, 15-segment tree), FGMRES(30)+network, tol 1e-8"},
+            "config": {"workload": f"{args.workload}: one instance per step ({WORKLOAD_TEXT[args.workload]}), "
+                                   "FGMRES(30)+network, tol 1e-8"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full solves (iterations {its})"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -151,12 +159,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--count", type=int, default=COUNT)
+    ap.add_argument("--count", type=int, default=None, help="instances per GPU (default 100, or 256 for batch256_mixed)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.count is None:
+        args.count = 256 if args.workload == "batch256_mixed" else COUNT
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -178,7 +189,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    insts = instances(rank, args.count)
+    insts = instances(args.workload, rank, args.count)
     ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
     params = default_network_params()
     net = Network(params)
@@ -214,6 +225,7 @@ def main():
         total_ms += e0.elapsed_time(e1)
         its_all.append(its)
         rel_all.append(max(rels))
+        lat = B.times()
         if not ok:
             raise SystemExit(f"solve did not converge: max relres {max(rels):.3e}")
     barrier()
@@ -278,6 +290,7 @@ def main():
 
     pk = peaks()
     launches = stats["conv_hidden_launches"]
+    nodes_total = sum(op.n3 for op in ops)
     flops = stats["precond_nodes"] * HIDDEN_FLOP_PER_NODE
     conv_s = stats["conv_hidden_ms"] / 1e3
     achieved = flops / conv_s / 1e12 if conv_s > 0 else 0.0
@@ -302,13 +315,16 @@ def main():
             "ms_per_step": ms_per_step, "s_per_solve": ms_per_step / 1e3 / args.count,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {args.count} seeded binary trees (15 segments, 8 el/seg), N=32, "
-                                   "beta=1, f~N(0,1), g=1; one batched FGMRES(30) solve per step, BF16 network, "
-                                   "tol 1e-8 (true FP64 residual)", "instances_per_gpu": args.count,
+            "config": {"workload": f"{args.workload}: {args.count} {WORKLOAD_TEXT[args.workload]}; one batched "
+                                   "FGMRES(30) solve per step, BF16 network, tol 1e-8 (true FP64 residual)",
+                       "instances_per_gpu": args.count, "grid_nodes_per_gpu": nodes_total,
                        "l2": "working set > L2, 256 MB flush between steps", "precision":
                        "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"},
             "iterations": {"mean": float(np.mean(its_all[-1])), "max": int(np.max(its_all[-1]))},
+            "instance_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                                   "note": "device globaltimer from solve start to each instance's convergence"},
             "max_relres": float(max(rel_all)),
+            "jacobi_fallback_instances": int(stats["fallback_instances"]) // args.steps,
             "jacobi_cg": cg,
             "roofline": roofline, "time_breakdown_ms": breakdown,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(b_all.numel() * 8),

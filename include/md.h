@@ -187,6 +187,10 @@ md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, fl
  *   cnn != NULL: flexible GMRES(restart) (Section 4, Saad 1993), right-
  *     preconditioned by md_precondition; Krylov vectors FP32, Hessenberg and
  *     Givens in FP64, and at every restart x += Z y and r = b - A x in FP64.
+ *     Safeguard (not in the paper): an instance whose network gives no
+ *     usable direction, a non-finite one, or a restart cycle of 10 or more
+ *     iterations that does not halve the true residual continues with the
+ *     Jacobi preconditioner (counted in md_batch_stats_t.fallback_instances).
  *   cnn == NULL: conjugate gradients with the Jacobi preconditioner in FP64.
  * b: device FP64 (n); x: device FP64 (n), in: initial guess, out: solution.
  * maxit bounds the total iterations.  *iters and *relres (host) receive the
@@ -205,7 +209,9 @@ typedef enum {
  * all instances (the ensembled stacking of Section 5.7), every restart cycle
  * replayed as one CUDA graph; instances stop independently on their own
  * convergence.  Vectors of the batch are concatenated: instance i occupies
- * [offset[i], offset[i] + n_i) of a batched vector. */
+ * [offset[i], offset[i] + n_i) of a batched vector.
+ * The batch borrows ops and cnn: they must not be destroyed before the
+ * batch (its captured graph reads their device buffers at every solve). */
 md_status md_batch_create(int n_ops, const md_op* const* ops, const md_cnn* cnn, md_solver solver,
                           int restart, md_batch** out);
 void md_batch_destroy(md_batch* b);
@@ -229,13 +235,14 @@ typedef struct {
     long long kernel_launches;   /* kernels launched by md_batch_solve calls */
     long long cycles;            /* restart cycles (CG: chunks of 25 iterations) */
     long long iterations;        /* sum over instances of Krylov iterations */
-    long long precond_nodes;     /* sum over instances of iterations x grid nodes */
+    long long precond_nodes;     /* sum over instances of network-preconditioned iterations x grid nodes */
     double prec_ms;              /* preconditioner applications (iteration slots) */
     double conv_hidden_ms;       /* the 4 hidden convolution launches per application */
     long long conv_hidden_launches;
     double apply_ms;             /* A z in FP32 */
     double arnoldi_ms;           /* dots, updates, Givens */
     double restart_ms;           /* least squares, x update, FP64 residual */
+    long long fallback_instances; /* network solves whose instance switched to Jacobi */
 } md_batch_stats_t;
 md_status md_batch_set_profiling(md_batch* b, int enable);
 md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);

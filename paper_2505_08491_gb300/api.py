@@ -246,7 +246,9 @@ class Batch:
 
     def __init__(self, ops: list[Operator], solver: str = "fgmres_cnn", net: Network | None = None, restart: int = 30):
         lib = L.load()
+        # the batch borrows the operators and the network: keep them alive
         self.ops = list(ops)
+        self.net = net
         arr = (C.c_void_p * len(ops))(*[o.handle.value for o in ops])
         h = C.c_void_p()
         L.check(lib.md_batch_create(len(ops), arr, net.handle if net is not None else None, self.SOLVERS[solver],

@@ -6,6 +6,7 @@
 // 'same' padding (the convolution of Section 4.2 in cross-correlation
 // orientation), then GELU(x) = x Phi(x) for l < 5.  Weights and hidden
 // activations are BF16, accumulation FP32.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,6 +36,11 @@ uint64_t fnv1a(const void* p, size_t n) {
 }  // namespace
 
 // ---- parameters --------------------------------------------------------------
+unsigned long long md_next_cnn_uid() {
+    static std::atomic<unsigned long long> next{1};
+    return next.fetch_add(1);
+}
+
 md_status cnn_upload(md_cnn* c) {
     // packed weights per layer: [tap][cin_pad][cout] BF16 (RN), biases FP32
     std::vector<__nv_bfloat16> w;

@@ -189,6 +189,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     float* xch = reinterpret_cast<float*>(bars + 2 * NS + 8);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // inside a solve most late iteration slots have no active instance: leave
+    // before any set-up when none of this CTA's units runs (uniform decision)
+    if (a.io.st) {
+        bool any = false;
+        for (int un = blockIdx.x; un < a.nunits && !any; un += gridDim.x) any = cnn_runs(a.io.st, a.units[un].inst);
+        if (!any) return;
+    }
+
     for (int i = threadIdx.x; i < WIMG / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(a.wimg)[i];
     if (threadIdx.x == 0) {

@@ -102,7 +102,12 @@ struct md_op {
 
 struct CnnLayer { int cin, cout, cin_pad; };
 
+unsigned long long md_next_cnn_uid();  // process-wide counter (md_cnn.cu)
+
 struct md_cnn {
+    // identity of this network for captured graphs: a handle address can be
+    // reused by a later network, a uid is never reused
+    unsigned long long uid = md_next_cnn_uid();
     std::vector<float> host;     // FP32 master copy (MD_CNN_NPARAMS)
     __nv_bfloat16* w = nullptr;  // device packed weights, per layer [tap][cout][cin_pad]
     float* b = nullptr;          // device biases, per layer [cout]
@@ -131,8 +136,20 @@ struct KState {
     double tol, inner_tol;
     double rho, alpha_cg, pq;            // CG scalars
     unsigned long long t_start, t_done;  // globaltimer stamps
+    double relres_prev;                  // true relative residual at the previous restart
     int j, m, active, converged, iters, reorth, nan_seen, fallback, maxit, cycle_iters, stalls;
+    int fb_iter;                         // iteration at which the Jacobi fallback began
     unsigned int counter[8];             // last-block counters per reduction kernel
+};
+
+// Per-instance results written when an instance finishes: iterations,
+// iterations preconditioned by the network (all of them unless the instance
+// fell back to Jacobi), true relative residual, seconds from solve start.
+struct ResOut {
+    int* iters;
+    int* net_iters;
+    double* relres;
+    double* time;
 };
 
 // An instance runs the network in this launch: inside its cycle and not

@@ -24,6 +24,7 @@
 #include "md_common.cuh"
 
 #define INNER_REL 1e-5
+#define STAGNATION_MIN_ITERS 10
 
 struct md_batch {
     int ninst = 0;
@@ -43,14 +44,12 @@ struct md_batch {
     KState* st = nullptr;
     double* part = nullptr;
     int* ndone = nullptr;
-    int* res_iters = nullptr;
-    double* res_relres = nullptr;
-    double* res_time = nullptr;
+    ResOut res{};
     int max_n1 = 0;
     CnnWork* cw = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
-    const md_cnn* graph_cnn = nullptr;
+    unsigned long long graph_cnn_uid = 0;  // network the graph was captured with (0: none)
     bool graph_prof = false;
     int graph_engine = -1;
     long long graph_kernels = 0;
@@ -115,6 +114,7 @@ __global__ void k_init_state(KState* st, int ninst, double tol, int maxit, int* 
     KState& S = st[i];
     S.tol = tol; S.maxit = maxit; S.iters = 0; S.converged = 0; S.active = 0; S.j = 0; S.m = 0;
     S.reorth = 0; S.nan_seen = 0; S.fallback = 0; S.bnorm = 0; S.relres = 1; S.cycle_iters = -1; S.stalls = 0;
+    S.fb_iter = 0; S.relres_prev = 1.0;
     S.inner_tol = INNER_REL;
     S.t_start = globaltimer();
     S.t_done = 0;
@@ -135,14 +135,23 @@ __global__ void __launch_bounds__(MD_TB) k_norm_b(const Seg* __restrict__ seg, c
     if (flag == 1.0 && threadIdx.x == 0) st[sg.inst].bnorm = sqrt(sh[0]);
 }
 
-__device__ inline void mark_done(KState& S, int* ndone, int* res_iters, double* res_relres, double* res_time, int inst) {
+// the instance's preconditioner becomes Jacobi for the rest of its solve
+__device__ inline void set_fallback(KState& S) {
+    if (!S.fallback) {
+        S.fallback = 1;
+        S.fb_iter = S.iters;
+    }
+}
+
+__device__ inline void mark_done(KState& S, int* ndone, ResOut res, int inst) {
     S.active = 0;
     S.converged = S.relres <= S.tol ? 1 : 0;
     S.t_done = globaltimer();
     S.m = 0;
-    res_iters[inst] = S.iters;
-    res_relres[inst] = S.relres;
-    res_time[inst] = (double)(S.t_done - S.t_start) * 1e-9;
+    res.iters[inst] = S.iters;
+    res.net_iters[inst] = S.fallback ? S.fb_iter : S.iters;
+    res.relres[inst] = S.relres;
+    res.time[inst] = (double)(S.t_done - S.t_start) * 1e-9;
     atomicAdd(ndone, 1);
 }
 
@@ -150,8 +159,7 @@ __device__ inline void mark_done(KState& S, int* ndone, int* res_iters, double* 
 __global__ void __launch_bounds__(MD_TB) k_resid(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                  const long long* __restrict__ off, const InstDesc* __restrict__ D,
                                                  const double* __restrict__ b, const double* __restrict__ y, float* V0,
-                                                 KState* st, double* part, int* ndone, int* res_iters,
-                                                 double* res_relres, double* res_time) {
+                                                 KState* st, double* part, int* ndone, ResOut res, int k) {
     __shared__ double sh[32 * 4];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
@@ -178,9 +186,17 @@ __global__ void __launch_bounds__(MD_TB) k_resid(const Seg* __restrict__ seg, co
         // stalls in a row, or a non-finite residual, end the instance unconverged
         if (S.cycle_iters == 0) S.stalls += 1;
         else if (S.cycle_iters > 0) S.stalls = 0;
+        // a cycle that did not halve the true residual -- a full one of
+        // STAGNATION_MIN_ITERS or more iterations, or one whose estimate
+        // claimed convergence early -- shows that the network does not
+        // precondition this instance, which continues under Jacobi
+        const bool stagnated = S.cycle_iters > 0 && (S.cycle_iters >= STAGNATION_MIN_ITERS || S.cycle_iters < k) &&
+                               S.relres > 0.5 * S.relres_prev;
+        S.relres_prev = S.relres;
         if (S.relres <= S.tol || S.iters >= S.maxit || S.stalls >= 3 || !isfinite(S.relres)) {
-            mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
+            mark_done(S, ndone, res, sg.inst);
         } else {
+            if (stagnated) set_fallback(S);
             S.active = 1;
             S.g[0] = S.beta;
             S.sig[0] = 1.0 / sqrt(sh[1]);
@@ -301,7 +317,7 @@ __global__ void k_givens(KState* st, int ninst, int j, int k) {
         // rest of this instance's solve
         S.active = 0;
         S.nan_seen |= !isfinite(den);
-        if (j == 0 || !isfinite(den)) S.fallback = 1;
+        if (j == 0 || !isfinite(den)) set_fallback(S);
         return;
     }
     S.cs[j] = H[j] / den;
@@ -459,7 +475,7 @@ __global__ void __launch_bounds__(MD_TB) k_cg_init(const Seg* __restrict__ seg, 
                                                    const long long* __restrict__ off, const InstDesc* __restrict__ D,
                                                    const double* __restrict__ b, const double* __restrict__ y,
                                                    double* r, double* p, KState* st, double* part, int* ndone,
-                                                   int* res_iters, double* res_relres, double* res_time) {
+                                                   ResOut res) {
     __shared__ double sh[32 * 4];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
@@ -479,7 +495,7 @@ __global__ void __launch_bounds__(MD_TB) k_cg_init(const Seg* __restrict__ seg, 
     if (flag == 1.0 && threadIdx.x == 0) {
         S.rho = sh[0];
         S.relres = S.bnorm > 0 ? sqrt(sh[1]) / S.bnorm : 0.0;
-        if (S.relres <= S.tol || S.iters >= S.maxit) mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
+        if (S.relres <= S.tol || S.iters >= S.maxit) mark_done(S, ndone, res, sg.inst);
         else S.active = 1;
     }
 }
@@ -506,7 +522,7 @@ __global__ void __launch_bounds__(MD_TB) k_cg_xr(const Seg* __restrict__ seg, co
                                                  const long long* __restrict__ off, const InstDesc* __restrict__ D,
                                                  double* x, double* r, const double* __restrict__ p,
                                                  const double* __restrict__ q, KState* st, double* part, int* ndone,
-                                                 int* res_iters, double* res_relres, double* res_time) {
+                                                 ResOut res) {
     __shared__ double sh[32 * 4];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
@@ -553,7 +569,7 @@ __global__ void __launch_bounds__(MD_TB) k_cg_p(const Seg* __restrict__ seg, con
 __global__ void __launch_bounds__(MD_TB) k_cg_final(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                     const long long* __restrict__ off, const double* __restrict__ b,
                                                     const double* __restrict__ y, KState* st, double* part, int* ndone,
-                                                    int* res_iters, double* res_relres, double* res_time) {
+                                                    ResOut res) {
     __shared__ double sh[32 * 4];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
@@ -569,7 +585,7 @@ __global__ void __launch_bounds__(MD_TB) k_cg_final(const Seg* __restrict__ seg,
     if (flag == 1.0 && threadIdx.x == 0) {
         S.relres = S.bnorm > 0 ? sqrt(sh[0]) / S.bnorm : 0.0;
         S.reorth = 0;
-        mark_done(S, ndone, res_iters, res_relres, res_time, sg.inst);
+        mark_done(S, ndone, res, sg.inst);
     }
 }
 
@@ -624,7 +640,7 @@ static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
     MD_CHECK_LAUNCH();
     MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
     k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st, B->part,
-                                             B->ndone, B->res_iters, B->res_relres, B->res_time);
+                                             B->ndone, B->res, B->k);
     MD_CHECK_LAUNCH();
     rec(ev_restart(B, 1), s);
     return MD_OK;
@@ -637,20 +653,21 @@ static md_status launch_cycle_cg(md_batch* B, cudaStream_t s) {
         MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->p64, B->off, B->y64, s, B->st, 1));
         k_cg_alpha<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->p64, B->y64, B->st, B->part);
         k_cg_xr<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->x, B->r64, B->p64, B->y64,
-                                                 B->st, B->part, B->ndone, B->res_iters, B->res_relres, B->res_time);
+                                                 B->st, B->part, B->ndone, B->res);
         k_cg_p<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, B->r64, B->p64, B->st);
         MD_CHECK_LAUNCH();
     }
     MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
     k_cg_final<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->b, B->y64, B->st, B->part, B->ndone,
-                                                B->res_iters, B->res_relres, B->res_time);
+                                                B->res);
     MD_CHECK_LAUNCH();
     return MD_OK;
 }
 
 static md_status build_graph(md_batch* B) {
     const int engine = B->cnn ? B->cnn->engine : 0;
-    if (B->graph && B->graph_cnn == B->cnn && B->graph_prof == B->profiling && B->graph_engine == engine) return MD_OK;
+    const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
+    if (B->graph && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine) return MD_OK;
     if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
     if (B->profiling && B->ev.empty()) {
         B->ev.resize((size_t)B->k * EV_PER_J + 2);
@@ -674,7 +691,7 @@ static md_status build_graph(md_batch* B) {
     e = cudaGraphInstantiate(&B->graph, g, 0);
     cudaGraphDestroy(g);
     MD_CUDA(e);
-    B->graph_cnn = B->cnn;
+    B->graph_cnn_uid = uid;
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
     return MD_OK;
@@ -748,9 +765,10 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
     chk(dev_alloc(&B->allocs, &B->st, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->part, (size_t)std::max(B->tabs.vec.nblocks, 1) * MD_MAXR));
     chk(dev_alloc(&B->allocs, &B->ndone, 1));
-    chk(dev_alloc(&B->allocs, &B->res_iters, (size_t)n_ops));
-    chk(dev_alloc(&B->allocs, &B->res_relres, (size_t)n_ops));
-    chk(dev_alloc(&B->allocs, &B->res_time, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->res.iters, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->res.net_iters, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->res.relres, (size_t)n_ops));
+    chk(dev_alloc(&B->allocs, &B->res.time, (size_t)n_ops));
     if (st == MD_OK && solver == MD_SOLVER_FGMRES_CNN) {
         chk(cnn_work_create(Ns, &B->cw));
         const size_t smem = (size_t)B->max_n1 * 20;
@@ -797,10 +815,10 @@ static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
     MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
     if (B->solver == MD_SOLVER_CG_JACOBI) {
         k_cg_init<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->r64, B->p64,
-                                                   B->st, B->part, B->ndone, B->res_iters, B->res_relres, B->res_time);
+                                                   B->st, B->part, B->ndone, B->res);
     } else {
         k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st,
-                                                 B->part, B->ndone, B->res_iters, B->res_relres, B->res_time);
+                                                 B->part, B->ndone, B->res, B->k);
     }
     MD_CHECK_LAUNCH();
     MD_TRY(build_graph(B));
@@ -834,12 +852,13 @@ extern "C" md_status md_batch_solve(md_batch* B, const double* b_all, double* x_
     MD_CUDA(cudaMemcpyAsync(B->x, x_all, sizeof(double) * B->total, cudaMemcpyDeviceToDevice, s));
     MD_TRY(batch_run(B, tol, maxit, s));
     MD_CUDA(cudaMemcpyAsync(x_all, B->x, sizeof(double) * B->total, cudaMemcpyDeviceToDevice, s));
-    std::vector<int> it(B->ninst);
+    std::vector<int> it(B->ninst), nit(B->ninst);
     std::vector<double> rr(B->ninst);
     B->last_times.resize(B->ninst);
-    MD_CUDA(cudaMemcpyAsync(it.data(), B->res_iters, sizeof(int) * B->ninst, cudaMemcpyDeviceToHost, s));
-    MD_CUDA(cudaMemcpyAsync(rr.data(), B->res_relres, sizeof(double) * B->ninst, cudaMemcpyDeviceToHost, s));
-    MD_CUDA(cudaMemcpyAsync(B->last_times.data(), B->res_time, sizeof(double) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(it.data(), B->res.iters, sizeof(int) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(nit.data(), B->res.net_iters, sizeof(int) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(rr.data(), B->res.relres, sizeof(double) * B->ninst, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(B->last_times.data(), B->res.time, sizeof(double) * B->ninst, cudaMemcpyDeviceToHost, s));
     MD_CUDA(cudaStreamSynchronize(s));
     bool all = true;
     for (int i = 0; i < B->ninst; ++i) {
@@ -847,7 +866,10 @@ extern "C" md_status md_batch_solve(md_batch* B, const double* b_all, double* x_
         if (relres) relres[i] = rr[i];
         if (!(rr[i] <= tol)) all = false;
         B->stats.iterations += it[i];
-        B->stats.precond_nodes += (long long)it[i] * B->hdesc[i].n3;
+        if (B->solver == MD_SOLVER_FGMRES_CNN) {
+            B->stats.precond_nodes += (long long)nit[i] * B->hdesc[i].n3;
+            B->stats.fallback_instances += nit[i] < it[i] ? 1 : 0;
+        }
     }
     return all ? MD_OK : MD_NOT_CONVERGED;
 }
@@ -920,8 +942,8 @@ extern "C" md_status md_solve_batched(int n, const md_op* const* ops, const md_c
         }
         std::vector<int> it(n);
         std::vector<double> rr(n);
-        cudaMemcpyAsync(it.data(), B->res_iters, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(rr.data(), B->res_relres, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(it.data(), B->res.iters, sizeof(int) * n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(rr.data(), B->res.relres, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess && st == MD_OK) st = md_cuda_status(e, "md_solve_batched", __FILE__, __LINE__);
         bool all = true;

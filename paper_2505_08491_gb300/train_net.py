@@ -1,8 +1,9 @@
 """Train the preconditioner network and save it (weights/cnn_trained.bin).
 
 Training set (the unsupervised residual set of Section 4.1, on seeded random
-trees): graphs of 3-31 segments (binary trees of depth 2-5) on grids N = 16
-and 32, beta = 1.  Per graph 8 right-hand sides of the block preconditioner:
+trees): workload train_trees = graphs of 3-31 segments (binary trees of depth
+2-5) on grids N = 16 and 32, beta = 1; train_trees_wide = 3-127 segments,
+radius U(0.005, 0.03), beta log-uniform in [1, 100].  Per graph 8 right-hand sides of the block preconditioner:
 4 random vectors (N(0,1) on every unknown, zero on Dirichlet nodes; the
 high-frequency augmentation of Section 4.1.2) and the residuals of the
 Jacobi-preconditioned FGMRES(30) solve of the graph's own problem after 5,
@@ -38,8 +39,8 @@ def interior_mask(N):
     return ~(b[:, None, None] | b[None, :, None] | b[None, None, :]).ravel()
 
 
-def build_set(n_graphs: int, first: int = 0):
-    insts = [mdgen.workload_instance("train_trees", first + i) for i in range(n_graphs)]
+def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees"):
+    insts = [mdgen.workload_instance(workload, first + i) for i in range(n_graphs)]
     ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
     samples, sample_op = [], []
     by_N = {}
@@ -82,9 +83,10 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=TRAINED)
     ap.add_argument("--init", default=None, help="start from this network file")
+    ap.add_argument("--workload", default="train_trees", choices=["train_trees", "train_trees_wide"])
     args = ap.parse_args()
     t0 = time.time()
-    ops, samples, sample_op = build_set(args.graphs)
+    ops, samples, sample_op = build_set(args.graphs, workload=args.workload)
     torch.cuda.synchronize()
     t1 = time.time()
     net = Network.load(args.init) if args.init else Network(random_params(args.seed))
@@ -93,7 +95,7 @@ def main():
     t2 = time.time()
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     net.save(args.out)
-    print(json.dumps({"graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
+    print(json.dumps({"workload": args.workload, "graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
                       "set_seconds": t1 - t0, "train_seconds": t2 - t1, "loss": hist}))
 
 

@@ -32,12 +32,14 @@ def setup():
     return insts, ops, torch.cat(bs)
 
 
-def mean_iters(ops, b_all, solver, params):
+def mean_iters(ops, b_all, solver, params, stats=None):
     from paper_2505_08491_gb300 import Batch, Network
     net = Network(params) if params is not None else None
     B = Batch(ops, solver, net, restart=30)
     x = torch.zeros_like(b_all)
     its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=2000)
+    if stats is not None:
+        stats.update(B.stats())
     B.close()
     return float(np.mean(its)), ok, x
 
@@ -45,7 +47,10 @@ def mean_iters(ops, b_all, solver, params):
 def test_trained_network_gain(setup):
     from paper_2505_08491_gb300.weights import default_network_params, identity_pair_params, random_params
     insts, ops, b_all = setup
-    trained, ok_t, _ = mean_iters(ops, b_all, "fgmres_cnn", default_network_params())
+    st = {}
+    trained, ok_t, _ = mean_iters(ops, b_all, "fgmres_cnn", default_network_params(), st)
+    # the stagnation safeguard stays off where the network works
+    assert st["fallback_instances"] == 0
     identity, ok_i, _ = mean_iters(ops, b_all, "fgmres_cnn", identity_pair_params())
     jacobi, ok_j, _ = mean_iters(ops, b_all, "fgmres_jacobi", None)
     untrained, ok_u, _ = mean_iters(ops, b_all, "fgmres_cnn", random_params(0))

@@ -1,5 +1,6 @@
 """Failure handling on the GPU with failures made on the host: a network
-whose activations overflow (non-finite preconditioner output) switches the
+whose activations overflow (non-finite preconditioner output), or one whose
+output does not reduce the residual (a constant field), switches the
 affected instances to the Jacobi fallback, and a useless network does not
 keep a batch from terminating."""
 import numpy as np
@@ -41,7 +42,43 @@ def test_useless_network_terminates_on_mixed_batch():
         f = mdgen.interior_source(w["N"], w["f_seed"])
         bs.append(op.rhs(torch.from_numpy(f).cuda(), w["g"]))
     b_all = torch.cat(bs)
-    B = Batch(ops, "fgmres_cnn", Network(random_params(0)), restart=30)
+    net = Network(random_params(0))
+    B = Batch(ops, "fgmres_cnn", net, restart=30)
     x = torch.zeros_like(b_all)
     its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=120)
     assert len(its) == 6 and all(i <= 120 for i in its)
+    # given the iterations, every instance converges (under Jacobi where the
+    # network stagnates)
+    x.zero_()
+    its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=4000)
+    assert ok, (its, rels)
+
+
+def _constant_network():
+    """All weights zero and the last bias 1: N(X) = 1 on every node whatever
+    the input, a preconditioner that gives the same direction every
+    iteration."""
+    from paper_2505_08491_gb300 import Network
+    from paper_2505_08491_gb300.weights import CHANNELS, layers_to_flat
+    layers = [(np.zeros((co, ci, 3, 3, 3)), np.zeros(co)) for ci, co in zip(CHANNELS[:-1], CHANNELS[1:])]
+    layers[-1] = (layers[-1][0], np.ones(1))
+    return Network(layers_to_flat(layers))
+
+
+def test_stagnating_network_falls_back_to_jacobi():
+    from paper_2505_08491_gb300 import Batch, Operator
+    cases = instance_cases()[:3]
+    probs = [fem.Problem(N, g, beta) for _, N, g, beta, _ in cases]
+    ops = [Operator(N, g, beta) for _, N, g, beta, _ in cases]
+    b_np = [p.rhs(p.source(c[4]), 1.0) for p, c in zip(probs, cases)]
+    b_all = torch.from_numpy(np.concatenate(b_np)).cuda()
+    net = _constant_network()
+    B = Batch(ops, "fgmres_cnn", net, restart=30)
+    x = torch.zeros_like(b_all)
+    its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=5000)
+    assert ok, (its, rels)
+    assert B.stats()["fallback_instances"] == len(ops)
+    xs = x.cpu().numpy()
+    for i, p in enumerate(probs):
+        xi = xs[B.offsets[i]:B.offsets[i + 1]]
+        assert np.linalg.norm(b_np[i] - p.A @ xi) <= 1.01e-8 * np.linalg.norm(b_np[i])
