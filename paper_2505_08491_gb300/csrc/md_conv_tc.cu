@@ -57,11 +57,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// try_wait suspends the thread until the phase completes or the hint
+// (100 us) elapses, so waiting warps do not take issue slots from working ones
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 100000;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -73,7 +75,7 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
-        for (int i = 0; i < 64; ++i)
+        for (int i = 0; i < 4; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (*(volatile int*)err) return false;
         if (globaltimer() - t0 > 2000000000ULL) {
@@ -81,6 +83,28 @@ __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
             return false;
         }
     }
+}
+
+// Hardware named barriers for the 4 epilogue warps of one channel group
+// (ids 1..TC_EPI_GROUPS; id 0 is __syncthreads).  Every warp of a group runs
+// the same sequence of them: the units, planes and instance states they walk
+// are identical, and the only early exit is taken by all four together after
+// nbar_and.
+__device__ __forceinline__ void nbar_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// barrier that also returns the AND of `p` over the participating threads
+__device__ __forceinline__ bool nbar_and(int id, int nthreads, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, q;\n\t"
+        "setp.ne.u32 a, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, a;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -183,7 +207,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     uint64_t* empty = bars + NS;       // [NS]
     uint64_t* tfull = bars + 2 * NS;   // [2]
     uint64_t* tempty = bars + 2 * NS + 2;
-    uint64_t* xbar = bars + 2 * NS + 4;  // [2] epilogue exchange, double-buffered
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6);
     // warp-boundary exchange of the epilogue: [buffer][quarter][half][2 x 16]
     float* xch = reinterpret_cast<float*>(bars + 2 * NS + 8);
@@ -207,7 +230,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], TC_EPI_WARPS);
-            mbar_init(&xbar[i], TC_EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -355,7 +377,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             __nv_bfloat16* zsU = (KIND != 2 && a.zsave) ? a.zsave + a.out_off[U.inst] : nullptr;
             for (int z = U.z0; z < U.z1; ++z, ++it) {
                 const int bsel = it & 1;
-                if (!mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err)) { ok = false; break; }
+                // every warp waits for the accumulator itself; the group leaves
+                // together if any of its warps gave up
+                ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err));
+                if (!ok) break;
                 tc_fence_after();
 #pragma unroll
                 for (int ut = 0; ut < TPS; ++ut) {
@@ -375,31 +400,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp);
                         tmem_wait_ld();
                     }
-                    // warp-boundary values: lane 31's dx=-1 group, lane 0's dx=+1 group
-                    // (bounded mbarrier handshake among the epilogue warps; buffer
-                    // xcnt & 1 is rewritten only after every warp passed the next one)
+                    // warp-boundary values: lane 31's dx=-1 group, lane 0's dx=+1 group,
+                    // exchanged among the 4 warps (lane quarters) of this channel
+                    // group through a named barrier; buffer xcnt & 1 is rewritten
+                    // only after every warp of the group passed the next barrier
                     const int xbuf = xcnt & 1;
                     float* xb = xch + (size_t)xbuf * (4 * TC_EPI_GROUPS * 2 * TC_EPI_CH);
                     float* mine = xb + (q * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
-                    if (lane == 31)
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) mine[c] = dm[c];
-                    if (lane == 0)
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) mine[TC_EPI_CH + c] = dp[c];
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&xbar[xbuf]);
-                    if (!mbar_wait(&xbar[xbuf], (xcnt >> 1) & 1, a.err)) { ok = false; break; }
+                    if constexpr (KIND == 2) {
+                        if (lane == 31) mine[0] = dm[0];
+                        if (lane == 0) mine[TC_EPI_CH] = dp[0];
+                    } else {
+                        static_assert(CH == 8, "the exchange moves 8 channels as two float4");
+                        float4* m4 = reinterpret_cast<float4*>(mine);
+                        if (lane == 31) {
+                            m4[0] = make_float4(dm[0], dm[1], dm[2], dm[3]);
+                            m4[1] = make_float4(dm[4], dm[5], dm[6], dm[7]);
+                        }
+                        if (lane == 0) {
+                            m4[2] = make_float4(dp[0], dp[1], dp[2], dp[3]);
+                            m4[3] = make_float4(dp[4], dp[5], dp[6], dp[7]);
+                        }
+                    }
+                    nbar_sync(1 + cg, 4 * 32);
                     ++xcnt;
                     const float* prev = xb + (((q + 3) & 3) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
                     const float* next = xb + (((q + 1) & 3) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
+                    // lanes 0 and 31 take their missing neighbour from the adjacent quarter
+                    float pv[CH], nx[CH];
+                    if constexpr (KIND == 2) {
+                        pv[0] = prev[0];
+                        nx[0] = next[0];
+                    } else {
+                        const float4 p0 = reinterpret_cast<const float4*>(prev)[0], p1 = reinterpret_cast<const float4*>(prev)[1];
+                        const float4 n0 = reinterpret_cast<const float4*>(next)[0], n1 = reinterpret_cast<const float4*>(next)[1];
+                        pv[0] = p0.x; pv[1] = p0.y; pv[2] = p0.z; pv[3] = p0.w;
+                        pv[4] = p1.x; pv[5] = p1.y; pv[6] = p1.z; pv[7] = p1.w;
+                        nx[0] = n0.x; nx[1] = n0.y; nx[2] = n0.z; nx[3] = n0.w;
+                        nx[4] = n1.x; nx[5] = n1.y; nx[6] = n1.z; nx[7] = n1.w;
+                    }
                     float o[CH];
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
                         float up = __shfl_up_sync(0xffffffffu, dm[c], 1);    // D[i-1][dx=-1]
                         float dn = __shfl_down_sync(0xffffffffu, dp[c], 1);  // D[i+1][dx=+1]
-                        if (lane == 0) up = prev[c];
-                        if (lane == 31) dn = next[c];
+                        if (lane == 0) up = pv[c];
+                        if (lane == 31) dn = nx[c];
                         o[c] = up + dc[c] + dn + bias[c];
                     }
                     if (!val[ut]) continue;
@@ -411,7 +457,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                             if (zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
                             float gl[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) gl[e] = gelu_fast(o[c8 * 8 + e]);
+                            for (int e = 0; e < 8; e += 2) {
+                                gl[e] = o[c8 * 8 + e];
+                                gl[e + 1] = o[c8 * 8 + e + 1];
+                                gelu_fast2(gl[e], gl[e + 1]);
+                            }
                             *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
                         }
                     } else {
