@@ -209,6 +209,16 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     w->W = tc_window_rows(w->tps, pd_max);
     w->NS = tc_ring_slots(w->W);
     if (w->NS == 0) { delete w; md_set_error("grid too large for the tensor-core convolution windows"); return MD_ERR_ARG; }
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            w->nsm = nsm;
+    }
+    // columns of tps*126 in-plane rows, each walked over the N+1 padded planes
+    // [1, N+2) that hold grid nodes
+    struct Column { int inst, s0, nz; };
+    std::vector<Column> cols;
+    long long steps = 0;
     const int CH = 512;
     for (int i = 0; i < w->ninst; ++i) {
         long long Pd = Ns[i] + 3, P = Pd * Pd * Pd;
@@ -222,29 +232,41 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
         ranges.push_back({(int)segs.size(), 0});
         for (int b = 0; b < n3; b += CH) segs.push_back({i, 0, b, std::min(n3, b + CH)});
         ranges.back().count = (int)segs.size() - ranges.back().first;
-        // columns of tps*126 in-plane rows, walked over the planes holding grid
-        // nodes (padded z in [1, N+2)) in chunks of at most 17 planes
-        const int nz = Ns[i] + 1, nch = (nz + 16) / 17;
-        for (long long s0 = 0; s0 < Pd * Pd; s0 += 126 * w->tps)
-            for (int c = 0; c < nch; ++c) {
-                const int z0 = 1 + (int)((long long)nz * c / nch), z1 = 1 + (int)((long long)nz * (c + 1) / nch);
-                units.push_back({i, (int)s0, z0, z1});
+        for (long long s0 = 0; s0 < Pd * Pd; s0 += 126 * w->tps) {
+            cols.push_back({i, (int)s0, Ns[i] + 1});
+            steps += Ns[i] + 1;
+        }
+    }
+    // one CTA per SM, each given a contiguous run of plane steps of equal
+    // length (columns split between CTAs where a run ends)
+    std::vector<int> ubeg;
+    w->ngroups = (int)std::max(1LL, std::min<long long>(w->nsm, steps));
+    {
+        size_t ci = 0;
+        int zdone = 0;
+        ubeg.push_back(0);
+        for (int b = 0; b < w->ngroups; ++b) {
+            long long need = steps * (b + 1) / w->ngroups - steps * b / w->ngroups;
+            while (need > 0 && ci < cols.size()) {
+                const int take = (int)std::min<long long>(need, cols[ci].nz - zdone);
+                units.push_back({cols[ci].inst, cols[ci].s0, 1 + zdone, 1 + zdone + take});
+                zdone += take;
+                need -= take;
+                if (zdone == cols[ci].nz) { ++ci; zdone = 0; }
             }
+            ubeg.push_back((int)units.size());
+        }
     }
     rx += CNN_MARGIN_ROWS;
     rab += CNN_MARGIN_ROWS;
     w->total_nodes = nodes;
     w->nunits = (int)units.size();
-    {
-        int dev = 0, nsm = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
-            w->nsm = nsm;
-    }
     md_status st = MD_OK;
     auto chk = [&](md_status s) { if (st == MD_OK) st = s; };
     chk(tc_prepare(w->W, w->tps));
     chk(dev_upload(&w->allocs, &w->N, Ns.data(), Ns.size()));
     chk(dev_upload(&w->allocs, &w->units, units.data(), units.size()));
+    chk(dev_upload(&w->allocs, &w->ubeg, ubeg.data(), ubeg.size()));
     chk(dev_alloc(&w->allocs, &w->err, 1));
     chk(dev_upload(&w->allocs, &w->off_x0, w->h_off_x0.data(), w->h_off_x0.size()));
     chk(dev_upload(&w->allocs, &w->off_ab, w->h_off_ab.data(), w->h_off_ab.size()));
@@ -373,10 +395,11 @@ static md_status launch_conv(const __nv_bfloat16* in, const long long* in_off, _
 
 static md_status tc_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
                                    cudaEvent_t e_hidden0, cudaEvent_t e_hidden1) {
-    const int grid = std::max(1, std::min(w->nunits, w->nsm));
+    const int grid = w->ngroups;
     TcArgs a{};
     a.Ns = w->N;
     a.units = w->units;
+    a.ubeg = w->ubeg;
     a.nunits = w->nunits;
     a.W = w->W;
     a.NS = w->NS;
@@ -414,14 +437,13 @@ md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A
         const bool last = l == MD_CNN_LAYERS - 1;
         if (c->engine == 0) {
             TcArgs a{};
-            a.Ns = w->N; a.units = w->units; a.nunits = w->nunits; a.W = w->W; a.NS = w->NS; a.err = w->err;
+            a.Ns = w->N; a.units = w->units; a.ubeg = w->ubeg; a.nunits = w->nunits; a.W = w->W; a.NS = w->NS; a.err = w->err;
             a.io = io; a.mode = CONV_RAW;
             a.in = src; a.in_off = src_off;
             a.out = last ? nullptr : A[l + 1]; a.out_off = w->off_ab;
             a.zsave = last ? nullptr : Z[l + 1];
             a.wimg = c->wmma + c->wmma_off[l]; a.bias = c->b + c->b_off[l]; a.cout = last ? 1 : 32;
-            const int grid = std::max(1, std::min(w->nunits, w->nsm));
-            MD_TRY(tc_launch(l == 0 ? 1 : (last ? 2 : 0), w->tps, a, grid, s));
+            MD_TRY(tc_launch(l == 0 ? 1 : (last ? 2 : 0), w->tps, a, w->ngroups, s));
         } else {
             const __nv_bfloat16* W = c->w + c->w_off[l];
             const float* B = c->b + c->b_off[l];

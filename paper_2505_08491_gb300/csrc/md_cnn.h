@@ -17,9 +17,11 @@ struct CnnWork {
     std::vector<int> hN;
     int* N = nullptr;              // device, per instance
     // tensor-core path: z-walking work units of tps*128 in-plane rows,
-    // window rows W, NS ring slots
+    // window rows W, NS ring slots; CTA b of a launch runs units
+    // [ubeg[b], ubeg[b+1]), ngroups CTAs with equal plane-step counts
     TcUnit* units = nullptr;
-    int nunits = 0, tps = 2, W = 0, NS = 0, nsm = 148;
+    int* ubeg = nullptr;
+    int nunits = 0, ngroups = 1, tps = 2, W = 0, NS = 0, nsm = 148;
     int* err = nullptr;            // set by a timed-out wait in a conv kernel
     __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
     __nv_bfloat16* a = nullptr;    // 4 chunks

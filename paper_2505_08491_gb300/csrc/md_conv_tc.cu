@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     // before any set-up when none of this CTA's units runs (uniform decision)
     if (a.io.st) {
         bool any = false;
-        for (int un = blockIdx.x; un < a.nunits && !any; un += gridDim.x) any = cnn_runs(a.io.st, a.units[un].inst);
+        for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && !any; ++un) any = cnn_runs(a.io.st, a.units[un].inst);
         if (!any) return;
     }
 
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         if (lane == 0) {
             int g = 0;
             bool ok = true;
-            for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
+            for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
                 const TcUnit U = a.units[un];
                 if (!cnn_runs(a.io.st, U.inst)) continue;
                 const long long Pd = a.Ns[U.inst] + 3, P = Pd * Pd * Pd;
@@ -274,72 +274,106 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int g = 0, it = 0;
+            int it = 0;
             bool ok = true;
             const uint32_t wb = smem_u32(wsm);
             const uint32_t rb0 = smem_u32(ring);
+            // Descriptors are formed once and advanced by adding 16-byte units to
+            // the start-address field (bits 0-13): a shared-memory address is
+            // below 2^18 bytes, so the sum never carries out of the field.  A
+            // single thread issues every MMA, so its instructions per MMA bound
+            // the issue rate.
             const uint64_t a_hi = (1ULL << 46) | ((uint64_t)((128 >> 4) & 0x3FFF) << 32);  // version, SBO = 128
-            for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
+            const uint64_t bd0 = sdesc(wb, NCOL * 16, 128);
+            const uint64_t a_lbo_w = (uint64_t)((uint32_t)W & 0x3FFF) << 16;  // next chunk: W rows of 16 B
+            // ring position of window g: slot g % NS and round g / NS, kept
+            // incrementally (no division by the runtime NS per step)
+            int gs = 0, gq = 0;
+            auto adv = [NS](int& s_, int& q_, int n) {
+                s_ += n;
+                while (s_ >= NS) { s_ -= NS; ++q_; }
+            };
+            for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
                 const TcUnit U = a.units[un];
                 if (!cnn_runs(a.io.st, U.inst)) continue;
-                const uint32_t pd16 = (uint32_t)(a.Ns[U.inst] + 3) * 16;
+                const uint32_t pdu = (uint32_t)(a.Ns[U.inst] + 3);  // one grid row of Pd nodes, in 16-byte rows
+                const uint64_t a_lbo_pd = (uint64_t)(pdu & 0x3FFF) << 16;
+                // A offsets of the (dy, K-half) combinations, in 16-byte rows
+                uint32_t offu[3][2];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) offu[dy][hh] = (uint32_t)dy * pdu + (uint32_t)(2 * hh) * (uint32_t)W;
                 const int nwin = U.z1 - U.z0 + 2;
+                bool next_ready = false;  // window of the next plane step already waited for
                 for (int k = 0; k < nwin - 2 && ok; ++k) {
-                    // windows k, k+1, k+2 of this unit (planes z-1, z, z+1)
-                    const int g0 = g + k;
+                    // windows k, k+1, k+2 of this unit (planes z-1, z, z+1); ring
+                    // positions of the unit's window k
+                    int s0w = gs, q0w = gq;
+                    int s1w = s0w, q1w = q0w, s2w = s0w, q2w = q0w;
+                    adv(s1w, q1w, 1);
+                    adv(s2w, q2w, 2);
                     if (k == 0) {
-                        if (!mbar_wait(&full[g0 % NS], (g0 / NS) & 1, a.err)) { ok = false; break; }
-                        if (!mbar_wait(&full[(g0 + 1) % NS], ((g0 + 1) / NS) & 1, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&full[s0w], q0w & 1, a.err)) { ok = false; break; }
+                        if (!mbar_wait(&full[s1w], q1w & 1, a.err)) { ok = false; break; }
                     }
-                    if (!mbar_wait(&full[(g0 + 2) % NS], ((g0 + 2) / NS) & 1, a.err)) { ok = false; break; }
+                    if (!next_ready && !mbar_wait(&full[s2w], q2w & 1, a.err)) { ok = false; break; }
+                    next_ready = false;
                     const int bsel = it & 1;
                     if (!mbar_wait(&tempty[bsel], ((it >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
                     tc_fence_after();
-                    uint32_t sb[3];
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz) sb[dz] = rb0 + (uint32_t)(((g0 + dz) % NS) * slot_bytes);
+                    const uint32_t sbu[3] = {(rb0 >> 4) + (uint32_t)(s0w * slot_bytes >> 4), (rb0 >> 4) + (uint32_t)(s1w * slot_bytes >> 4),
+                                             (rb0 >> 4) + (uint32_t)(s2w * slot_bytes >> 4)};  // window slots, in 16-byte units
 #pragma unroll
                     for (int ut = 0; ut < TPS; ++ut) {
                         const uint32_t d = tmem + (uint32_t)((bsel * TPS + ut) * NCOL);
-                        const uint32_t ub = (uint32_t)(ut * 126 * 16);
                         if (KIND == 1) {
                             // one 8-channel chunk: per z-window the (dy=-1, dy=0) rows in
-                            // one K=16 step, (dy=+1, zero-weight row + 1) in a second
+                            // one K=16 step (second core matrix one grid row further),
+                            // (dy=+1, zero-weight row + 1) in a second (one node further)
 #pragma unroll
                             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
                                 for (int pr = 0; pr < 2; ++pr) {
-                                    const uint32_t a1 = sb[dz] + ub + (uint32_t)(2 * pr) * pd16;
-                                    const uint32_t a2 = pr == 0 ? a1 + pd16 : a1 + 16;
-                                    const uint64_t ad = a_hi | ((uint64_t)(((a2 - a1) >> 4) & 0x3FFF) << 16) | ((a1 >> 4) & 0x3FFF);
-                                    const uint64_t bd = sdesc(wb + (uint32_t)((dz * 2 + pr) * 2 * NCOL * 16), NCOL * 16, 128);
+                                    const uint64_t ad = (a_hi | (pr == 0 ? a_lbo_pd : (1ULL << 16))) +
+                                                        (uint64_t)(sbu[dz] + (uint32_t)(ut * 126) + (uint32_t)(2 * pr) * pdu);
+                                    const uint64_t bd = bd0 + (uint64_t)(((dz * 2 + pr) * 2 * NCOL * 16) >> 4);
                                     mma_bf16(d, ad, bd, IDESC, (dz > 0 || pr > 0) ? 1u : 0u);
                                 }
                         } else {
-                            const uint64_t a_lbo = (uint64_t)(((W * 16) >> 4) & 0x3FFF) << 16;
+                            const uint64_t a0 = a_hi | a_lbo_w;
 #pragma unroll
-                            for (int dz = 0; dz < 3; ++dz)
+                            for (int dz = 0; dz < 3; ++dz) {
+                                const uint64_t az = a0 + (uint64_t)(sbu[dz] + (uint32_t)(ut * 126));
 #pragma unroll
                                 for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                                     for (int hh = 0; hh < 2; ++hh) {
                                         const int combo = dz * 3 + dy;
-                                        const uint32_t aa = sb[dz] + (uint32_t)(2 * hh * W * 16) + ub + (uint32_t)dy * pd16;
-                                        const uint64_t ad = a_hi | a_lbo | ((aa >> 4) & 0x3FFF);
-                                        const uint64_t bd = sdesc(wb + (uint32_t)((combo * 4 + 2 * hh) * NCOL * 16), NCOL * 16, 128);
-                                        mma_bf16(d, ad, bd, IDESC, (combo > 0 || hh > 0) ? 1u : 0u);
+                                        const uint64_t bd = bd0 + (uint64_t)(((combo * 4 + 2 * hh) * NCOL * 16) >> 4);
+                                        mma_bf16(d, az + (uint64_t)offu[dy][hh], bd, IDESC, (combo > 0 || hh > 0) ? 1u : 0u);
                                     }
+                            }
+                        }
+                        if (ut == 0 && k + 1 < nwin - 2) {
+                            // while the tensor pipe works through this tile, make sure
+                            // the window the next plane step adds has arrived
+                            int s3w = s0w, q3w = q0w;
+                            adv(s3w, q3w, 3);
+                            if (!mbar_wait(&full[s3w], q3w & 1, a.err)) ok = false;
+                            next_ready = true;
                         }
                     }
                     mma_commit(&tfull[bsel]);
-                    mma_commit(&empty[g0 % NS]);  // window k is not read by later planes
+                    mma_commit(&empty[s0w]);  // window k is not read by later planes
                     if (k == nwin - 3) {
-                        mma_commit(&empty[(g0 + 1) % NS]);
-                        mma_commit(&empty[(g0 + 2) % NS]);
+                        mma_commit(&empty[s1w]);
+                        mma_commit(&empty[s2w]);
                     }
                     ++it;
+                    adv(gs, gq, 1);
                 }
-                g += nwin;
+                adv(gs, gq, 2);  // the unit's last two windows
             }
             // MMAs in flight complete before the tensor memory is freed
             if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
@@ -357,7 +391,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         const bool writer = KIND != 2 || cg == 0;
         int it = 0, xcnt = 0;
         bool ok = true;
-        for (int un = blockIdx.x; un < a.nunits && ok; un += gridDim.x) {
+        for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
             const TcUnit U = a.units[un];
             if (!cnn_runs(a.io.st, U.inst)) continue;
             const int N = a.Ns[U.inst], M = N + 1;
@@ -382,50 +416,60 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err));
                 if (!ok) break;
                 tc_fence_after();
+                // this lane's three column groups (dx = -1, 0, +1) of every tile of
+                // the step, loaded together; the accumulator is then handed back
+                // to the MMA issuer before any of the arithmetic below
+                float dm[TPS][CH], dc[TPS][CH], dp[TPS][CH];
 #pragma unroll
                 for (int ut = 0; ut < TPS; ++ut) {
-                    // this lane's three column groups (dx = -1, 0, +1)
-                    float dm[CH], dc[CH], dp[CH];
                     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
                     if constexpr (KIND == 2) {
                         float v[8];
                         tmem_ld_nowait<8>(tb, v);
-                        tmem_wait_ld();
-                        dm[0] = v[0];
-                        dc[0] = v[1];
-                        dp[0] = v[2];
+                        dm[ut][0] = v[0];
+                        dc[ut][0] = v[1];
+                        dp[ut][0] = v[2];
                     } else {
-                        tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm);
-                        tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc);
-                        tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp);
-                        tmem_wait_ld();
+                        tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm[ut]);
+                        tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc[ut]);
+                        tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp[ut]);
                     }
-                    // warp-boundary values: lane 31's dx=-1 group, lane 0's dx=+1 group,
-                    // exchanged among the 4 warps (lane quarters) of this channel
-                    // group through a named barrier; buffer xcnt & 1 is rewritten
-                    // only after every warp of the group passed the next barrier
-                    const int xbuf = xcnt & 1;
-                    float* xb = xch + (size_t)xbuf * (4 * TC_EPI_GROUPS * 2 * TC_EPI_CH);
-                    float* mine = xb + (q * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
+                }
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[bsel]);
+                // warp-boundary values: lane 31's dx=-1 group, lane 0's dx=+1 group,
+                // exchanged among the 4 warps (lane quarters) of this channel
+                // group through a named barrier; buffer xcnt & 1 is rewritten
+                // only after every warp of the group passed the next barrier
+                const int xbuf = xcnt & 1;
+                float* xb = xch + (size_t)xbuf * (TPS * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH);
+#pragma unroll
+                for (int ut = 0; ut < TPS; ++ut) {
+                    float* mine = xb + ((ut * 4 + q) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
                     if constexpr (KIND == 2) {
-                        if (lane == 31) mine[0] = dm[0];
-                        if (lane == 0) mine[TC_EPI_CH] = dp[0];
+                        if (lane == 31) mine[0] = dm[ut][0];
+                        if (lane == 0) mine[TC_EPI_CH] = dp[ut][0];
                     } else {
                         static_assert(CH == 8, "the exchange moves 8 channels as two float4");
                         float4* m4 = reinterpret_cast<float4*>(mine);
                         if (lane == 31) {
-                            m4[0] = make_float4(dm[0], dm[1], dm[2], dm[3]);
-                            m4[1] = make_float4(dm[4], dm[5], dm[6], dm[7]);
+                            m4[0] = make_float4(dm[ut][0], dm[ut][1], dm[ut][2], dm[ut][3]);
+                            m4[1] = make_float4(dm[ut][4], dm[ut][5], dm[ut][6], dm[ut][7]);
                         }
                         if (lane == 0) {
-                            m4[2] = make_float4(dp[0], dp[1], dp[2], dp[3]);
-                            m4[3] = make_float4(dp[4], dp[5], dp[6], dp[7]);
+                            m4[2] = make_float4(dp[ut][0], dp[ut][1], dp[ut][2], dp[ut][3]);
+                            m4[3] = make_float4(dp[ut][4], dp[ut][5], dp[ut][6], dp[ut][7]);
                         }
                     }
-                    nbar_sync(1 + cg, 4 * 32);
-                    ++xcnt;
-                    const float* prev = xb + (((q + 3) & 3) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
-                    const float* next = xb + (((q + 1) & 3) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
+                }
+                nbar_sync(1 + cg, 4 * 32);
+                ++xcnt;
+#pragma unroll
+                for (int ut = 0; ut < TPS; ++ut) {
+                    const float* prev = xb + ((ut * 4 + ((q + 3) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
+                    const float* next = xb + ((ut * 4 + ((q + 1) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
                     // lanes 0 and 31 take their missing neighbour from the adjacent quarter
                     float pv[CH], nx[CH];
                     if constexpr (KIND == 2) {
@@ -442,11 +486,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     float o[CH];
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
-                        float up = __shfl_up_sync(0xffffffffu, dm[c], 1);    // D[i-1][dx=-1]
-                        float dn = __shfl_down_sync(0xffffffffu, dp[c], 1);  // D[i+1][dx=+1]
+                        float up = __shfl_up_sync(0xffffffffu, dm[ut][c], 1);    // D[i-1][dx=-1]
+                        float dn = __shfl_down_sync(0xffffffffu, dp[ut][c], 1);  // D[i+1][dx=+1]
                         if (lane == 0) up = pv[c];
                         if (lane == 31) dn = nx[c];
-                        o[c] = up + dc[c] + dn + bias[c];
+                        o[c] = up + dc[ut][c] + dn + bias[c];
                     }
                     if (!val[ut]) continue;
                     const int p = z * P2 + rr[ut];
@@ -478,10 +522,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         }
                     }
                 }
-                if (!ok) break;
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[bsel]);
             }
         }
     }
@@ -498,7 +538,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 // host side
 int tc_smem_bytes(int kind, int W, int ns) {
     const int cin8 = kind == 1 ? 1 : 4;
-    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 8) * 8 + 2 * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH * 4 + 16;
+    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 8) * 8 + 2 * TC_TPS_MAX * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH * 4 + 16;
 }
 
 // Ring slots that fit next to the hidden-layer weights (at most 8).

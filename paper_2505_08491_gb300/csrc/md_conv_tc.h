@@ -13,6 +13,7 @@ struct TcUnit { int inst, s0, z0, z1; };
 #define TC_EPI_GROUPS (32 / TC_EPI_CH)       // channel groups
 #define TC_EPI_WARPS (4 * TC_EPI_GROUPS)     // epilogue warps: 4 TMEM lane quarters x channel groups
 #define TC_THREADS (32 * (2 + TC_EPI_WARPS))  // + producer and MMA warps
+#define TC_TPS_MAX 2                         // tiles per plane step (epilogue exchange buffers)
 
 struct TcArgs {
     const __nv_bfloat16* in;     // activation buffer (chunk-major padded layout)
@@ -21,6 +22,7 @@ struct TcArgs {
     const long long* out_off;
     const int* Ns;               // per instance grid size N
     const TcUnit* units;
+    const int* ubeg;             // CTA b runs units [ubeg[b], ubeg[b + 1]); the grid has one CTA per range
     int nunits;
     int W;                       // rows per (window, chunk) region in shared memory
     int NS;                      // ring slots
