@@ -37,6 +37,11 @@ COUNT = 100
 TOL = 1e-8
 RESTART = 30
 HIDDEN_FLOP_PER_NODE = 4 * 2 * 27 * 32 * 32     # the four 32->32 layers
+METRIC = "solves/sec and s/solve to rel. residual 1e-8, CNN-FGMRES vs Jacobi-CG, 1 GB300"
+# DRAM bytes (read + write) per grid node of one hidden-layer launch, from the
+# ncu capture summarised in profiles/conv_hidden_tcgen05_64x33cube.md (64 grids
+# of 33^3; traffic grows with the grid nodes a launch processes)
+HIDDEN_TRAFFIC_BYTES_PER_NODE = 153.0
 NET_FLOP_PER_NODE = 2 * 27 * (3 * 32 + 4 * 32 * 32 + 32)
 
 
@@ -124,6 +129,14 @@ def oracle_solve_seconds(inst, params_flat, max_seconds=None):
     return time.perf_counter() - t0, it, rel, rel <= TOL
 
 
+def bench_config(args, grid_nodes):
+    return {"workload": f"{args.workload}: {args.count} {WORKLOAD_TEXT[args.workload]}; one batched "
+                        "FGMRES(30) solve per step, BF16 network, tol 1e-8 (true FP64 residual)",
+            "instances_per_gpu": args.count, "grid_nodes_per_gpu": grid_nodes,
+            "l2": "working set > L2, 256 MB flush between steps", "precision":
+            "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -141,14 +154,14 @@ def reference_arm(args):
     total = sum(ts)
     value = args.steps / total
     cores = os.cpu_count()
-    line = {"impl": "reference", "metric": "solves/sec to rel. residual 1e-8 (CNN-FGMRES)", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: one instance per step ({WORKLOAD_TEXT[args.workload]}), "
-                                   "FGMRES(30)+network, tol 1e-8"},
+            "config": bench_config(args, sum((w["N"] + 1) ** 3 for w in insts)),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} full solves (iterations {its})"},
+                             "sample": f"one instance of the workload per step ({args.steps} full FP64 oracle "
+                                       f"solves, iterations {its}; numpy BLAS threads: default)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -294,10 +307,13 @@ def main():
     flops = stats["precond_nodes"] * HIDDEN_FLOP_PER_NODE
     conv_s = stats["conv_hidden_ms"] / 1e3
     achieved = flops / conv_s / 1e12 if conv_s > 0 else 0.0
+    traffic = HIDDEN_TRAFFIC_BYTES_PER_NODE * stats["precond_nodes"] * 4 / max(launches, 1)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_tflops_sustained"], "traffic": None,
+                "frac": achieved / pk["bf16_tflops_sustained"], "traffic": traffic,
                 "kernel": "hidden 3x3x3 32->32 convolutions (4 per network application)",
                 "launches": launches, "avg_launch_ms": stats["conv_hidden_ms"] / max(launches, 1),
+                "traffic_note": "bytes per launch (average over the timed launches, like achieved): "
+                                "153 B/node measured by ncu on 64 grids of 33^3, scaled by the nodes processed",
                 "peak_source": pk["source"] + " bf16 dense, sustained"}
     breakdown = {k: stats[k] for k in ("prec_ms", "conv_hidden_ms", "apply_ms", "arnoldi_ms", "restart_ms")}
 
@@ -310,16 +326,12 @@ def main():
                "sample": f"instance 0, FP64 oracle FGMRES(30)+network: {it} iterations timed ({t:.1f} s), "
                          f"scaled to the {its0} iterations its solve takes"}
 
-    line = {"metric": "solves/sec to rel. residual 1e-8, CNN-FGMRES vs Jacobi-CG, 1 GB300", "value": value,
+    line = {"metric": METRIC, "value": value,
             "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "s_per_solve": ms_per_step / 1e3 / args.count,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {args.count} {WORKLOAD_TEXT[args.workload]}; one batched "
-                                   "FGMRES(30) solve per step, BF16 network, tol 1e-8 (true FP64 residual)",
-                       "instances_per_gpu": args.count, "grid_nodes_per_gpu": nodes_total,
-                       "l2": "working set > L2, 256 MB flush between steps", "precision":
-                       "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"},
+            "config": bench_config(args, nodes_total),
             "iterations": {"mean": float(np.mean(its_all[-1])), "max": int(np.max(its_all[-1]))},
             "instance_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "note": "device globaltimer from solve start to each instance's convergence"},
