@@ -21,9 +21,9 @@
 //               (TMA, cp.async.bulk) of the TPS*128 + 2(Pd+1) + 8 contiguous
 //               rows the taps read, into a ring of NS shared-memory slots,
 //               completion counted on mbarriers (transaction bytes);
-//   warp 1      one thread issues tcgen05.mma (M=128, N=32 (16 for the last
-//               layer), K=16): 27 taps x 2 K-halves per tile, fully unrolled
-//               from per-unit row offsets, into a double-buffered TMEM
+//   warps 1, 18 one thread each issues tcgen05.mma (M=128, N=96 (16 for the
+//               last layer), K=16) for one of the two tiles of a step, fully
+//               unrolled from per-unit row offsets, into a double-buffered TMEM
 //               accumulator; commits free the accumulator for the epilogue
 //               and the oldest window for the producer;
 //   warps 2..17 epilogue: tcgen05.ld of their 32-lane quarter and 8-channel group, bias, GELU,
@@ -32,8 +32,10 @@
 //               is preserved).
 // The first layer (3 input channels in one 8-channel chunk) pairs two taps
 // of one z-window per K=16 step (5 MMAs per window, the ninth tap with a
-// zero-weight partner); the last (1 output channel) runs N=16 with zero
-// weights in the extra columns.
+// zero-weight partner); the last (1 output channel) puts the nine (dz, dx)
+// taps side by side in N = 16 columns, so each window alone feeds 6 MMAs (3 dy
+// x 2 K-halves) and the epilogue adds the dz contributions of consecutive
+// windows in registers.
 //
 // Every mbarrier wait is bounded (2 s of globaltimer); on timeout the kernel
 // sets an error flag, waits (bounded) for its own work in flight, frees its
@@ -225,10 +227,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], TC_MMA_WARPS);  // every issuer releases the window
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&tfull[i], 1);
+            mbar_init(&tfull[i], TC_MMA_WARPS);  // every issuer's MMAs of the step
             mbar_init(&tempty[i], TC_EPI_WARPS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -271,8 +273,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             // copies still in flight complete before the CTA leaves
             for (int k = (g > NS ? g - NS : 0); k < g; ++k) mbar_wait(&full[k % NS], (k / NS) & 1, a.err);
         }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer
+    } else if (warp == 1 || warp == TC_MMA2_WARP) {
+        // ---------------- MMA issuers: one thread of warp 1 and one of the last
+        // warp (other SM sub-partitions), each issuing the tiles ut = mi mod 2 of
+        // every step (one thread cannot issue tcgen05.mma as fast as the tensor
+        // pipe executes N = 96 MMAs); both wait on the same windows and
+        // accumulators and both commit to the barriers, which count two arrivals
+        const int mi = warp == 1 ? 0 : 1;
+        // tiles this thread issues: the first layer (6 MMAs per tile) is left to
+        // warp 1 alone, the second issuer only commits there
+        auto issues = [mi](int ut) { return KIND == 1 ? mi == 0 : ut % TC_MMA_WARPS == mi; };
+        auto prewaits = [mi](int ut) { return KIND == 1 ? (mi == 0 && ut == 0) : ut == mi; };
         if (lane == 0) {
             int it = 0;
             bool ok = true;
@@ -305,6 +316,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                     for (int hh = 0; hh < 2; ++hh) offu[dy][hh] = (uint32_t)dy * pdu + (uint32_t)(2 * hh) * (uint32_t)W;
                 const int nwin = U.z1 - U.z0 + 2;
+                if constexpr (KIND == 2) {
+                    // last layer: dz folded into N with dx (n = 3 dz + dx), so every
+                    // window alone feeds one step of 6 MMAs and is released after it
+                    bool win_ready = false;
+                    for (int k = 0; k < nwin && ok; ++k) {
+                        const int sw = gs, qw = gq;
+                        if (!win_ready && !mbar_wait(&full[sw], qw & 1, a.err)) { ok = false; break; }
+                        win_ready = false;
+                        const int bsel = it & 1;
+                        if (!mbar_wait(&tempty[bsel], ((it >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sbu = (rb0 >> 4) + (uint32_t)(sw * slot_bytes >> 4);
+#pragma unroll
+                        for (int ut = 0; ut < TPS; ++ut) {
+                            if (!issues(ut)) continue;
+                            const uint32_t d = tmem + (uint32_t)((bsel * TPS + ut) * NCOL);
+                            const uint64_t az = (a_hi | a_lbo_w) + (uint64_t)(sbu + (uint32_t)(ut * 126));
+#pragma unroll
+                            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                                for (int hh = 0; hh < 2; ++hh) {
+                                    const uint64_t bd = bd0 + (uint64_t)(((dy * 4 + 2 * hh) * NCOL * 16) >> 4);
+                                    mma_bf16(d, az + (uint64_t)offu[dy][hh], bd, IDESC, (dy > 0 || hh > 0) ? 1u : 0u);
+                                }
+                            if (prewaits(ut) && k + 1 < nwin) {
+                                int sn = gs, qn = gq;
+                                adv(sn, qn, 1);
+                                if (!mbar_wait(&full[sn], qn & 1, a.err)) ok = false;
+                                win_ready = true;
+                            }
+                        }
+                        mma_commit(&tfull[bsel]);
+                        mma_commit(&empty[sw]);
+                        ++it;
+                        adv(gs, gq, 1);
+                    }
+                    continue;
+                }
                 bool next_ready = false;  // window of the next plane step already waited for
                 for (int k = 0; k < nwin - 2 && ok; ++k) {
                     // windows k, k+1, k+2 of this unit (planes z-1, z, z+1); ring
@@ -326,6 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                                              (rb0 >> 4) + (uint32_t)(s2w * slot_bytes >> 4)};  // window slots, in 16-byte units
 #pragma unroll
                     for (int ut = 0; ut < TPS; ++ut) {
+                        if (!issues(ut)) continue;
                         const uint32_t d = tmem + (uint32_t)((bsel * TPS + ut) * NCOL);
                         if (KIND == 1) {
                             // one 8-channel chunk: per z-window the (dy=-1, dy=0) rows in
@@ -355,7 +405,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                                     }
                             }
                         }
-                        if (ut == 0 && k + 1 < nwin - 2) {
+                        if (prewaits(ut) && k + 1 < nwin - 2) {
                             // while the tensor pipe works through this tile, make sure
                             // the window the next plane step adds has arrived
                             int s3w = s0w, q3w = q0w;
@@ -409,6 +459,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             }
             __nv_bfloat16* outU = (KIND != 2) ? a.out + a.out_off[U.inst] : nullptr;
             __nv_bfloat16* zsU = (KIND != 2 && a.zsave) ? a.zsave + a.out_off[U.inst] : nullptr;
+            if constexpr (KIND == 2) {
+                // Window p holds D_p[i][3 dz + dx]; after the dx recombination
+                // across lanes, P[dz] is window p's contribution to output plane
+                // p + 1 - dz.  acc_m1 / acc_0: partial sums of planes p - 1 and p
+                // before window p; plane p - 1 is complete after it.
+                float acc_m1[TPS], acc_0[TPS];
+#pragma unroll
+                for (int ut = 0; ut < TPS; ++ut) acc_m1[ut] = acc_0[ut] = 0.0f;
+                const int nwin = U.z1 - U.z0 + 2;
+                float* ov = a.io.out + a.io.off[U.inst];
+                const float scale = (a.mode == CONV_PREC) ? (float)(a.io.st[U.inst].s / a.io.D[U.inst].alpha) : 1.0f;
+                for (int k = 0; k < nwin; ++k, ++it) {
+                    const int pz = U.z0 - 1 + k;  // plane of this window
+                    const int bsel = it & 1;
+                    ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err));
+                    if (!ok) break;
+                    tc_fence_after();
+                    float v[TPS][16];
+#pragma unroll
+                    for (int ut = 0; ut < TPS; ++ut) {
+                        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
+                        float* lo = v[ut];
+                        tmem_ld_nowait<8>(tb, *reinterpret_cast<float(*)[8]>(lo));
+                        tmem_ld_nowait<8>(tb + 8, *reinterpret_cast<float(*)[8]>(lo + 8));
+                    }
+                    tmem_wait_ld();
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[bsel]);
+                    const int xbuf = xcnt & 1;
+                    float* xb = xch + (size_t)xbuf * (TPS * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH);
+#pragma unroll
+                    for (int ut = 0; ut < TPS; ++ut) {
+                        float* mine = xb + ((ut * 4 + q) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
+                        if (lane == 31)
+#pragma unroll
+                            for (int dz = 0; dz < 3; ++dz) mine[dz] = v[ut][3 * dz];
+                        if (lane == 0)
+#pragma unroll
+                            for (int dz = 0; dz < 3; ++dz) mine[TC_EPI_CH + dz] = v[ut][3 * dz + 2];
+                    }
+                    nbar_sync(1 + cg, 4 * 32);
+                    ++xcnt;
+#pragma unroll
+                    for (int ut = 0; ut < TPS; ++ut) {
+                        const float* prev = xb + ((ut * 4 + ((q + 3) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
+                        const float* next = xb + ((ut * 4 + ((q + 1) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
+                        float P[3];
+#pragma unroll
+                        for (int dz = 0; dz < 3; ++dz) {
+                            float up = __shfl_up_sync(0xffffffffu, v[ut][3 * dz], 1);        // D[i-1][dx=-1]
+                            float dn = __shfl_down_sync(0xffffffffu, v[ut][3 * dz + 2], 1);  // D[i+1][dx=+1]
+                            if (lane == 0) up = prev[dz];
+                            if (lane == 31) dn = next[dz];
+                            P[dz] = up + v[ut][3 * dz + 1] + dn;
+                        }
+                        const float done = acc_m1[ut] + P[2];  // plane pz - 1
+                        acc_m1[ut] = acc_0[ut] + P[1];
+                        acc_0[ut] = P[0];
+                        const int z = pz - 1;
+                        if (!val[ut] || z < U.z0 || z >= U.z1) continue;
+                        const int xp = rr[ut] % Pd, yp = rr[ut] / Pd;
+                        const int ii = xp - 1, jj = yp - 1, kk = z - 1;
+                        const int n = ii + M * (jj + M * kk);
+                        const float o = done + bias[0];
+                        if (a.mode == CONV_PREC) {
+                            const bool bd = (ii == 0 || ii == N || jj == 0 || jj == N || kk == 0 || kk == N);
+                            ov[n] = bd ? a.io.vin[a.io.vin_off[U.inst] + n] : scale * o;
+                        } else {
+                            ov[n] = o;
+                        }
+                    }
+                }
+            } else {
             for (int z = U.z0; z < U.z1; ++z, ++it) {
                 const int bsel = it & 1;
                 // every warp waits for the accumulator itself; the group leaves
@@ -523,6 +647,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     }
                 }
             }
+            }  // KIND != 2
         }
     }
 
@@ -595,7 +720,7 @@ md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s
 //   kind 0: [combo = dz*3+dy (9)][k-chunk 4][n 96][8]
 //   kind 1: [dz 3][pair 2][k-chunk 2][n 96][8]; pair 0 = (dy -1, dy 0),
 //           pair 1 = (dy +1, zero)
-//   kind 2: [combo 9][k-chunk 4][n 16][8]; n = dx index for o = 0, rest zero
+//   kind 2: [dy 3][k-chunk 4][n 16][8]; n = 3 dz + dx for o = 0 (9 columns), rest zero
 void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img) {
     img.assign(tc_wimg_bytes(kind) / 2, __float2bfloat16_rn(0.0f));
     auto w_at = [&](int o, int c, int tap) -> float {
@@ -624,10 +749,13 @@ void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__
                             __float2bfloat16_rn(w_at(o, kc * 8 + l, combo * 3 + g));
                     }
     } else {
-        for (int combo = 0; combo < 9; ++combo)
+        for (int dy = 0; dy < 3; ++dy)
             for (int kc = 0; kc < 4; ++kc)
-                for (int n = 0; n < 3; ++n)
-                    for (int l = 0; l < 8; ++l)
-                        img[((size_t)(combo * 4 + kc) * 16 + n) * 8 + l] = __float2bfloat16_rn(w_at(0, kc * 8 + l, combo * 3 + n));
+                for (int n = 0; n < 9; ++n)
+                    for (int l = 0; l < 8; ++l) {
+                        const int dz = n / 3, dx = n % 3;
+                        img[((size_t)(dy * 4 + kc) * 16 + n) * 8 + l] =
+                            __float2bfloat16_rn(w_at(0, kc * 8 + l, dz * 9 + dy * 3 + dx));
+                    }
     }
 }

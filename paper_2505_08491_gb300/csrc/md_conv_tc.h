@@ -12,7 +12,9 @@ struct TcUnit { int inst, s0, z0, z1; };
 #define TC_EPI_CH 8                          // output channels per epilogue thread
 #define TC_EPI_GROUPS (32 / TC_EPI_CH)       // channel groups
 #define TC_EPI_WARPS (4 * TC_EPI_GROUPS)     // epilogue warps: 4 TMEM lane quarters x channel groups
-#define TC_THREADS (32 * (2 + TC_EPI_WARPS))  // + producer and MMA warps
+#define TC_MMA_WARPS 2                       // MMA issuers: warp 1 and the last warp, one tile of a step each
+#define TC_MMA2_WARP (2 + TC_EPI_WARPS)      // warp index of the second issuer
+#define TC_THREADS (32 * (1 + TC_MMA_WARPS + TC_EPI_WARPS))  // + producer warp
 #define TC_TPS_MAX 2                         // tiles per plane step (epilogue exchange buffers)
 
 struct TcArgs {
@@ -36,7 +38,7 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_wimg_bytes(int kind) {
-    return kind == 1 ? 3 * 2 * 2 * 96 * 16 : 9 * 4 * (kind == 2 ? 16 : 96) * 16;
+    return kind == 1 ? 3 * 2 * 2 * 96 * 16 : (kind == 2 ? 3 * 4 * 16 * 16 : 9 * 4 * 96 * 16);
 }
 // rows one window copy holds: TPS tiles 126 rows apart, 128 rows each, read
 // at dy offsets 0..2 Pd from the window start, plus 8 rows of slack
