@@ -58,7 +58,16 @@ WORKLOAD_TEXT = {
     "tree15_32": "seeded binary trees (15 segments, 8 el/seg), N=32, beta=1, f~N(0,1), g=1",
     "batch256_mixed": "seeded binary trees (7-255 segments), N in {32,48,64}, beta log-uniform [1,100], "
                       "R~U(.01,.03), f~N(0,1), g=1",
+    "transfer_64": "seeded binary trees (31-127 segments, 16 el/seg), N=64, beta in {1,10,100}, R~U(.005,.02), "
+                   "f~N(0,1), g=1; network trained at N<=32",
+    "transfer_128": "seeded binary trees (31-127 segments, 16 el/seg), N=128, beta in {1,10,100}, R~U(.005,.02), "
+                    "f~N(0,1), g=1; network trained at N<=32",
 }
+DEFAULT_COUNT = {"tree15_32": 100, "batch256_mixed": 256, "transfer_64": 30, "transfer_128": 12}
+
+
+def restart_of(workload: str) -> int:
+    return int(mdgen.WORKLOADS[workload].get("restart", RESTART))
 
 
 def instances(workload: str, rank: int, count: int):
@@ -129,9 +138,18 @@ def oracle_solve_seconds(inst, params_flat, max_seconds=None):
     return time.perf_counter() - t0, it, rel, rel <= TOL
 
 
+def by_group(keys, its):
+    """Mean iterations per distinct key (beta or N), keys rounded for beta log-uniform draws."""
+    groups = {}
+    for k, it in zip(keys, its):
+        kk = k if isinstance(k, int) or len(set(keys)) <= 4 else (1 if k < 3 else (10 if k < 30 else 100))
+        groups.setdefault(str(kk), []).append(it)
+    return {k: float(np.mean(v)) for k, v in sorted(groups.items(), key=lambda kv: float(kv[0]))}
+
+
 def bench_config(args, grid_nodes):
     return {"workload": f"{args.workload}: {args.count} {WORKLOAD_TEXT[args.workload]}; one batched "
-                        "FGMRES(30) solve per step, BF16 network, tol 1e-8 (true FP64 residual)",
+                        f"FGMRES({restart_of(args.workload)}) solve per step, BF16 network, tol 1e-8 (true FP64 residual)",
             "instances_per_gpu": args.count, "grid_nodes_per_gpu": grid_nodes,
             "l2": "working set > L2, 256 MB flush between steps", "precision":
             "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"}
@@ -172,7 +190,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--count", type=int, default=None, help="instances per GPU (default 100, or 256 for batch256_mixed)")
+    ap.add_argument("--count", type=int, default=None, help="instances per GPU (default: the workload's)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
@@ -180,7 +198,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.count is None:
-        args.count = 256 if args.workload == "batch256_mixed" else COUNT
+        args.count = DEFAULT_COUNT[args.workload]
     if args.impl == "reference":
         return reference_arm(args)
 
@@ -212,7 +230,7 @@ def main():
         bs.append(op.rhs(torch.from_numpy(f).cuda() if f is not None else None, w["g"]))
     b_all = torch.cat(bs).contiguous()
     x_all = torch.zeros_like(b_all)
-    B = Batch(ops, "fgmres_cnn", net, restart=RESTART)
+    B = Batch(ops, "fgmres_cnn", net, restart=restart_of(args.workload))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -298,6 +316,7 @@ def main():
         cg_value = args.count / (cg_ms / reps / 1e3)
         cg = {"solves_per_s": cg_value, "s_per_solve_batched": cg_ms / reps / 1e3 / args.count,
               "mean_iterations": float(np.mean(cg_its)), "converged": bool(cg_ok),
+              "iterations_by_beta": by_group([w["beta"] for w in insts], cg_its),
               "speedup_fgmres_cnn_over_cg": value / world / cg_value}
         Bc.close()
 
@@ -332,7 +351,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": bench_config(args, nodes_total),
-            "iterations": {"mean": float(np.mean(its_all[-1])), "max": int(np.max(its_all[-1]))},
+            "iterations": {"mean": float(np.mean(its_all[-1])), "max": int(np.max(its_all[-1])),
+                           "by_beta": by_group([w["beta"] for w in insts], its_all[-1]),
+                           "by_N": by_group([w["N"] for w in insts], its_all[-1])},
             "instance_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "note": "device globaltimer from solve start to each instance's convergence"},
             "max_relres": float(max(rel_all)),

@@ -154,3 +154,24 @@ def test_bf16_emulation_close_to_fp64():
     rel = np.linalg.norm(y16 - y64) / np.linalg.norm(y64)
     assert rel < 3e-2
     assert rel > 0
+
+
+def test_output_depends_on_radius_six_box_only():
+    """Six 3x3x3 'same' layers: the output at a node is the network applied to
+    the grid box of radius 6 around it, clipped at the grid faces (the
+    property the full-size GPU parity samples rely on); a radius-5 box is not
+    enough."""
+    rng = np.random.default_rng(11)
+    n = 15
+    X = rng.standard_normal((3, n, n, n))
+    params = cnn.init_params(5)
+    full = cnn.forward(X, params)[0]
+    for (z, y, x) in [(0, 0, 0), (7, 7, 7), (14, 3, 9), (2, 12, 6)]:
+        for r, exact in ((6, True), (5, False)):
+            lo = [max(0, c - r) for c in (z, y, x)]
+            hi = [min(n, c + r + 1) for c in (z, y, x)]
+            v = cnn.forward(X[:, lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]], params)[0][z - lo[0], y - lo[1], x - lo[2]]
+            if exact:
+                assert abs(v - full[z, y, x]) <= 1e-12 * (1 + abs(full[z, y, x]))
+            elif (z, y, x) == (7, 7, 7):
+                assert abs(v - full[z, y, x]) > 1e-9
