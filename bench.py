@@ -71,7 +71,23 @@ def restart_of(workload: str) -> int:
 
 
 def instances(workload: str, rank: int, count: int):
+    """The instances rank `rank` solves: a disjoint block of `count` seeded
+    instances per rank (weak scaling: every rank holds the same amount)."""
     return [mdgen.workload_instance(workload, rank * count + i) for i in range(count)]
+
+
+def job_throughput(local_ms: float, local_solves: int, world: int, device, dist=None):
+    """Whole-job solves/s from every rank's timed milliseconds and solve count:
+    the slowest rank's time (MAX) and the solves of all ranks (SUM).
+    Returns (max_ms, total_solves, solves_per_s)."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    n = torch.tensor([float(local_solves)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    max_ms, total = float(t.item()), int(round(n.item()))
+    return max_ms, total, total / (max_ms / 1e3)
 
 
 class ClockSampler:
@@ -221,7 +237,11 @@ def main():
         torch.cuda.synchronize()
 
     insts = instances(args.workload, rank, args.count)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter()
     ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    torch.cuda.synchronize()
+    assembly_s = (time.perf_counter() - t_asm) / len(ops)
     params = default_network_params()
     net = Network(params)
     bs = []
@@ -263,12 +283,8 @@ def main():
     clk = clocks.stop()
     stats = B.stats()
     B.set_profiling(False)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms, _, value = job_throughput(total_ms, args.count * args.steps, world, "cuda", dist)
     ms_per_step = total_ms / args.steps
-    value = world * args.count * args.steps / (total_ms / 1e3)
 
     # end to end through the public API: pinned host b in, x out, every step
     b_host = b_all.cpu().pin_memory()
@@ -288,10 +304,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.count * args.steps / (float(t.item()) / 1e3)
+    _, _, e2e_value = job_throughput(e2e_ms, args.count * args.steps, world, "cuda", dist)
 
     # Jacobi-CG on the same batch and GPU
     cg = None
@@ -357,6 +370,8 @@ def main():
             "instance_latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                    "note": "device globaltimer from solve start to each instance's convergence"},
             "max_relres": float(max(rel_all)),
+            "assembly_s_per_instance": assembly_s,
+            "s_per_solve_with_assembly": ms_per_step / 1e3 / args.count + assembly_s,
             "jacobi_fallback_instances": int(stats["fallback_instances"]) // args.steps,
             "jacobi_cg": cg,
             "roofline": roofline, "time_breakdown_ms": breakdown,
