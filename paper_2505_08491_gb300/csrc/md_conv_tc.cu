@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], TC_MMA_WARPS);  // every issuer's MMAs of the step
-            mbar_init(&tempty[i], TC_EPI_WARPS);
+            mbar_init(&tempty[i], KIND == 2 ? 4 : TC_EPI_WARPS);  // last layer: one channel group
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -440,7 +440,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         for (int c = 0; c < CH; ++c) bias[c] = (KIND == 2) ? a.bias[0] : a.bias[cg * CH + c];
         const bool writer = KIND != 2 || cg == 0;
         int it = 0, xcnt = 0;
-        bool ok = true;
+        // the last layer's single output channel is handled by channel group 0
+        // alone; the other epilogue warps go straight to the end
+        bool ok = KIND != 2 || cg == 0;
         for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
             const TcUnit U = a.units[un];
             if (!cnn_runs(a.io.st, U.inst)) continue;
