@@ -182,6 +182,15 @@ md_status md_cnn_backward(const md_cnn* c, int n_nodes_edge, int batch, const fl
  * r, z: device float, n.  Asynchronous. */
 md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream s);
 
+/* md_lift -- the 1D part of the preconditioner on its own (Section 3 eqs.
+ * (matrixC), (setB)): z1 = B11^{-1} r1 (tree factorisation) and its forcing on
+ * the 3D problem l = -beta M01 z1 = beta Pi^T W Psi z1.  With r1 the 1D load
+ * this is an element of the set B the training set is built from (Section 4.1).
+ * r: device float, n (only the 1D part r1 is read); z1: device float, n1
+ * (nullable); l: device float, n3 (zero on nodes the averaging does not
+ * reach).  Asynchronous. */
+md_status md_lift(const md_op* op, const float* r, float* z1, float* l, md_stream s);
+
 /* ---- solves -----------------------------------------------------------------
  * md_solve -- solve A x = b to ||b - A x||_2 / ||b||_2 <= tol.
  *   cnn != NULL: flexible GMRES(restart) (Section 4, Saad 1993), right-

@@ -69,6 +69,7 @@ SIGNATURES = {
     "md_cnn_forward": (st, [vp, i32, i32, vp, vp, vp]),
     "md_cnn_backward": (st, [vp, i32, i32, vp, vp, vp, vp, vp]),
     "md_precondition": (st, [vp, vp, vp, vp, vp]),
+    "md_lift": (st, [vp, vp, vp, vp, vp]),
     "md_solve": (st, [vp, vp, vp, vp, f64, i32, i32, C.POINTER(i32), C.POINTER(f64), vp]),
     "md_batch_create": (st, [i32, C.POINTER(vp), vp, i32, i32, C.POINTER(vp)]),
     "md_batch_destroy": (None, [vp]),

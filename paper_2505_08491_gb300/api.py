@@ -103,6 +103,14 @@ class Operator:
                                          _stream()), "md_precondition")
         return z
 
+    def lift(self, r: torch.Tensor):
+        """(l, z1): z1 = B11^{-1} r1 and its 3D forcing l = beta Pi^T W Psi z1
+        (float32, n3 and n1) for a float32 vector r of length n."""
+        l = torch.empty(self.n3, dtype=torch.float32, device="cuda")
+        z1 = torch.empty(self.n1, dtype=torch.float32, device="cuda")
+        L.check(L.load().md_lift(self._h, _ptr(r, torch.float32, self.n, "r"), _ptr(z1), _ptr(l), _stream()), "md_lift")
+        return l, z1
+
     def solve(self, b: torch.Tensor, x0: torch.Tensor | None = None, net: "Network | None" = None,
               tol: float = 1e-8, restart: int = 30, maxit: int = 10000):
         """FGMRES with the network preconditioner (net given) or Jacobi-CG.

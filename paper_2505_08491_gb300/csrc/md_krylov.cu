@@ -973,6 +973,30 @@ md_status launch_prec_input(const Tables& T, const InstDesc* d, const long long*
 
 // Standalone preconditioner application (one instance).
 __global__ void k_prec_setup(KState* st) { st[0].active = 1; }
+__global__ void k_lift_setup(KState* st) {
+    st[0].active = 1;
+    st[0].fallback = 0;
+    st[0].v3n2 = 0.0;
+}
+
+extern "C" md_status md_lift(const md_op* op, const float* r, float* z1, float* l, md_stream stream) {
+    if (!op || !r || !l) { md_set_error("md_lift: NULL argument"); return MD_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    md_batch* B = nullptr;
+    MD_TRY(op_batch(op, MD_SOLVER_FGMRES_JACOBI, 1, nullptr, &B));
+    const size_t smem = (size_t)B->max_n1 * 20;
+    if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lift_setup<<<1, 1, 0, s>>>(B->st);
+    // z1 = B11^{-1} r1 into the 1D part of the batch's first Z vector (scratch);
+    // l = beta Pi^T W Psi z1 into the operator's lift buffer (zero off the
+    // nodes the averaging reaches)
+    k_tree_lift<<<1, 256, smem, s>>>(B->d, B->off, r, B->Z, B->st);
+    MD_CHECK_LAUNCH();
+    const InstDesc& d = B->hdesc[0];
+    MD_CUDA(cudaMemcpyAsync(l, d.lift32, sizeof(float) * d.n3, cudaMemcpyDeviceToDevice, s));
+    if (z1) MD_CUDA(cudaMemcpyAsync(z1, B->Z + d.n3, sizeof(float) * d.n1, cudaMemcpyDeviceToDevice, s));
+    return MD_OK;
+}
 
 extern "C" md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream stream) {
     if (!op || !r || !z) { md_set_error("md_precondition: NULL argument"); return MD_ERR_ARG; }

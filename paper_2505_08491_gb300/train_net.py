@@ -7,8 +7,11 @@ radius U(0.005, 0.03), beta log-uniform in [1, 100].  Per graph 8 right-hand sid
 4 random vectors (N(0,1) on every unknown, zero on Dirichlet nodes; the
 high-frequency augmentation of Section 4.1.2) and the residuals of the
 Jacobi-preconditioned FGMRES(30) solve of the graph's own problem after 5,
-10, 20 and 30 iterations (residuals the solver actually meets).  Loss, AdamW
-and the cosine schedule run in md_train.
+10, 20 and 30 iterations (residuals the solver actually meets).  --set kry,
+hf and all build the paper's sets instead or in addition: b, the 3D forcing
+of the 1D problem (eq. (setB)), with the Krylov vectors q5..q8 of the 3D
+block started at b (Section 4.1.1) or with random vectors (Section 4.1.2).
+Loss, AdamW and the cosine schedule run in md_train.
 
 Usage: python -m paper_2505_08491_gb300.train_net --graphs 1024 --epochs 20
 """
@@ -39,18 +42,61 @@ def interior_mask(N):
     return ~(b[:, None, None] | b[None, :, None] | b[None, None, :]).ravel()
 
 
-def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees"):
+def krylov_samples(op, g: float):
+    """The paper's samples for one graph (Section 4.1, eq. (setB) and the
+    Krylov augmentation of Section 4.1.1): b = the 3D forcing of the 1D
+    problem (l = beta Pi^T W Psi B11^{-1} f1 for the 1D load f1), as the
+    residual [0; f1] that produces it, and q5..q8 of an orthonormal basis
+    q0 = b/||b||, q1, ..., q8 of the Krylov space of the 3D block C started
+    at b (modified Gram-Schmidt, twice, in FP64), as residuals [q; 0]."""
+    n3, n = op.n3, op.n
+    f1 = op.rhs(None, g)[n3:].float()
+    rb = torch.zeros(n, dtype=torch.float32, device="cuda")
+    rb[n3:] = f1
+    l, _ = op.lift(rb)
+    out = [rb]
+    q = [l.double() / torch.linalg.vector_norm(l.double())]
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(8):
+        u.zero_()
+        u[:n3] = q[-1]
+        w = op.apply(u)[:n3].clone()                 # C q: the 3D block, 1D input zero
+        for _ in range(2):
+            for qi in q:
+                w -= torch.dot(qi, w) * qi
+        q.append(w / torch.linalg.vector_norm(w))
+    for qi in q[5:9]:
+        r = torch.zeros(n, dtype=torch.float32, device="cuda")
+        r[:n3] = qi.float()
+        out.append(r)
+    return out
+
+
+def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees", kind: str = "residuals"):
+    """kind: 'residuals' (4 random vectors + 4 harvested FGMRES residuals per
+    graph), 'kry' ({b} and q5..q8, the paper's Krylov-augmented set), 'hf'
+    ({b} and 4 random vectors, the paper's high-frequency set) or 'all'
+    (residuals, b and q5..q8)."""
     insts = [mdgen.workload_instance(workload, first + i) for i in range(n_graphs)]
     ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
     samples, sample_op = [], []
     by_N = {}
     for i, (w, op) in enumerate(zip(insts, ops)):
         by_N.setdefault(w["N"], []).append(i)
+        if kind in ("kry", "hf", "all"):
+            ks = krylov_samples(op, w["g"])
+            for r in (ks if kind != "hf" else ks[:1]):
+                samples.append(r)
+                sample_op.append(i)
+        if kind == "kry":
+            continue
         mask = torch.from_numpy(np.concatenate([interior_mask(w["N"]), np.ones(op.n1, bool)])).cuda()
         for k in range(4):
             v = torch.from_numpy(mdgen.normal_vector(w["f_seed"] or 0, first + i, op.n, stream=k).astype(np.float32)).cuda()
             samples.append(v * mask)
             sample_op.append(i)
+    if kind in ("kry", "hf"):
+        return ops, samples, sample_op
     # harvested residuals, batched per grid size
     for N, idx in by_N.items():
         sub = [ops[i] for i in idx]
@@ -84,9 +130,11 @@ def main():
     ap.add_argument("--out", default=TRAINED)
     ap.add_argument("--init", default=None, help="start from this network file")
     ap.add_argument("--workload", default="train_trees", choices=["train_trees", "train_trees_wide"])
+    ap.add_argument("--set", default="residuals", choices=["residuals", "kry", "hf", "all"],
+                    help="training vectors per graph (see build_set)")
     args = ap.parse_args()
     t0 = time.time()
-    ops, samples, sample_op = build_set(args.graphs, workload=args.workload)
+    ops, samples, sample_op = build_set(args.graphs, workload=args.workload, kind=args.set)
     torch.cuda.synchronize()
     t1 = time.time()
     net = Network.load(args.init) if args.init else Network(random_params(args.seed))
@@ -95,7 +143,7 @@ def main():
     t2 = time.time()
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     net.save(args.out)
-    print(json.dumps({"workload": args.workload, "graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
+    print(json.dumps({"workload": args.workload, "set": args.set, "graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
                       "set_seconds": t1 - t0, "train_seconds": t2 - t1, "loss": hist}))
 
 

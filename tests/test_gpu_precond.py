@@ -75,3 +75,24 @@ def test_preconditioner_positive_homogeneity():
     z1 = op.precondition(torch.from_numpy(r).cuda(), net).cpu().numpy()
     z2 = op.precondition(torch.from_numpy(4.0 * r).cuda(), net).cpu().numpy()
     assert rel_l2(z2, 4.0 * z1) <= 1e-5
+
+
+@pytest.mark.parametrize("case", instance_cases(), ids=lambda c: c[0])
+def test_lift_matches_oracle(case):
+    """md_lift: z1 = B11^{-1} r1 and l = -beta M01 z1 against the oracle's
+    sparse LU of B11 and its M01 (FP32 tree sweeps and FP32 sums: 1e-5)."""
+    from paper_2505_08491_gb300 import Operator
+    name, N, g, beta, _ = case
+    p = fem.Problem(N, g, beta)
+    op = Operator(N, g, beta)
+    r = np.random.default_rng(6).standard_normal(p.n).astype(np.float32)
+    l, z1 = op.lift(torch.from_numpy(r).cuda())
+    z1_ref = solvers.BlockPreconditioner(p, mode="jacobi").B11_lu.solve(r[p.n3:].astype(np.float64))
+    l_ref = -beta * (p.M01 @ z1_ref)
+    assert rel_l2(z1.cpu().numpy(), z1_ref) <= 1e-5
+    assert rel_l2(l.cpu().numpy(), l_ref) <= 1e-5
+    # the input's 3D part does not enter
+    r2 = r.copy()
+    r2[:p.n3] = 0.0
+    l2, _ = op.lift(torch.from_numpy(r2).cuda())
+    assert torch.equal(l, l2)
