@@ -169,7 +169,14 @@ md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_diag, con
                            cudaStream_t s);
 
 // Tables (md_tables.cpp)
-md_status build_tables(const std::vector<const InstDesc*>& insts, Tables* T, std::vector<void*>* allocs);
+// vec_chunk: elements per block of the streaming vector kernels.  The Krylov
+// kernels of FGMRES carry per-block fixed costs (a reduction per basis
+// vector, the last-block combine) and prefer long chunks; the CG kernels
+// stream one or two vectors and prefer more, shorter blocks.
+#define MD_VEC_CHUNK_FGMRES 8192
+#define MD_VEC_CHUNK_CG 2048
+md_status build_tables(const std::vector<const InstDesc*>& insts, Tables* T, std::vector<void*>* allocs,
+                       int vec_chunk = MD_VEC_CHUNK_FGMRES);
 void free_tables(Tables* T);
 
 // device memory helpers

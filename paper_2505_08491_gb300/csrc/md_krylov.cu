@@ -25,6 +25,9 @@
 
 #define INNER_REL 1e-5
 #define STAGNATION_MIN_ITERS 10
+// threads of the per-instance tree solve + lift: the lift walks the touched grid
+// nodes with dependent loads, so it wants many threads in flight
+#define TREE_TB 1024
 
 struct md_batch {
     int ninst = 0;
@@ -205,41 +208,67 @@ __global__ void __launch_bounds__(MD_TB) k_resid(const Seg* __restrict__ seg, co
     }
 }
 
-// W (= V_{j+1} slot) dots: d_i = (W, V_i), i <= j, and ||W||^2
+// W (= V_{j+1} slot) dots: d_i = (W, V_i), i <= j, and ||W||^2.  JB >= j + 1
+// bounds the basis length at compile time: every thread keeps the products of
+// its elements with all basis vectors in registers, so the loads of all V_i
+// are independent and in flight together (one memory-bound pass over the
+// data), and the block reduces once at the end.
+template <int JB>
 __global__ void __launch_bounds__(MD_TB) k_dots(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                 const long long* __restrict__ off, const float* __restrict__ V,
                                                 long long total, int j, int pass, KState* st, double* part) {
-    __shared__ double sh[32 * (MD_KMAX + 2)];
-    __shared__ float sw[2048];
+    constexpr int NW = MD_TB / 32;
+    __shared__ double sh[(JB + 1) * NW];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
     if (!S.active || (pass == 1 && !S.reorth)) return;
     const long long o = off[sg.inst];
     const float* W = V + (long long)(j + 1) * total + o;
-    const int len = sg.end - sg.begin;
-    float wn = 0.f;
-    for (int e = threadIdx.x; e < len; e += blockDim.x) {
-        float w = W[sg.begin + e];
-        sw[e] = w;
-        wn = fmaf(w, w, wn);
+    const float* V0 = V + o;
+    // U elements per thread and loop trip, so U x (j + 1) independent loads are
+    // in flight before the first FMA needs one
+    constexpr int U = JB <= 8 ? 4 : (JB <= 16 ? 2 : 1);
+    float acc[JB + 1];
+#pragma unroll
+    for (int i = 0; i <= JB; ++i) acc[i] = 0.f;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += U * MD_TB) {
+        float w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * MD_TB;
+            w[u] = e < sg.end ? W[e] : 0.f;
+        }
+        // all loads of the trip first: instructions issue in order, so an FMA
+        // waiting on one load would hold back the loads behind it
+        float x[JB][U];
+#pragma unroll
+        for (int i = 0; i < JB; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * MD_TB;
+                x[i][u] = (i <= j && e < sg.end) ? V0[(long long)i * total + e] : 0.f;
+            }
+#pragma unroll
+        for (int i = 0; i < JB; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc[i] = fmaf(w[u], x[i][u], acc[i]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[JB] = fmaf(w[u], w[u], acc[JB]);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = 0; i <= j; ++i) {
-        const float* Vi = V + (long long)i * total + o + sg.begin;
-        float acc = 0.f;
-        for (int e = threadIdx.x; e < len; e += blockDim.x) acc = fmaf(sw[e], Vi[e], acc);
-        double x = warp_sum((double)acc);
-        if (lane == 0) sh[i * 32 + warp] = x;
-    }
-    {
-        double x = warp_sum((double)wn);
-        if (lane == 0) sh[(j + 1) * 32 + warp] = x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i <= JB; ++i) {
+        if (i <= j || i == JB) {
+            const double x = warp_sum((double)acc[i]);
+            if (lane == 0) sh[i * NW + warp] = x;
+        }
     }
     __syncthreads();
-    const int cnt = j + 2;
+    const int cnt = j + 2;  // dots i = 0..j, then ||W||^2
     for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        const int src = r <= j ? r : JB;
         double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += sh[r * 32 + w];
+        for (int w2 = 0; w2 < NW; ++w2) s += sh[src * NW + w2];
         part[(size_t)blockIdx.x * MD_MAXR + r] = s;
     }
     const InstRange rg = rng[sg.inst];
@@ -258,27 +287,53 @@ __global__ void __launch_bounds__(MD_TB) k_dots(const Seg* __restrict__ seg, con
     }
 }
 
-// W -= sum_i coef_i V_i ; ||W||^2, ||W_3D||^2
+// W -= sum_i coef_i V_i ; ||W||^2, ||W_3D||^2.  As k_dots: the basis length is
+// bounded by JB at compile time so the loads of all V_i are issued together.
+template <int JB>
 __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                   const long long* __restrict__ off, const InstDesc* __restrict__ D,
                                                   float* V, long long total, int j, int pass, KState* st, double* part) {
     __shared__ double sh[32 * 4];
-    __shared__ float sc[MD_KMAX + 1];
+    __shared__ float sc[JB];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
     if (!S.active || (pass == 1 && !S.reorth)) return;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) sc[i] = (float)S.coef[i];
+    for (int i = threadIdx.x; i < JB; i += blockDim.x) sc[i] = i <= j ? (float)S.coef[i] : 0.f;
     __syncthreads();
     const long long o = off[sg.inst];
     const int n3 = D[sg.inst].n3;
     float* W = V + (long long)(j + 1) * total + o;
+    const float* V0 = V + o;
+    constexpr int U = JB <= 8 ? 4 : (JB <= 16 ? 2 : 1);
     float a = 0.f, a3 = 0.f;
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
-        float w = W[e];
-        for (int i = 0; i <= j; ++i) w = fmaf(-sc[i], V[(long long)i * total + o + e], w);
-        W[e] = w;
-        a = fmaf(w, w, a);
-        if (e < n3) a3 = fmaf(w, w, a3);
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += U * MD_TB) {
+        float w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * MD_TB;
+            w[u] = e < sg.end ? W[e] : 0.f;
+        }
+        float x[JB][U];
+#pragma unroll
+        for (int i = 0; i < JB; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * MD_TB;
+                x[i][u] = (i <= j && e < sg.end) ? V0[(long long)i * total + e] : 0.f;
+            }
+#pragma unroll
+        for (int i = 0; i < JB; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) w[u] = fmaf(-sc[i], x[i][u], w[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) {
+                W[e] = w[u];
+                a = fmaf(w[u], w[u], a);
+                if (e < n3) a3 = fmaf(w[u], w[u], a3);
+            }
+        }
     }
     double v[2] = {(double)a, (double)a3};
     double flag;
@@ -295,6 +350,22 @@ __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, c
             S.v3n2 = sh[1];
         }
     }
+}
+
+// One Gram-Schmidt pass of Arnoldi step j, with the basis-length bound that
+// covers j + 1 vectors.
+template <int JB>
+static void launch_gs_pass(md_batch* B, int j, int pass, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    k_dots<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, B->total, j, pass, B->st, B->part);
+    k_update<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, B->total, j, pass, B->st,
+                                                 B->part);
+}
+static void launch_gs(md_batch* B, int j, int pass, cudaStream_t s) {
+    if (j < 8) launch_gs_pass<8>(B, j, pass, s);
+    else if (j < 16) launch_gs_pass<16>(B, j, pass, s);
+    else if (j < 32) launch_gs_pass<32>(B, j, pass, s);
+    else launch_gs_pass<MD_KMAX>(B, j, pass, s);
 }
 
 // Givens rotations, residual estimate, cycle exit; one thread per instance
@@ -384,7 +455,7 @@ __global__ void __launch_bounds__(MD_TB) k_jacobi(const Seg* __restrict__ seg, c
 // 1D block solve z1 = B11^{-1} v1 (tree LDL^T sweeps in shared memory), the
 // lift l = beta Pi^T W Psi z1 on the touched grid nodes, and the input norm
 // s = ||v0 + l|| from ||v0||^2 (st.v3n2) and the touched-node correction.
-__global__ void __launch_bounds__(256) k_tree_lift(const InstDesc* __restrict__ D, const long long* __restrict__ off,
+__global__ void __launch_bounds__(TREE_TB) k_tree_lift(const InstDesc* __restrict__ D, const long long* __restrict__ off,
                                                    const float* __restrict__ v, float* z, KState* st) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ double sh[32];
@@ -605,7 +676,7 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 1);
     MD_CHECK_LAUNCH();
     const size_t smem = (size_t)B->max_n1 * 20;
-    k_tree_lift<<<B->ninst, 256, smem, s>>>(B->d, B->off, vin, zout, B->st);
+    k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
     MD_CHECK_LAUNCH();
     MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, s));
     OutIO io{zout, B->off, vin, B->off, B->st, B->d};
@@ -628,8 +699,7 @@ static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
         MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
         rec(ev_at(B, j, EV_APPLY1), s);
         for (int pass = 0; pass < 2; ++pass) {
-            k_dots<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, tot, j, pass, B->st, B->part);
-            k_update<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, tot, j, pass, B->st, B->part);
+            launch_gs(B, j, pass, s);
         }
         k_givens<<<gb, 32, 0, s>>>(B->st, B->ninst, j, B->k);
         MD_CHECK_LAUNCH();
@@ -750,7 +820,7 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
     md_status st = MD_OK;
     auto chk = [&](md_status s2) { if (st == MD_OK) st = s2; };
     chk(dev_upload(&B->allocs, &B->d, B->hdesc.data(), B->hdesc.size()));
-    chk(build_tables(ptrs, &B->tabs, &B->allocs));
+    chk(build_tables(ptrs, &B->tabs, &B->allocs, solver == MD_SOLVER_CG_JACOBI ? MD_VEC_CHUNK_CG : MD_VEC_CHUNK_FGMRES));
     chk(dev_upload(&B->allocs, &B->off, B->hoff.data(), B->hoff.size()));
     chk(dev_alloc(&B->allocs, &B->x, (size_t)tot));
     chk(dev_alloc(&B->allocs, &B->b, (size_t)tot));
@@ -966,7 +1036,7 @@ md_status launch_prec_input(const Tables& T, const InstDesc* d, const long long*
     MD_CHECK_LAUNCH();
     const size_t smem = (size_t)max_n1 * 20;
     if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tree_lift<<<ninst, 256, smem, s>>>(d, off, v, z, st);
+    k_tree_lift<<<ninst, TREE_TB, smem, s>>>(d, off, v, z, st);
     MD_CHECK_LAUNCH();
     return MD_OK;
 }
@@ -990,7 +1060,7 @@ extern "C" md_status md_lift(const md_op* op, const float* r, float* z1, float* 
     // z1 = B11^{-1} r1 into the 1D part of the batch's first Z vector (scratch);
     // l = beta Pi^T W Psi z1 into the operator's lift buffer (zero off the
     // nodes the averaging reaches)
-    k_tree_lift<<<1, 256, smem, s>>>(B->d, B->off, r, B->Z, B->st);
+    k_tree_lift<<<1, TREE_TB, smem, s>>>(B->d, B->off, r, B->Z, B->st);
     MD_CHECK_LAUNCH();
     const InstDesc& d = B->hdesc[0];
     MD_CUDA(cudaMemcpyAsync(l, d.lift32, sizeof(float) * d.n3, cudaMemcpyDeviceToDevice, s));

@@ -27,9 +27,9 @@ md_status upload(const Builder& B, Table* T, std::vector<void*>* allocs) {
 
 }  // namespace
 
-md_status build_tables(const std::vector<const InstDesc*>& insts, Tables* T, std::vector<void*>* allocs) {
+md_status build_tables(const std::vector<const InstDesc*>& insts, Tables* T, std::vector<void*>* allocs, int vec_chunk) {
     Builder a, b, v, n3, tch;
-    const int CH_NODES = 1024, CH_Q = 256, CH_TOUCH = 256, CH_1D = 256, CH_VEC = 2048;
+    const int CH_NODES = 1024, CH_Q = 256, CH_TOUCH = 256, CH_1D = 256, CH_VEC = vec_chunk;
     for (int i = 0; i < (int)insts.size(); ++i) {
         const InstDesc& d = *insts[i];
         a.begin_inst(); a.add(i, 0, d.n3, CH_NODES); a.add(i, 1, d.nq, CH_Q); a.end_inst();
