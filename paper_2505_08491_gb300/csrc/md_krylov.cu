@@ -28,6 +28,8 @@
 // threads of the per-instance tree solve + lift: the lift walks the touched grid
 // nodes with dependent loads, so it wants many threads in flight
 #define TREE_TB 1024
+// elements per thread and loop trip of the CG streaming kernels
+#define CG_U 4
 
 struct md_batch {
     int ninst = 0;
@@ -580,7 +582,18 @@ __global__ void __launch_bounds__(MD_TB) k_cg_alpha(const Seg* __restrict__ seg,
     if (!S.active) return;
     const long long o = off[sg.inst];
     double v[1] = {0.0};
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) v[0] += p[o + e] * q[o + e];
+    // CG_U elements per thread and trip, loads before arithmetic (in-order issue)
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += CG_U * MD_TB) {
+        double pp[CG_U], qq[CG_U];
+#pragma unroll
+        for (int u = 0; u < CG_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            pp[u] = e < sg.end ? p[o + e] : 0.0;
+            qq[u] = e < sg.end ? q[o + e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < CG_U; ++u) v[0] += pp[u] * qq[u];
+    }
     double flag;
     reduce_values<1>(v, 1, part, blockIdx.x, rng[sg.inst], &S.counter[2], &flag, sh);
     if (flag == 1.0 && threadIdx.x == 0) {
@@ -602,12 +615,29 @@ __global__ void __launch_bounds__(MD_TB) k_cg_xr(const Seg* __restrict__ seg, co
     const double a = S.alpha_cg;
     const double* dinv = D[sg.inst].dinv64;
     double v[2] = {0.0, 0.0};
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
-        x[o + e] += a * p[o + e];
-        const double rr = r[o + e] - a * q[o + e];
-        r[o + e] = rr;
-        v[0] += rr * (dinv[e] * rr);
-        v[1] += rr * rr;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += CG_U * MD_TB) {
+        double xx[CG_U], pp[CG_U], rr0[CG_U], qq[CG_U], dd[CG_U];
+#pragma unroll
+        for (int u = 0; u < CG_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in = e < sg.end;
+            xx[u] = in ? x[o + e] : 0.0;
+            pp[u] = in ? p[o + e] : 0.0;
+            rr0[u] = in ? r[o + e] : 0.0;
+            qq[u] = in ? q[o + e] : 0.0;
+            dd[u] = in ? dinv[e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < CG_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) {
+                x[o + e] = xx[u] + a * pp[u];
+                const double rr = rr0[u] - a * qq[u];
+                r[o + e] = rr;
+                v[0] += rr * (dd[u] * rr);
+                v[1] += rr * rr;
+            }
+        }
     }
     double flag;
     reduce_values<2>(v, 2, part, blockIdx.x, rng[sg.inst], &S.counter[3], &flag, sh);
@@ -633,7 +663,22 @@ __global__ void __launch_bounds__(MD_TB) k_cg_p(const Seg* __restrict__ seg, con
     const long long o = off[sg.inst];
     const double bc = S.coef[0];
     const double* dinv = D[sg.inst].dinv64;
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) p[o + e] = dinv[e] * r[o + e] + bc * p[o + e];
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += CG_U * MD_TB) {
+        double dd[CG_U], rr[CG_U], pp[CG_U];
+#pragma unroll
+        for (int u = 0; u < CG_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in = e < sg.end;
+            dd[u] = in ? dinv[e] : 0.0;
+            rr[u] = in ? r[o + e] : 0.0;
+            pp[u] = in ? p[o + e] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < CG_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) p[o + e] = dd[u] * rr[u] + bc * pp[u];
+        }
+    }
 }
 
 // true residual after CG stopped: relres = ||b - A x|| / ||b||
