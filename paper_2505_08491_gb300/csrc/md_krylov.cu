@@ -53,7 +53,19 @@ struct md_batch {
     int max_n1 = 0;
     CnnWork* cw = nullptr;
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;     // CG: one chunk of iterations
+    // FGMRES: the iteration slots of a restart cycle in parts [part_end[p-1],
+    // part_end[p]), each a graph ending with a flag "some instance still
+    // iterates", and the restart step as its own graph; a cycle launches the
+    // next part only while the flag is set
+    std::vector<cudaGraphExec_t> parts;
+    std::vector<int> part_end;
+    std::vector<long long> part_kernels;
+    cudaGraphExec_t restart_graph = nullptr;
+    long long restart_kernels = 0;
+    int* d_any = nullptr;
+    int* h_any = nullptr;                // pinned host copy
+    int executed_slots = 0;              // slots the last cycle ran
     unsigned long long graph_cnn_uid = 0;  // network the graph was captured with (0: none)
     bool graph_prof = false;
     int graph_engine = -1;
@@ -729,11 +741,20 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     return MD_OK;
 }
 
-static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
+// 1 if some instance still iterates in the current restart cycle
+__global__ void k_any_active(const KState* st, int ninst, int* any) {
+    int a = 0;
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x) a |= st[i].active;
+    a = __syncthreads_or(a);
+    if (threadIdx.x == 0) *any = a;
+}
+
+// Iteration slots j in [j0, j1) of a restart cycle.
+static md_status launch_slots(md_batch* B, int j0, int j1, cudaStream_t s) {
     const Tables& T = B->tabs;
     const long long tot = B->total;
     const int gb = (B->ninst + 31) / 32;
-    for (int j = 0; j < B->k; ++j) {
+    for (int j = j0; j < j1; ++j) {
         const float* Vj = B->V + (long long)j * tot;
         float* Zj = B->Z + (long long)j * tot;
         float* W = B->V + (long long)(j + 1) * tot;
@@ -750,6 +771,17 @@ static md_status launch_cycle_fgmres(md_batch* B, cudaStream_t s) {
         MD_CHECK_LAUNCH();
         rec(ev_at(B, j, EV_ARN1), s);
     }
+    k_any_active<<<1, 1024, 0, s>>>(B->st, B->ninst, B->d_any);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+// Restart: x += Z y (least squares of the cycle), r = b - A x in FP64.
+static md_status launch_restart(md_batch* B, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    const long long tot = B->total;
+    const int gb = (B->ninst + 31) / 32;
+    rec(ev_restart(B, 0), s);
     k_lsq<<<gb, 32, 0, s>>>(B->st, B->ninst);
     k_xupd<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->Z, tot, B->x, B->st);
     MD_CHECK_LAUNCH();
@@ -779,18 +811,12 @@ static md_status launch_cycle_cg(md_batch* B, cudaStream_t s) {
     return MD_OK;
 }
 
-static md_status build_graph(md_batch* B) {
-    const int engine = B->cnn ? B->cnn->engine : 0;
-    const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
-    if (B->graph && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine) return MD_OK;
-    if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
-    if (B->profiling && B->ev.empty()) {
-        B->ev.resize((size_t)B->k * EV_PER_J + 2);
-        for (auto& e : B->ev) MD_CUDA(cudaEventCreate(&e));
-    }
+// Capture what `launch` issues on the capture stream into an executable graph.
+template <class F>
+static md_status capture_graph(md_batch* B, F&& launch, cudaGraphExec_t* out, long long* kernels) {
     cudaGraph_t g;
     MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
-    md_status st = (B->solver == MD_SOLVER_CG_JACOBI) ? launch_cycle_cg(B, B->cap) : launch_cycle_fgmres(B, B->cap);
+    md_status st = launch(B->cap);
     cudaError_t e = cudaStreamEndCapture(B->cap, &g);
     if (st != MD_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return st; }
     MD_CUDA(e);
@@ -798,14 +824,57 @@ static md_status build_graph(md_batch* B) {
     cudaGraphGetNodes(g, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
     if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
-    B->graph_kernels = 0;
+    *kernels = 0;
     for (auto nd : nodes) {
         cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) B->graph_kernels++;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++*kernels;
     }
-    e = cudaGraphInstantiate(&B->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     MD_CUDA(e);
+    return MD_OK;
+}
+
+static void destroy_graphs(md_batch* B) {
+    if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+    for (auto g : B->parts) cudaGraphExecDestroy(g);
+    B->parts.clear();
+    B->part_end.clear();
+    B->part_kernels.clear();
+    if (B->restart_graph) { cudaGraphExecDestroy(B->restart_graph); B->restart_graph = nullptr; }
+}
+
+static md_status build_graph(md_batch* B) {
+    const int engine = B->cnn ? B->cnn->engine : 0;
+    const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
+    const bool have = B->solver == MD_SOLVER_CG_JACOBI ? B->graph != nullptr : B->restart_graph != nullptr;
+    if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine) return MD_OK;
+    destroy_graphs(B);
+    if (B->profiling && B->ev.empty()) {
+        B->ev.resize((size_t)B->k * EV_PER_J + 2);
+        for (auto& e : B->ev) MD_CUDA(cudaEventCreate(&e));
+    }
+    if (B->solver == MD_SOLVER_CG_JACOBI) {
+        MD_TRY(capture_graph(B, [&](cudaStream_t s) { return launch_cycle_cg(B, s); }, &B->graph, &B->graph_kernels));
+    } else {
+        // slot parts [0, 8), [8, 16), [16, k): a batch that converges early in a
+        // cycle skips the empty slots of the later parts
+        const int bounds[] = {8, 16, B->k};
+        int j0 = 0;
+        for (int b : bounds) {
+            const int j1 = std::min(b, B->k);
+            if (j1 <= j0) continue;
+            cudaGraphExec_t gx = nullptr;
+            long long nk = 0;
+            MD_TRY(capture_graph(B, [&](cudaStream_t s) { return launch_slots(B, j0, j1, s); }, &gx, &nk));
+            B->parts.push_back(gx);
+            B->part_end.push_back(j1);
+            B->part_kernels.push_back(nk);
+            j0 = j1;
+        }
+        MD_TRY(capture_graph(B, [&](cudaStream_t s) { return launch_restart(B, s); }, &B->restart_graph,
+                             &B->restart_kernels));
+    }
     B->graph_cnn_uid = uid;
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
@@ -822,14 +891,14 @@ static void accumulate_events(md_batch* B) {
         }
         return (double)ms;
     };
-    for (int j = 0; j < B->k; ++j) {
+    for (int j = 0; j < B->executed_slots; ++j) {
         B->stats.prec_ms += el(ev_at(B, j, EV_PRE0), ev_at(B, j, EV_APPLY0));
         B->stats.conv_hidden_ms += el(ev_at(B, j, EV_CONV0), ev_at(B, j, EV_CONV1));
         B->stats.apply_ms += el(ev_at(B, j, EV_APPLY0), ev_at(B, j, EV_APPLY1));
         B->stats.arnoldi_ms += el(ev_at(B, j, EV_APPLY1), ev_at(B, j, EV_ARN1));
         if (B->solver == MD_SOLVER_FGMRES_CNN) B->stats.conv_hidden_launches += 4;
     }
-    B->stats.restart_ms += el(ev_at(B, B->k - 1, EV_ARN1), ev_restart(B, 1));
+    B->stats.restart_ms += el(ev_restart(B, 0), ev_restart(B, 1));
 }
 
 extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const md_cnn* cnn, md_solver solver,
@@ -880,6 +949,8 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
     chk(dev_alloc(&B->allocs, &B->st, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->part, (size_t)std::max(B->tabs.vec.nblocks, 1) * MD_MAXR));
     chk(dev_alloc(&B->allocs, &B->ndone, 1));
+    chk(dev_alloc(&B->allocs, &B->d_any, 1));
+    if (st == MD_OK && cudaMallocHost(&B->h_any, sizeof(int)) != cudaSuccess) chk(MD_ERR_OOM);
     chk(dev_alloc(&B->allocs, &B->res.iters, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->res.net_iters, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->res.relres, (size_t)n_ops));
@@ -908,7 +979,8 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
 extern "C" void md_batch_destroy(md_batch* B) {
     if (!B) return;
     for (auto e : B->ev) cudaEventDestroy(e);
-    if (B->graph) cudaGraphExecDestroy(B->graph);
+    destroy_graphs(B);
+    if (B->h_any) cudaFreeHost(B->h_any);
     if (B->cap) cudaStreamDestroy(B->cap);
     cnn_work_destroy(B->cw);
     dev_free_all(&B->allocs);
@@ -946,9 +1018,24 @@ static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
         MD_CUDA(cudaStreamSynchronize(s));
         if (c > 0) accumulate_events(B);
         if (ndone >= B->ninst) break;
-        MD_CUDA(cudaGraphLaunch(B->graph, s));
+        if (B->solver == MD_SOLVER_CG_JACOBI) {
+            MD_CUDA(cudaGraphLaunch(B->graph, s));
+            B->stats.kernel_launches += B->graph_kernels;
+        } else {
+            for (size_t p = 0; p < B->parts.size(); ++p) {
+                MD_CUDA(cudaGraphLaunch(B->parts[p], s));
+                B->stats.kernel_launches += B->part_kernels[p];
+                B->executed_slots = B->part_end[p];
+                if (p + 1 < B->parts.size()) {
+                    MD_CUDA(cudaMemcpyAsync(B->h_any, B->d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
+                    MD_CUDA(cudaStreamSynchronize(s));
+                    if (!*B->h_any) break;
+                }
+            }
+            MD_CUDA(cudaGraphLaunch(B->restart_graph, s));
+            B->stats.kernel_launches += B->restart_kernels;
+        }
         B->stats.cycles += 1;
-        B->stats.kernel_launches += B->graph_kernels;
     }
     if (B->cw) {
         int err = 0;
