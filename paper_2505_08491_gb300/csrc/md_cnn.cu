@@ -371,10 +371,11 @@ __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restri
         } else {
             float* o = io.out + io.off[sg.inst];
             if (mode == CONV_PREC) {
+                // Dirichlet nodes were written by the input pack (z0 = v0)
                 const bool bd = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
                 const double s = io.st[sg.inst].s;
                 const float scale = (float)(s / io.D[sg.inst].alpha);
-                o[n] = bd ? io.vin[io.vin_off[sg.inst] + n] : scale * acc[0];
+                if (!bd) o[n] = scale * acc[0];
             } else {
                 o[n] = acc[0];
             }
@@ -479,9 +480,12 @@ md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvO
 }
 
 // ---- input packing -------------------------------------------------------------------
+// Network input X = [v0 / s, l / s, d] in the padded BF16 layout; and the
+// preconditioner output on Dirichlet nodes, z0 = v0 (the last layer writes
+// the interior nodes only).
 __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__ Ns, const InstDesc* __restrict__ D,
                             const float* __restrict__ v, const long long* __restrict__ voff, const KState* __restrict__ st,
-                            __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off) {
+                            __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off, float* __restrict__ z) {
     const Seg sg = seg[blockIdx.x];
     if (!cnn_runs(st, sg.inst)) return;
     const InstDesc& d = D[sg.inst];
@@ -501,12 +505,13 @@ __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__
         }
         c[2] = d.dist[n];
         *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
+        if (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N) z[voff[sg.inst] + n] = vi[n];
     }
 }
 
 md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
-                        cudaStream_t s) {
-    k_pack_prec<<<w->nodes.nblocks, 128, 0, s>>>(w->nodes.seg, w->N, D, v, voff, st, w->x0, w->off_x0);
+                        float* z, cudaStream_t s) {
+    k_pack_prec<<<w->nodes.nblocks, 128, 0, s>>>(w->nodes.seg, w->N, D, v, voff, st, w->x0, w->off_x0, z);
     MD_CHECK_LAUNCH();
     return MD_OK;
 }

@@ -58,6 +58,7 @@ md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A
 md_status cnn_upload(md_cnn* c);
 // X0 = [v0 / s, l / s, d] from a preconditioner input (instance 3D part at v + voff[i])
 md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
+                        float* z,
                         cudaStream_t s);
 // X0 from a raw channel-major FP32 input (sample, channel, z, y, x)
 md_status cnn_pack_raw(CnnWork* w, const float* X, cudaStream_t s);

@@ -198,7 +198,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     constexpr int NCOL = (KIND == 2) ? 16 : 96;   // MMA N (accumulator columns per tile)
     constexpr int WIMG = tc_wimg_bytes(KIND);
     constexpr uint32_t IDESC = idesc_bf16(128, NCOL);
-    constexpr int TMEM_COLS = (2 * TPS * NCOL <= 128) ? 128 : ((2 * TPS * NCOL <= 256) ? 256 : 512);
+    // accumulator ring: two stages, eight for the last layer, whose steps are
+    // short (6 MMAs per tile) and would otherwise wait on the hand-over latency
+    constexpr int NBUF = (KIND == 2) ? TC_NBUF_MAX : 2;
+    constexpr int TMEM_COLS = (NBUF * TPS * NCOL <= 128) ? 128 : ((NBUF * TPS * NCOL <= 256) ? 256 : 512);
+    static_assert(NBUF * TPS * NCOL <= 512, "accumulator ring exceeds tensor memory");
     extern __shared__ __align__(1024) unsigned char sm[];
     const int W = a.W, NS = a.NS;
     const int slot_bytes = CIN8 * W * 16;
@@ -207,11 +211,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)NS * slot_bytes);
     uint64_t* full = bars;             // [NS]
     uint64_t* empty = bars + NS;       // [NS]
-    uint64_t* tfull = bars + 2 * NS;   // [2]
-    uint64_t* tempty = bars + 2 * NS + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6);
+    uint64_t* tfull = bars + 2 * NS;   // [NBUF]
+    uint64_t* tempty = bars + 2 * NS + TC_NBUF_MAX;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 2 * TC_NBUF_MAX + 2);
     // warp-boundary exchange of the epilogue: [buffer][quarter][half][2 x 16]
-    float* xch = reinterpret_cast<float*>(bars + 2 * NS + 8);
+    float* xch = reinterpret_cast<float*>(bars + 2 * NS + 2 * TC_NBUF_MAX + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // inside a solve most late iteration slots have no active instance: leave
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], TC_MMA_WARPS);  // every issuer releases the window
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&tfull[i], TC_MMA_WARPS);  // every issuer's MMAs of the step
             mbar_init(&tempty[i], KIND == 2 ? 4 : TC_EPI_WARPS);  // last layer: one channel group
         }
@@ -324,8 +328,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         const int sw = gs, qw = gq;
                         if (!win_ready && !mbar_wait(&full[sw], qw & 1, a.err)) { ok = false; break; }
                         win_ready = false;
-                        const int bsel = it & 1;
-                        if (!mbar_wait(&tempty[bsel], ((it >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+                        const int bsel = it % NBUF;
+                        if (!mbar_wait(&tempty[bsel], ((it / NBUF) & 1) ^ 1, a.err)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sbu = (rb0 >> 4) + (uint32_t)(sw * slot_bytes >> 4);
 #pragma unroll
@@ -368,8 +372,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     }
                     if (!next_ready && !mbar_wait(&full[s2w], q2w & 1, a.err)) { ok = false; break; }
                     next_ready = false;
-                    const int bsel = it & 1;
-                    if (!mbar_wait(&tempty[bsel], ((it >> 1) & 1) ^ 1, a.err)) { ok = false; break; }
+                    const int bsel = it % NBUF;
+                    if (!mbar_wait(&tempty[bsel], ((it / NBUF) & 1) ^ 1, a.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sbu[3] = {(rb0 >> 4) + (uint32_t)(s0w * slot_bytes >> 4), (rb0 >> 4) + (uint32_t)(s1w * slot_bytes >> 4),
                                              (rb0 >> 4) + (uint32_t)(s2w * slot_bytes >> 4)};  // window slots, in 16-byte units
@@ -426,7 +430,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 adv(gs, gq, 2);  // the unit's last two windows
             }
             // MMAs in flight complete before the tensor memory is freed
-            if (it > 0) mbar_wait(&tfull[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err);
+            if (it > 0) mbar_wait(&tfull[(it - 1) % NBUF], ((it - 1) / NBUF) & 1, a.err);
         }
     } else {
         // ---------------- epilogue: warps 2 .. 2+TC_EPI_WARPS-1; TMEM lane
@@ -467,15 +471,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 // p + 1 - dz.  acc_m1 / acc_0: partial sums of planes p - 1 and p
                 // before window p; plane p - 1 is complete after it.
                 float acc_m1[TPS], acc_0[TPS];
+                int inplane[TPS];  // grid index of this lane's row within a plane
+                bool edge[TPS];    // row on the x or y faces of the grid
 #pragma unroll
-                for (int ut = 0; ut < TPS; ++ut) acc_m1[ut] = acc_0[ut] = 0.0f;
+                for (int ut = 0; ut < TPS; ++ut) {
+                    acc_m1[ut] = acc_0[ut] = 0.0f;
+                    const int xp = rr[ut] % Pd, yp = rr[ut] / Pd;
+                    inplane[ut] = (xp - 1) + M * (yp - 1);
+                    edge[ut] = xp == 1 || xp == M || yp == 1 || yp == M;
+                }
                 const int nwin = U.z1 - U.z0 + 2;
                 float* ov = a.io.out + a.io.off[U.inst];
                 const float scale = (a.mode == CONV_PREC) ? (float)(a.io.st[U.inst].s / a.io.D[U.inst].alpha) : 1.0f;
                 for (int k = 0; k < nwin; ++k, ++it) {
                     const int pz = U.z0 - 1 + k;  // plane of this window
-                    const int bsel = it & 1;
-                    ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err));
+                    const int bsel = it % NBUF;
+                    ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it / NBUF) & 1, a.err));
                     if (!ok) break;
                     tc_fence_after();
                     float v[TPS][16];
@@ -522,13 +533,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         acc_0[ut] = P[0];
                         const int z = pz - 1;
                         if (!val[ut] || z < U.z0 || z >= U.z1) continue;
-                        const int xp = rr[ut] % Pd, yp = rr[ut] / Pd;
-                        const int ii = xp - 1, jj = yp - 1, kk = z - 1;
-                        const int n = ii + M * (jj + M * kk);
+                        const int kk = z - 1;
+                        const int n = inplane[ut] + M * M * kk;
                         const float o = done + bias[0];
                         if (a.mode == CONV_PREC) {
-                            const bool bd = (ii == 0 || ii == N || jj == 0 || jj == N || kk == 0 || kk == N);
-                            ov[n] = bd ? a.io.vin[a.io.vin_off[U.inst] + n] : scale * o;
+                            // Dirichlet nodes were written by the input pack (z0 = v0)
+                            if (!edge[ut] && kk != 0 && kk != N) ov[n] = scale * o;
                         } else {
                             ov[n] = o;
                         }
@@ -536,10 +546,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 }
             } else {
             for (int z = U.z0; z < U.z1; ++z, ++it) {
-                const int bsel = it & 1;
+                const int bsel = it % NBUF;
                 // every warp waits for the accumulator itself; the group leaves
                 // together if any of its warps gave up
-                ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it >> 1) & 1, a.err));
+                ok = nbar_and(1 + cg, 4 * 32, mbar_wait(&tfull[bsel], (it / NBUF) & 1, a.err));
                 if (!ok) break;
                 tc_fence_after();
                 // this lane's three column groups (dx = -1, 0, +1) of every tile of
@@ -665,7 +675,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 // host side
 int tc_smem_bytes(int kind, int W, int ns) {
     const int cin8 = kind == 1 ? 1 : 4;
-    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 8) * 8 + 2 * TC_TPS_MAX * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH * 4 + 16;
+    return tc_align(tc_wimg_bytes(kind)) + ns * cin8 * W * 16 + (2 * ns + 2 * TC_NBUF_MAX + 4) * 8 +
+           2 * TC_TPS_MAX * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH * 4 + 16;
 }
 
 // Ring slots that fit next to the hidden-layer weights (at most 8).

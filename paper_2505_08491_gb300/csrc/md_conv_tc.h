@@ -16,6 +16,7 @@ struct TcUnit { int inst, s0, z0, z1; };
 #define TC_MMA2_WARP (2 + TC_EPI_WARPS)      // warp index of the second issuer
 #define TC_THREADS (32 * (1 + TC_MMA_WARPS + TC_EPI_WARPS))  // + producer warp
 #define TC_TPS_MAX 2                         // tiles per plane step (epilogue exchange buffers)
+#define TC_NBUF_MAX 8                        // deepest accumulator ring (last layer)
 
 struct TcArgs {
     const __nv_bfloat16* in;     // activation buffer (chunk-major padded layout)

@@ -735,7 +735,7 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     const size_t smem = (size_t)B->max_n1 * 20;
     k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
     MD_CHECK_LAUNCH();
-    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, s));
+    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, zout, s));
     OutIO io{zout, B->off, vin, B->off, B->st, B->d};
     MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
     return MD_OK;

@@ -524,7 +524,7 @@ static md_status minibatch(const md_cnn* c, TrainWork* t, const std::vector<cons
         MD_CHECK_LAUNCH();
         // preconditioner input: ||r0||^2, 1D solve + lift, s, packed X
         MD_TRY(launch_prec_input(T, t->d, t->voff, t->rv, t->yv, t->st, B, t->max_n1, t->part3, s));
-        MD_TRY(cnn_pack_prec(t->cw, t->d, t->rv, t->voff, t->st, s));
+        MD_TRY(cnn_pack_prec(t->cw, t->d, t->rv, t->voff, t->st, t->yv, s));  // y is overwritten by the raw forward
         OutIO io{t->yv, t->voff, nullptr, nullptr, nullptr, nullptr};
         MD_TRY(cnn_forward_train(c, t->cw, t->A, t->Z, io, s));
         k_mask_grid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, t->d, t->voff, t->yv, 1);
