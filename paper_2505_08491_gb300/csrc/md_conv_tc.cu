@@ -559,17 +559,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                 for (int ut = 0; ut < TPS; ++ut) {
                     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
-                    if constexpr (KIND == 2) {
-                        float v[8];
-                        tmem_ld_nowait<8>(tb, v);
-                        dm[ut][0] = v[0];
-                        dc[ut][0] = v[1];
-                        dp[ut][0] = v[2];
-                    } else {
-                        tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm[ut]);
-                        tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc[ut]);
-                        tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp[ut]);
-                    }
+                    tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm[ut]);
+                    tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc[ut]);
+                    tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp[ut]);
                 }
                 tmem_wait_ld();
                 tc_fence_before();
@@ -584,20 +576,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                 for (int ut = 0; ut < TPS; ++ut) {
                     float* mine = xb + ((ut * 4 + q) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
-                    if constexpr (KIND == 2) {
-                        if (lane == 31) mine[0] = dm[ut][0];
-                        if (lane == 0) mine[TC_EPI_CH] = dp[ut][0];
-                    } else {
-                        static_assert(CH == 8, "the exchange moves 8 channels as two float4");
-                        float4* m4 = reinterpret_cast<float4*>(mine);
-                        if (lane == 31) {
-                            m4[0] = make_float4(dm[ut][0], dm[ut][1], dm[ut][2], dm[ut][3]);
-                            m4[1] = make_float4(dm[ut][4], dm[ut][5], dm[ut][6], dm[ut][7]);
-                        }
-                        if (lane == 0) {
-                            m4[2] = make_float4(dp[ut][0], dp[ut][1], dp[ut][2], dp[ut][3]);
-                            m4[3] = make_float4(dp[ut][4], dp[ut][5], dp[ut][6], dp[ut][7]);
-                        }
+                    static_assert(CH == 8, "the exchange moves 8 channels as two float4");
+                    float4* m4 = reinterpret_cast<float4*>(mine);
+                    if (lane == 31) {
+                        m4[0] = make_float4(dm[ut][0], dm[ut][1], dm[ut][2], dm[ut][3]);
+                        m4[1] = make_float4(dm[ut][4], dm[ut][5], dm[ut][6], dm[ut][7]);
+                    }
+                    if (lane == 0) {
+                        m4[2] = make_float4(dp[ut][0], dp[ut][1], dp[ut][2], dp[ut][3]);
+                        m4[3] = make_float4(dp[ut][4], dp[ut][5], dp[ut][6], dp[ut][7]);
                     }
                 }
                 nbar_sync(1 + cg, 4 * 32);
@@ -608,10 +595,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     const float* next = xb + ((ut * 4 + ((q + 1) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
                     // lanes 0 and 31 take their missing neighbour from the adjacent quarter
                     float pv[CH], nx[CH];
-                    if constexpr (KIND == 2) {
-                        pv[0] = prev[0];
-                        nx[0] = next[0];
-                    } else {
+                    {
                         const float4 p0 = reinterpret_cast<const float4*>(prev)[0], p1 = reinterpret_cast<const float4*>(prev)[1];
                         const float4 n0 = reinterpret_cast<const float4*>(next)[0], n1 = reinterpret_cast<const float4*>(next)[1];
                         pv[0] = p0.x; pv[1] = p0.y; pv[2] = p0.z; pv[3] = p0.w;
@@ -630,32 +614,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     }
                     if (!val[ut]) continue;
                     const int p = z * P2 + rr[ut];
-                    if constexpr (KIND != 2) {
 #pragma unroll
-                        for (int c8 = 0; c8 < CH / 8; ++c8) {
-                            const int at = ((cg * (CH / 8) + c8) * P + p) * 8;
-                            if (zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
-                            float gl[8];
+                    for (int c8 = 0; c8 < CH / 8; ++c8) {
+                        const int at = ((cg * (CH / 8) + c8) * P + p) * 8;
+                        if (zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
+                        float gl[8];
 #pragma unroll
-                            for (int e = 0; e < 8; e += 2) {
-                                gl[e] = o[c8 * 8 + e];
-                                gl[e + 1] = o[c8 * 8 + e + 1];
-                                gelu_fast2(gl[e], gl[e + 1]);
-                            }
-                            *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
+                        for (int e = 0; e < 8; e += 2) {
+                            gl[e] = o[c8 * 8 + e];
+                            gl[e + 1] = o[c8 * 8 + e + 1];
+                            gelu_fast2(gl[e], gl[e + 1]);
                         }
-                    } else {
-                        const int xp = rr[ut] % Pd, yp = rr[ut] / Pd;
-                        const int ii = xp - 1, jj = yp - 1, kk = z - 1;
-                        const int n = ii + M * (jj + M * kk);
-                        float* ov = a.io.out + a.io.off[U.inst];
-                        if (a.mode == CONV_PREC) {
-                            const bool bd = (ii == 0 || ii == N || jj == 0 || jj == N || kk == 0 || kk == N);
-                            const float scale = (float)(a.io.st[U.inst].s / a.io.D[U.inst].alpha);
-                            ov[n] = bd ? a.io.vin[a.io.vin_off[U.inst] + n] : scale * o[0];
-                        } else {
-                            ov[n] = o[0];
-                        }
+                        *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
                     }
                 }
             }
