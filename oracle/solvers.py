@@ -124,31 +124,46 @@ class BlockPreconditioner:
                     on interior nodes (alpha as in the training loss of Section 5.1,
                     evaluated for this instance), z0 = r0 on Dirichlet nodes;
         'jacobi' -- z0 = b0 / diag(C).
+
+    order='lower' inverts the block lower-triangular part instead (the other
+    reading of how the 1D unknowns follow from the network): the 3D block
+    first with the 1D part absent from its right-hand side (l = 0, b0 = r0),
+    then z1 = B11^{-1} (r1 - beta M10 z0) = B11^{-1} (r1 + beta Psi^T W Pi z0).
     """
 
-    def __init__(self, prob, mode: str = "cnn", params=None, bf16: bool = True):
+    def __init__(self, prob, mode: str = "cnn", params=None, bf16: bool = True, order: str = "upper"):
+        if order not in ("upper", "lower"):
+            raise ValueError("order must be 'upper' or 'lower'")
         self.p = prob
         self.mode = mode
         self.params = params
         self.bf16 = bf16
+        self.order = order
         self.B11_lu = spla.splu(prob.B11.tocsc())
         self.C_lu = spla.splu(prob.C.tocsc()) if mode == "exact" else None
 
     def lift(self, z1):
         return -self.p.beta * (self.p.M01 @ z1)
 
+    def solve3(self, r0, l):
+        """The 3D block solve for right-hand side r0 + l (l = the lifted 1D part)."""
+        p = self.p
+        b0 = r0 + l
+        if self.mode == "exact":
+            return self.C_lu.solve(b0)
+        if self.mode == "jacobi":
+            return b0 / p.C.diagonal()
+        return network_solve(p, r0, l, self.params, self.bf16)
+
     def __call__(self, r):
         p = self.p
         r0, r1 = r[:p.n3], r[p.n3:]
+        if self.order == "lower":
+            z0 = self.solve3(r0, np.zeros_like(r0))
+            z1 = self.B11_lu.solve(r1 - p.beta * (p.M01.T @ z0))
+            return np.concatenate([z0, z1])
         z1 = self.B11_lu.solve(r1)
-        l = self.lift(z1)
-        b0 = r0 + l
-        if self.mode == "exact":
-            z0 = self.C_lu.solve(b0)
-        elif self.mode == "jacobi":
-            z0 = b0 / p.C.diagonal()
-        else:
-            z0 = network_solve(p, r0, l, self.params, self.bf16)
+        z0 = self.solve3(r0, self.lift(z1))
         return np.concatenate([z0, z1])
 
 

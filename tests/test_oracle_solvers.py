@@ -87,6 +87,24 @@ def test_block_preconditioner_inverts_upper_triangular_part(tree8):
     assert abs(L[p.n3:, p.n3:]).max() == 0
 
 
+def test_block_preconditioner_lower_order_inverts_lower_triangular_part(tree8):
+    """order='lower' with the exact 3D solve is the inverse of [[C, 0], [A10, B11]],
+    A10 the 1-0 block of A; its off-diagonal block is the one the upper order
+    drops, and both orders give the same iterations on this instance (the
+    reading that builds only the upper one on the GPU)."""
+    p = tree8
+    Lw = sp.bmat([[p.C, None], [p.A[p.n3:, :p.n3], p.B11]], format="csr")
+    Q = solvers.BlockPreconditioner(p, mode="exact", order="lower")
+    x = np.random.default_rng(3).standard_normal(p.n)
+    assert np.linalg.norm(Q(Lw @ x) - x) / np.linalg.norm(x) < 1e-10
+    assert abs((p.A - Lw)[p.n3:, :]).max() == 0
+    b = p.rhs(p.source(7), 1.0)
+    _, it_u, rel_u = solvers.fgmres(p.A, b, solvers.BlockPreconditioner(p, mode="exact"), 1e-8)
+    _, it_l, rel_l = solvers.fgmres(p.A, b, Q, 1e-8)
+    assert rel_u <= 1e-8 and rel_l <= 1e-8
+    assert abs(it_u - it_l) <= 2
+
+
 def test_cnn_preconditioner_homogeneous(tree8):
     """P(c v) = c P(v) for c > 0 (input normalisation by s = ||b0||)."""
     params = cnn.init_params(3)
