@@ -167,6 +167,7 @@ def bench_config(args, grid_nodes):
     return {"workload": f"{args.workload}: {args.count} {WORKLOAD_TEXT[args.workload]}; one batched "
                         f"FGMRES({restart_of(args.workload)}) solve per step, BF16 network, tol 1e-8 (true FP64 residual)",
             "instances_per_gpu": args.count, "grid_nodes_per_gpu": grid_nodes,
+            "prec_order": getattr(args, "prec_order", "upper"),
             "l2": "working set > L2, 256 MB flush between steps", "precision":
             "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"}
 
@@ -208,6 +209,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--count", type=int, default=None, help="instances per GPU (default: the workload's)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--prec-order", default="upper", choices=["upper", "lower"],
+                    help="block order of the preconditioner (the paper's upper-triangular one by default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
@@ -251,6 +254,7 @@ def main():
     b_all = torch.cat(bs).contiguous()
     x_all = torch.zeros_like(b_all)
     B = Batch(ops, "fgmres_cnn", net, restart=restart_of(args.workload))
+    B.set_prec_order(args.prec_order)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 

@@ -182,6 +182,14 @@ md_status md_cnn_backward(const md_cnn* c, int n_nodes_edge, int batch, const fl
  * r, z: device float, n.  Asynchronous. */
 md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream s);
 
+/* md_precondition_lower -- the block lower-triangular order of the same
+ * preconditioner (the other reading of how the network and the 1D solve are
+ * composed in eq. (twosteps)): the network first on [r0/s, 0, d_h] with
+ * s = ||r0||, z0 = (s / alpha) N(X) on interior nodes and r0 on Dirichlet
+ * nodes; then z1 = B11^{-1} (r1 + beta Psi^T W Pi z0).  Arguments as
+ * md_precondition; cnn must not be NULL.  Asynchronous. */
+md_status md_precondition_lower(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream s);
+
 /* md_lift -- the 1D part of the preconditioner on its own (Section 3 eqs.
  * (matrixC), (setB)): z1 = B11^{-1} r1 (tree factorisation) and its forcing on
  * the 3D problem l = -beta M01 z1 = beta Pi^T W Psi z1.  With r1 the 1D load
@@ -254,6 +262,9 @@ typedef struct {
     long long fallback_instances; /* network solves whose instance switched to Jacobi */
 } md_batch_stats_t;
 md_status md_batch_set_profiling(md_batch* b, int enable);
+/* lower = 1: the network-preconditioned batch uses md_precondition_lower's
+ * block order; 0 (default): the paper's upper-triangular order. */
+md_status md_batch_set_prec_order(md_batch* b, int lower);
 md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
 md_status md_batch_reset_stats(md_batch* b);
 

@@ -96,8 +96,19 @@ class Operator:
                                           _ptr(out, u.dtype, self.n, "out"), _stream()), "md_apply_noalloc")
         return out
 
-    def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None) -> torch.Tensor:
+    def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None, order: str = "upper") -> torch.Tensor:
+        """z = Q r: block upper-triangular order (the paper's), or order='lower'
+        (network first, then the 1D solve); net=None gives Jacobi."""
         z = torch.empty_like(r) if out is None else out
+        if order == "lower":
+            if net is None:
+                raise ValueError("the lower order needs a network")
+            L.check(L.load().md_precondition_lower(self._h, net.handle, _ptr(r, torch.float32, self.n, "r"),
+                                                   _ptr(z, torch.float32, self.n, "z"), _stream()),
+                    "md_precondition_lower")
+            return z
+        if order != "upper":
+            raise ValueError("order must be 'upper' or 'lower'")
         L.check(L.load().md_precondition(self._h, net.handle if net is not None else None,
                                          _ptr(r, torch.float32, self.n, "r"), _ptr(z, torch.float32, self.n, "z"),
                                          _stream()), "md_precondition")
@@ -287,6 +298,12 @@ class Batch:
                                             it, rr, _stream()),
                     "md_batch_solve", allow=(L.MD_OK, L.MD_NOT_CONVERGED))
         return list(it), list(rr), s == L.MD_OK
+
+    def set_prec_order(self, order: str):
+        """'upper' (the paper's block order, default) or 'lower'."""
+        if order not in ("upper", "lower"):
+            raise ValueError("order must be 'upper' or 'lower'")
+        L.check(L.load().md_batch_set_prec_order(self._h, 1 if order == "lower" else 0), "md_batch_set_prec_order")
 
     def set_profiling(self, enable: bool):
         L.check(L.load().md_batch_set_profiling(self._h, 1 if enable else 0), "md_batch_set_profiling")

@@ -485,7 +485,8 @@ md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvO
 // the interior nodes only).
 __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__ Ns, const InstDesc* __restrict__ D,
                             const float* __restrict__ v, const long long* __restrict__ voff, const KState* __restrict__ st,
-                            __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off, float* __restrict__ z) {
+                            __nv_bfloat16* __restrict__ x0, const long long* __restrict__ x0off, float* __restrict__ z,
+                            int use_lift) {
     const Seg sg = seg[blockIdx.x];
     if (!cnn_runs(st, sg.inst)) return;
     const InstDesc& d = D[sg.inst];
@@ -501,7 +502,7 @@ __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__
         float c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (s > 0.0) {
             c[0] = vi[n] / sf;
-            c[1] = d.lift32[n] / sf;
+            c[1] = use_lift ? d.lift32[n] / sf : 0.f;
         }
         c[2] = d.dist[n];
         *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
@@ -510,8 +511,8 @@ __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__
 }
 
 md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
-                        float* z, cudaStream_t s) {
-    k_pack_prec<<<w->nodes.nblocks, 128, 0, s>>>(w->nodes.seg, w->N, D, v, voff, st, w->x0, w->off_x0, z);
+                        float* z, cudaStream_t s, bool use_lift) {
+    k_pack_prec<<<w->nodes.nblocks, 128, 0, s>>>(w->nodes.seg, w->N, D, v, voff, st, w->x0, w->off_x0, z, use_lift ? 1 : 0);
     MD_CHECK_LAUNCH();
     return MD_OK;
 }

@@ -57,8 +57,8 @@ md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A
                             const OutIO& io, cudaStream_t s);
 md_status cnn_upload(md_cnn* c);
 // X0 = [v0 / s, l / s, d] from a preconditioner input (instance 3D part at v + voff[i])
+// use_lift = false: the lifted-1D channel is zero (block lower-triangular order)
 md_status cnn_pack_prec(CnnWork* w, const InstDesc* D, const float* v, const long long* voff, const KState* st,
-                        float* z,
-                        cudaStream_t s);
+                        float* z, cudaStream_t s, bool use_lift = true);
 // X0 from a raw channel-major FP32 input (sample, channel, z, y, x)
 md_status cnn_pack_raw(CnnWork* w, const float* X, cudaStream_t s);

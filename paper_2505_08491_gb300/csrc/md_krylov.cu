@@ -50,7 +50,7 @@ struct md_batch {
     double* part = nullptr;
     int* ndone = nullptr;
     ResOut res{};
-    int max_n1 = 0;
+    int max_n1 = 0, max_nq = 0;
     CnnWork* cw = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;     // CG: one chunk of iterations
@@ -66,6 +66,8 @@ struct md_batch {
     int* d_any = nullptr;
     int* h_any = nullptr;                // pinned host copy
     int executed_slots = 0;              // slots the last cycle ran
+    int prec_order = 0;                  // 0: block upper-triangular (the paper's), 1: lower
+    int graph_prec_order = 0;
     unsigned long long graph_cnn_uid = 0;  // network the graph was captured with (0: none)
     bool graph_prof = false;
     int graph_engine = -1;
@@ -466,6 +468,82 @@ __global__ void __launch_bounds__(MD_TB) k_jacobi(const Seg* __restrict__ seg, c
     for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) z[o + e] = dinv[e] * v[o + e];
 }
 
+// Tree LDL^T solve in place on y (length n1, shared memory): forward sweep
+// leaves-to-root, diagonal scaling, backward sweep root-to-leaves.
+__device__ inline void tree_solve_smem(float* y, const float* sl, const float* sdi, const int* sord, const int* spar,
+                                       int n1) {
+    if (threadIdx.x == 0) {
+        for (int idx = 0; idx < n1; ++idx) {
+            const int i = sord[idx], p = spar[i];
+            if (p >= 0) y[p] -= sl[i] * y[i];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) y[i] *= sdi[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int idx = n1 - 1; idx >= 0; --idx) {
+            const int i = sord[idx], p = spar[i];
+            if (p >= 0) y[i] -= sl[i] * y[p];
+        }
+    }
+    __syncthreads();
+}
+
+// Lower block order: the network input scale is s = ||v0|| (no lifted 1D part).
+__global__ void k_lower_setup(KState* st, int ninst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    KState& S = st[i];
+    if (!S.active || S.fallback) return;
+    S.s2_touch = 0.0;
+    S.s = S.v3n2 > 0.0 ? sqrt(S.v3n2) : 0.0;
+}
+
+// Lower block order, 1D part after the network: z1 = B11^{-1} (v1 + beta Psi^T W Pi z0),
+// i.e. v1 minus the 1-0 block of A applied to z0 (Pi at the quadrature
+// points in shared memory, then the Psi^T W rows, then the tree solve).
+__global__ void __launch_bounds__(TREE_TB) k_lower_1d(const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                                                      const float* __restrict__ v, float* z, const KState* st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int inst = blockIdx.x;
+    const KState& S = st[inst];
+    if (!S.active || S.fallback) return;
+    const InstDesc& d = D[inst];
+    const int n1 = d.n1, nq = d.nq;
+    float* y = reinterpret_cast<float*>(smraw);
+    float* sl = y + n1;
+    float* sdi = sl + n1;
+    int* sord = reinterpret_cast<int*>(sdi + n1);
+    int* spar = sord + n1;
+    float* t = reinterpret_cast<float*>(spar + n1);
+    const long long o = off[inst];
+    const float* z0 = z + o;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        float a = 0.f;
+        for (int jj = d.pi_ptr[q]; jj < d.pi_ptr[q + 1]; ++jj) a += d.pi_v32[jj] * z0[d.pi_col[jj]];
+        t[q] = a;
+    }
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        sl[i] = d.tr_l32[i];
+        sdi[i] = d.tr_dinv32[i];
+        sord[i] = d.tr_order[i];
+        spar[i] = d.tr_parent[i];
+    }
+    __syncthreads();
+    const float beta = (float)d.beta;
+    const float* v1 = v + o + d.n3;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        float a = 0.f;
+        for (int jj = d.pw_ptr[i]; jj < d.pw_ptr[i + 1]; ++jj) a += d.pw_v32[jj] * t[d.pw_q[jj]];
+        y[i] = v1[i] + beta * a;
+    }
+    __syncthreads();
+    tree_solve_smem(y, sl, sdi, sord, spar, n1);
+    float* z1 = z + o + d.n3;
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) z1[i] = y[i];
+}
+
 // 1D block solve z1 = B11^{-1} v1 (tree LDL^T sweeps in shared memory), the
 // lift l = beta Pi^T W Psi z1 on the touched grid nodes, and the input norm
 // s = ||v0 + l|| from ||v0||^2 (st.v3n2) and the touched-node correction.
@@ -493,22 +571,7 @@ __global__ void __launch_bounds__(TREE_TB) k_tree_lift(const InstDesc* __restric
         spar[i] = d.tr_parent[i];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int idx = 0; idx < n1; ++idx) {
-            const int i = sord[idx], p = spar[i];
-            if (p >= 0) y[p] -= sl[i] * y[i];
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) y[i] *= sdi[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int idx = n1 - 1; idx >= 0; --idx) {
-            const int i = sord[idx], p = spar[i];
-            if (p >= 0) y[i] -= sl[i] * y[p];
-        }
-    }
-    __syncthreads();
+    tree_solve_smem(y, sl, sdi, sord, spar, n1);
     float* z1 = z + o + d.n3;
     for (int i = threadIdx.x; i < n1; i += blockDim.x) z1[i] = y[i];
     const float beta = (float)d.beta;
@@ -733,11 +796,20 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 1);
     MD_CHECK_LAUNCH();
     const size_t smem = (size_t)B->max_n1 * 20;
-    k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
+    const bool lower = B->prec_order == 1;
+    if (lower) {
+        k_lower_setup<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
+    } else {
+        k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
+    }
     MD_CHECK_LAUNCH();
-    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, zout, s));
+    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, zout, s, !lower));
     OutIO io{zout, B->off, vin, B->off, B->st, B->d};
     MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
+    if (lower) {
+        k_lower_1d<<<B->ninst, TREE_TB, smem + (size_t)B->max_nq * 4, s>>>(B->d, B->off, vin, zout, B->st);
+        MD_CHECK_LAUNCH();
+    }
     return MD_OK;
 }
 
@@ -848,7 +920,9 @@ static md_status build_graph(md_batch* B) {
     const int engine = B->cnn ? B->cnn->engine : 0;
     const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
     const bool have = B->solver == MD_SOLVER_CG_JACOBI ? B->graph != nullptr : B->restart_graph != nullptr;
-    if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine) return MD_OK;
+    if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
+        B->graph_prec_order == B->prec_order)
+        return MD_OK;
     destroy_graphs(B);
     if (B->profiling && B->ev.empty()) {
         B->ev.resize((size_t)B->k * EV_PER_J + 2);
@@ -876,6 +950,7 @@ static md_status build_graph(md_batch* B) {
                              &B->restart_kernels));
     }
     B->graph_cnn_uid = uid;
+    B->graph_prec_order = B->prec_order;
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
     return MD_OK;
@@ -926,6 +1001,7 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
         B->hoff.push_back(tot);
         tot += ops[i]->h.n;
         B->max_n1 = std::max(B->max_n1, ops[i]->h.n1);
+        B->max_nq = std::max(B->max_nq, ops[i]->h.nq);
         Ns.push_back(ops[i]->h.N);
     }
     B->hoff.push_back(tot);
@@ -960,6 +1036,11 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
         const size_t smem = (size_t)B->max_n1 * 20;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) chk(md_cuda_status(e, "tree smem", __FILE__, __LINE__));
+        }
+        if (smem + (size_t)B->max_nq * 4 > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_lower_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(smem + (size_t)B->max_nq * 4));
             if (e != cudaSuccess) chk(md_cuda_status(e, "tree smem", __FILE__, __LINE__));
         }
     }
@@ -1074,6 +1155,12 @@ extern "C" md_status md_batch_solve(md_batch* B, const double* b_all, double* x_
         }
     }
     return all ? MD_OK : MD_NOT_CONVERGED;
+}
+
+extern "C" md_status md_batch_set_prec_order(md_batch* B, int lower) {
+    if (!B || (lower != 0 && lower != 1)) { md_set_error("md_batch_set_prec_order: bad argument"); return MD_ERR_ARG; }
+    B->prec_order = lower;
+    return MD_OK;
 }
 
 extern "C" md_status md_batch_set_profiling(md_batch* B, int enable) {
@@ -1198,6 +1285,23 @@ extern "C" md_status md_lift(const md_op* op, const float* r, float* z1, float* 
     MD_CUDA(cudaMemcpyAsync(l, d.lift32, sizeof(float) * d.n3, cudaMemcpyDeviceToDevice, s));
     if (z1) MD_CUDA(cudaMemcpyAsync(z1, B->Z + d.n3, sizeof(float) * d.n1, cudaMemcpyDeviceToDevice, s));
     return MD_OK;
+}
+
+extern "C" md_status md_precondition_lower(const md_op* op, const md_cnn* cnn, const float* r, float* z,
+                                           md_stream stream) {
+    if (!op || !cnn || !r || !z) { md_set_error("md_precondition_lower: NULL argument"); return MD_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    md_batch* B = nullptr;
+    MD_TRY(op_batch(op, MD_SOLVER_FGMRES_CNN, 1, cnn, &B));
+    const int keep = B->prec_order;
+    B->prec_order = 1;
+    k_prec_setup<<<1, 1, 0, s>>>(B->st);
+    const Tables& T = B->tabs;
+    k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
+    MD_CHECK_LAUNCH();
+    const md_status st = launch_precond(B, cnn, r, z, s);
+    B->prec_order = keep;
+    return st;
 }
 
 extern "C" md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream stream) {

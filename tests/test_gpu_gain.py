@@ -79,3 +79,28 @@ def test_trained_solution_and_iterations_match_oracle(setup):
     xo, it_o, rel_o = solvers.fgmres(p.A, b, Q, 1e-8, restart=30, maxit=500)
     assert rel_o <= 1e-8
     assert its <= 1.2 * it_o + 2 and it_o <= 1.2 * its + 2, (its, it_o)
+
+
+def test_lower_block_order_solves_and_matches_oracle_iterations(setup):
+    """The lower-triangular block order (network first, then the 1D solve)
+    with the shipped network: converges on the benchmark instances, and its
+    iteration count on instance 0 is the oracle's FP64 FGMRES with the same
+    order and weights within 1.2x + 2."""
+    from paper_2505_08491_gb300 import Batch, Network
+    from paper_2505_08491_gb300.weights import default_network_params, flat_to_layers
+    insts, ops, b_all = setup
+    net = Network(default_network_params())
+    B = Batch(ops, "fgmres_cnn", net, restart=30)
+    B.set_prec_order("lower")
+    x = torch.zeros_like(b_all)
+    its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=2000)
+    assert ok and max(rels) <= 1e-8
+    w = insts[0]
+    p = fem.Problem(w["N"], w["graph"], w["beta"])
+    b = p.rhs(p.source(w["f_seed"]), w["g"])
+    layers = [(cnn.round_bf16(W), np.asarray(bb, np.float32).astype(np.float64))
+              for W, bb in flat_to_layers(default_network_params())]
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order="lower")
+    _, it_o, rel_o = solvers.fgmres(p.A, b, Q, 1e-8, restart=30, maxit=500)
+    assert rel_o <= 1e-8
+    assert its[0] <= 1.2 * it_o + 2 and it_o <= 1.2 * its[0] + 2, (its[0], it_o)

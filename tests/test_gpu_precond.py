@@ -96,3 +96,31 @@ def test_lift_matches_oracle(case):
     r2[:p.n3] = 0.0
     l2, _ = op.lift(torch.from_numpy(r2).cuda())
     assert torch.equal(l, l2)
+
+
+@pytest.mark.parametrize("case", instance_cases()[1:], ids=lambda c: c[0])
+def test_lower_order_preconditioner_matches_oracle(case):
+    """md_precondition_lower against the oracle's order='lower' with the same
+    BF16 network: the 3D part is the network (1e-2, as for the upper order);
+    the 1D part follows from it through Pi and the tree solve, so it carries
+    the network's deviation (1e-2); Dirichlet rows copy the input."""
+    from paper_2505_08491_gb300 import Network, Operator
+    from paper_2505_08491_gb300.weights import random_params
+    name, N, g, beta, _ = case
+    p = fem.Problem(N, g, beta)
+    op = Operator(N, g, beta)
+    flat = random_params(9)
+    layers = [(cnn.round_bf16(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in oracle_layers(flat)]
+    net = Network(flat)
+    r = np.random.default_rng(8).standard_normal(p.n).astype(np.float32)
+    r[:p.n3][p.bd] = 0.0
+    z = op.precondition(torch.from_numpy(r).cuda(), net, order="lower").cpu().numpy()
+    ref = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order="lower")(r.astype(np.float64))
+    assert rel_l2(z[:p.n3], ref[:p.n3]) <= 1e-2
+    assert rel_l2(z[p.n3:], ref[p.n3:]) <= 1e-2
+    assert np.array_equal(z[:p.n3][p.bd], r[:p.n3][p.bd])
+    # given the GPU's own z0, the 1D part is the FP32 gather and tree solve of
+    # the right-hand side the oracle builds from that z0
+    z1_ref = solvers.BlockPreconditioner(p, mode="jacobi").B11_lu.solve(
+        r[p.n3:].astype(np.float64) - beta * (p.M01.T @ z[:p.n3].astype(np.float64)))
+    assert rel_l2(z[p.n3:], z1_ref) <= 1e-5
