@@ -245,7 +245,7 @@ def main():
     ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
     torch.cuda.synchronize()
     assembly_s = (time.perf_counter() - t_asm) / len(ops)
-    params = default_network_params()
+    params = default_network_params(args.prec_order)
     net = Network(params)
     bs = []
     for w, op in zip(insts, ops):

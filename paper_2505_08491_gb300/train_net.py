@@ -132,9 +132,21 @@ def main():
     ap.add_argument("--workload", default="train_trees", choices=["train_trees", "train_trees_wide"])
     ap.add_argument("--set", default="residuals", choices=["residuals", "kry", "hf", "all"],
                     help="training vectors per graph (see build_set)")
+    ap.add_argument("--zero-1d", action="store_true",
+                    help="train for the block lower-triangular order: the 1D part of every training vector is "
+                         "zeroed, so the network sees [r0/s, 0, d] and is fitted to C z0 = r0")
     args = ap.parse_args()
     t0 = time.time()
     ops, samples, sample_op = build_set(args.graphs, workload=args.workload, kind=args.set)
+    if args.zero_1d:
+        kept, kept_op = [], []
+        for r, i in zip(samples, sample_op):
+            r = r.clone()
+            r[ops[i].n3:] = 0.0
+            if float(torch.linalg.vector_norm(r)) > 0.0:
+                kept.append(r)
+                kept_op.append(i)
+        samples, sample_op = kept, kept_op
     torch.cuda.synchronize()
     t1 = time.time()
     net = Network.load(args.init) if args.init else Network(random_params(args.seed))
@@ -143,7 +155,7 @@ def main():
     t2 = time.time()
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     net.save(args.out)
-    print(json.dumps({"workload": args.workload, "set": args.set, "graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
+    print(json.dumps({"workload": args.workload, "set": args.set, "zero_1d": args.zero_1d, "graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
                       "set_seconds": t1 - t0, "train_seconds": t2 - t1, "loss": hist}))
 
 

@@ -14,6 +14,9 @@ CHANNELS = (3, 32, 32, 32, 32, 32, 1)
 NPARAMS = sum(co * ci * 27 + co for ci, co in zip(CHANNELS[:-1], CHANNELS[1:]))
 HERE = os.path.dirname(os.path.abspath(__file__))
 TRAINED = os.path.join(HERE, "weights", "cnn_trained.bin")
+# fine-tuned for the block lower-triangular order (1D parts of the training
+# vectors zeroed: the network fitted to C z0 = r0)
+TRAINED_LOWER = os.path.join(HERE, "weights", "cnn_trained_lower.bin")
 
 
 def layers_to_flat(layers) -> np.ndarray:
@@ -86,9 +89,11 @@ def read_network_file(path: str) -> np.ndarray:
     return vals
 
 
-def default_network_params() -> np.ndarray:
-    """The trained network shipped with the package if present, else the
-    identity-pair network."""
-    if os.path.exists(TRAINED):
-        return read_network_file(TRAINED)
+def default_network_params(order: str = "upper") -> np.ndarray:
+    """The trained network shipped with the package for the block order
+    ('upper', the paper's, or 'lower') if present, else the identity-pair
+    network."""
+    path = TRAINED_LOWER if order == "lower" and os.path.exists(TRAINED_LOWER) else TRAINED
+    if os.path.exists(path):
+        return read_network_file(path)
     return identity_pair_params()
