@@ -130,7 +130,7 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_solve_seconds(inst, params_flat, max_seconds=None):
+def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper"):
     """Oracle FGMRES(30) + network (FP64 CPU) on one instance.  Returns
     (seconds, iterations, relres, completed)."""
     from oracle import fem, solvers
@@ -138,7 +138,7 @@ def oracle_solve_seconds(inst, params_flat, max_seconds=None):
     layers = [(W, b) for W, b in flat_to_layers(params_flat)]
     p = fem.Problem(inst["N"], inst["graph"], inst["beta"])
     b = p.rhs(p.source(inst["f_seed"]), inst["g"])
-    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True)
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order=order)
     hist = []
     t0 = time.perf_counter()
     if max_seconds is None:
@@ -177,13 +177,13 @@ def reference_arm(args):
     if rank != 0:
         return
     from paper_2505_08491_gb300.weights import default_network_params
-    params = default_network_params()
+    params = default_network_params(args.prec_order)
     insts = instances(args.workload, 0, args.count)
     for w in range(args.warmup):
-        oracle_solve_seconds(insts[w % len(insts)], params)
+        oracle_solve_seconds(insts[w % len(insts)], params, order=args.prec_order)
     ts, its = [], []
     for k in range(args.steps):
-        t, it, rel, done = oracle_solve_seconds(insts[(args.warmup + k) % len(insts)], params)
+        t, it, rel, done = oracle_solve_seconds(insts[(args.warmup + k) % len(insts)], params, order=args.prec_order)
         ts.append(t)
         its.append(it)
     total = sum(ts)
@@ -356,7 +356,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         its0 = its_all[-1][0]
-        t, it, rel, done = oracle_solve_seconds(insts[0], params, max_seconds=20.0)
+        t, it, rel, done = oracle_solve_seconds(insts[0], params, max_seconds=20.0, order=args.prec_order)
         per_it = t / max(it, 1)
         cpu = {"value": 1.0 / (per_it * its0), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"instance 0, FP64 oracle FGMRES(30)+network: {it} iterations timed ({t:.1f} s), "
