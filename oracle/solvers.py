@@ -110,6 +110,17 @@ def fgmres(A, b: np.ndarray, precond, tol: float, restart: int = 30, maxit: int 
     return x, it, float(np.linalg.norm(b - A @ x) / nb)
 
 
+def jacobi_smooth(C: sp.spmatrix, b: np.ndarray, x0: np.ndarray, sweeps: int, omega: float) -> np.ndarray:
+    """S_J(C, b, x0, maxit) of Section 5 ('Effect of pre- and post-smoothing'):
+    `sweeps` damped Jacobi relaxations x <- x + omega D^{-1} (b - C x),
+    D = diag(C), started at x0."""
+    dinv = 1.0 / C.diagonal()
+    x = x0.copy()
+    for _ in range(sweeps):
+        x = x + omega * dinv * (b - C @ x)
+    return x
+
+
 class BlockPreconditioner:
     """Q~: inverse of the block upper-triangular part of A, eq. (right-prec)
     and the two-step back substitution of eq. (twosteps):
@@ -129,16 +140,28 @@ class BlockPreconditioner:
     reading of how the 1D unknowns follow from the network): the 3D block
     first with the 1D part absent from its right-hand side (l = 0, b0 = r0),
     then z1 = B11^{-1} (r1 - beta M10 z0) = B11^{-1} (r1 + beta Psi^T W Pi z0).
+
+    smooth=(nu, omega) wraps the 3D solve in Jacobi pre- and post-smoothing
+    (Section 5, 'Effect of pre- and post-smoothing'):
+        x = S_J(C, b0, 0, nu);  x += solve(b0 - C x);  z0 = S_J(C, b0, x, nu)
+    where the correction solve sees the 3D residual b0 - C x with the lifted
+    1D part l kept in its own network channel: [(b0 - C x - l)/s, l/s, d],
+    s = ||b0 - C x|| (the split of b0 into r0 and l carried over to the
+    residual).  nu = 0 is the plain preconditioner.
     """
 
-    def __init__(self, prob, mode: str = "cnn", params=None, bf16: bool = True, order: str = "upper"):
+    def __init__(self, prob, mode: str = "cnn", params=None, bf16: bool = True, order: str = "upper",
+                 smooth: tuple[int, float] = (0, 1.0)):
         if order not in ("upper", "lower"):
             raise ValueError("order must be 'upper' or 'lower'")
+        if smooth[0] < 0:
+            raise ValueError("smoothing sweeps must be >= 0")
         self.p = prob
         self.mode = mode
         self.params = params
         self.bf16 = bf16
         self.order = order
+        self.nu, self.omega = int(smooth[0]), float(smooth[1])
         self.B11_lu = spla.splu(prob.B11.tocsc())
         self.C_lu = spla.splu(prob.C.tocsc()) if mode == "exact" else None
 
@@ -146,7 +169,18 @@ class BlockPreconditioner:
         return -self.p.beta * (self.p.M01 @ z1)
 
     def solve3(self, r0, l):
-        """The 3D block solve for right-hand side r0 + l (l = the lifted 1D part)."""
+        """The 3D block solve for right-hand side r0 + l (l = the lifted 1D
+        part), with Jacobi pre- and post-smoothing when nu > 0."""
+        if self.nu == 0:
+            return self.inner3(r0, l)
+        C = self.p.C
+        b0 = r0 + l
+        x = jacobi_smooth(C, b0, np.zeros_like(b0), self.nu, self.omega)
+        x = x + self.inner3(b0 - C @ x - l, l)
+        return jacobi_smooth(C, b0, x, self.nu, self.omega)
+
+    def inner3(self, r0, l):
+        """One application of the 3D solve of `mode` to r0 + l."""
         p = self.p
         b0 = r0 + l
         if self.mode == "exact":

@@ -163,3 +163,92 @@ def test_fgmres_cnn_preconditioner_converges(tree8):
     assert rel <= 1e-8
     xd = solvers.direct_solve(tree8.A, b)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+
+
+def _smoother(p, omega):
+    """S = I - omega D^{-1} C as a function (D = diag(C))."""
+    dinv = 1.0 / p.C.diagonal()
+    return lambda v: v - omega * dinv * (p.C @ v)
+
+
+def test_jacobi_smooth_error_contracts_by_iteration_matrix(tree8):
+    """Damped Jacobi on C x = b: the error after nu sweeps is
+    (I - omega D^{-1} C)^nu times the initial error (textbook stationary
+    iteration), and from x0 = 0 the first sweep is omega D^{-1} b."""
+    p = tree8
+    rng = np.random.default_rng(11)
+    xs = rng.standard_normal(p.n3)
+    b = p.C @ xs
+    x0 = rng.standard_normal(p.n3)
+    S = _smoother(p, 0.8)
+    for nu in (1, 2, 3):
+        e = x0 - xs
+        for _ in range(nu):
+            e = S(e)
+        x = solvers.jacobi_smooth(p.C, b, x0, nu, 0.8)
+        assert np.linalg.norm(x - xs - e) <= 1e-12 * np.linalg.norm(xs)
+    x1 = solvers.jacobi_smooth(p.C, b, np.zeros(p.n3), 1, 0.8)
+    assert np.allclose(x1, 0.8 * b / p.C.diagonal(), rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+@pytest.mark.parametrize("nu", [1, 2])
+def test_smoothed_3d_solve_error_propagation(tree8, order, nu):
+    """Pre- and post-smoothing around a linear 3D solve N: the error
+    propagation of the smoothed solve is I - Q C = S^nu (I - N C) S^nu
+    (symmetric two-level composition, S the Jacobi iteration matrix), with
+    the lifted part l in its own channel, which must not change a linear
+    solve: N = D^{-1} ('jacobi'), and N = I / alpha on interior rows, I on
+    Dirichlet rows (the network returning channel 0 + channel 1)."""
+    p = tree8
+    omega = 0.7
+    S = _smoother(p, omega)
+    rng = np.random.default_rng(12 + nu)
+    for mode, params, Nd in (("jacobi", None, 1.0 / p.C.diagonal()),
+                             ("cnn", identity_params(), np.where(p.bd, 1.0, 1.0 / p.alpha))):
+        Q = solvers.BlockPreconditioner(p, mode=mode, params=params, bf16=False, order=order,
+                                        smooth=(nu, omega))
+        for _ in range(2):
+            x = rng.standard_normal(p.n3)
+            x[p.bd] = rng.standard_normal(int(p.bd.sum()))
+            l = rng.standard_normal(p.n3) if order == "upper" else np.zeros(p.n3)
+            l[p.bd] = 0.0
+            got = x - Q.solve3(p.C @ x - l, l)
+            e = x.copy()
+            for _ in range(nu):
+                e = S(e)
+            e = e - Nd * (p.C @ e)
+            for _ in range(nu):
+                e = S(e)
+            assert np.linalg.norm(got - e) <= 1e-10 * np.linalg.norm(x), (mode, order, nu)
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+def test_smoothing_keeps_exact_block_inverse(tree8, order):
+    """With the exact 3D solve the smoothed preconditioner still inverts the
+    block triangular part (the correction removes the whole residual and
+    post-smoothing leaves an exact solution unchanged)."""
+    p = tree8
+    if order == "upper":
+        T = sp.bmat([[p.C, p.beta * p.M01], [None, p.B11]], format="csr")
+    else:
+        T = sp.bmat([[p.C, None], [p.A[p.n3:, :p.n3], p.B11]], format="csr")
+    Q = solvers.BlockPreconditioner(p, mode="exact", order=order, smooth=(2, 0.8))
+    x = np.random.default_rng(13).standard_normal(p.n)
+    assert np.linalg.norm(Q(T @ x) - x) / np.linalg.norm(x) < 1e-10
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+def test_smoothed_cnn_preconditioner_homogeneous(tree8, order):
+    """The smoothed network preconditioner stays positively homogeneous and
+    reproduces r0 on Dirichlet nodes (identity rows of C, unit diagonal)."""
+    p = tree8
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=cnn.init_params(5), bf16=False, order=order,
+                                    smooth=(1, 0.8))
+    v = np.random.default_rng(14).standard_normal(p.n)
+    v[:p.n3][p.bd] = 0
+    z = Q(v)
+    assert np.allclose(Q(2.5 * v), 2.5 * z, rtol=1e-12, atol=1e-14)
+    v2 = v.copy()
+    v2[:p.n3][p.bd] = 1.25
+    assert np.allclose(Q(v2)[:p.n3][p.bd], 1.25, rtol=1e-14, atol=0)
