@@ -190,6 +190,24 @@ md_status md_precondition(const md_op* op, const md_cnn* cnn, const float* r, fl
  * md_precondition; cnn must not be NULL.  Asynchronous. */
 md_status md_precondition_lower(const md_op* op, const md_cnn* cnn, const float* r, float* z, md_stream s);
 
+/* md_precondition_smoothed -- the network preconditioner with Jacobi pre- and
+ * post-smoothing around its 3D solve (Section 5, 'Effect of pre- and
+ * post-smoothing', the relaxation S_J(C, b0, x0, nu)): with b0 the right-hand
+ * side of the 3D solve (r0 + l in the upper order, r0 in the lower one) and
+ * D = diag(C),
+ *     x  = nu damped Jacobi sweeps x <- x + omega D^{-1} (b0 - C x) from 0,
+ *     x += N(b0 - C x)   (network input [(b0 - C x - l)/s, l/s, d_h],
+ *                         s = ||b0 - C x||, output (s / alpha) N(X),
+ *                         b0 - C x itself on Dirichlet nodes),
+ *     z0 = nu more sweeps from x,
+ * and z1 as in md_precondition (lower = 0) or md_precondition_lower
+ * (lower = 1).  nu in [0, 8] (0 gives the unsmoothed preconditioner),
+ * 0 < omega < 2, else MD_ERR_ARG.  cnn must not be NULL.  r, z: device
+ * float, n.  Uses the operator's cached solver scratch: calls on one
+ * operator must be ordered.  Asynchronous. */
+md_status md_precondition_smoothed(const md_op* op, const md_cnn* cnn, int lower, int nu, double omega,
+                                   const float* r, float* z, md_stream s);
+
 /* md_lift -- the 1D part of the preconditioner on its own (Section 3 eqs.
  * (matrixC), (setB)): z1 = B11^{-1} r1 (tree factorisation) and its forcing on
  * the 3D problem l = -beta M01 z1 = beta Pi^T W Psi z1.  With r1 the 1D load
@@ -265,6 +283,11 @@ md_status md_batch_set_profiling(md_batch* b, int enable);
 /* lower = 1: the network-preconditioned batch uses md_precondition_lower's
  * block order; 0 (default): the paper's upper-triangular order. */
 md_status md_batch_set_prec_order(md_batch* b, int lower);
+/* nu > 0: the network-preconditioned batch smooths its 3D solve with nu
+ * damped Jacobi sweeps (damping omega) before and after the network, as
+ * md_precondition_smoothed; 0 (default): no smoothing.  Limits and errors as
+ * md_precondition_smoothed. */
+md_status md_batch_set_smoothing(md_batch* b, int nu, double omega);
 md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
 md_status md_batch_reset_stats(md_batch* b);
 

@@ -14,6 +14,18 @@ import torch
 from . import _lib as L
 
 
+# Default damping of the Jacobi smoothing: the weighted Jacobi of the
+# multigrid literature the paper's smoother follows (Trottenberg et al.),
+# omega = 2/3.  For the Q1 stiffness stencil (centre 8/3, edges -1/6, corners
+# -1/12, times h) the eigenvalues of D^{-1} K are
+# 1 - (c1 c2 + c1 c3 + c2 c3)/4 - c1 c2 c3/4, c_i = cos(theta_i), which span
+# [1/2, 3/2] on the high frequencies: omega = 2/3 damps those by at least 2/3
+# (omega = 1 by 1/2), and the coupling rows, which at beta = 100 raise the top
+# of the spectrum of D^{-1} C to about 3, are amplified by at most ~1.06 per
+# sweep instead of the factor ~2 of omega = 1.
+SMOOTH_OMEGA = 2.0 / 3.0
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
@@ -96,10 +108,24 @@ class Operator:
                                           _ptr(out, u.dtype, self.n, "out"), _stream()), "md_apply_noalloc")
         return out
 
-    def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None, order: str = "upper") -> torch.Tensor:
+    def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None, order: str = "upper",
+                     smooth: tuple[int, float] | None = None) -> torch.Tensor:
         """z = Q r: block upper-triangular order (the paper's), or order='lower'
-        (network first, then the 1D solve); net=None gives Jacobi."""
+        (network first, then the 1D solve); net=None gives Jacobi.
+        smooth=(nu, omega): nu damped Jacobi sweeps before and after the
+        network (md_precondition_smoothed)."""
         z = torch.empty_like(r) if out is None else out
+        if order not in ("upper", "lower"):
+            raise ValueError("order must be 'upper' or 'lower'")
+        if smooth is not None:
+            if net is None:
+                raise ValueError("smoothing wraps the network solve: give a network")
+            L.check(L.load().md_precondition_smoothed(self._h, net.handle, 1 if order == "lower" else 0,
+                                                      int(smooth[0]), float(smooth[1]),
+                                                      _ptr(r, torch.float32, self.n, "r"),
+                                                      _ptr(z, torch.float32, self.n, "z"), _stream()),
+                    "md_precondition_smoothed")
+            return z
         if order == "lower":
             if net is None:
                 raise ValueError("the lower order needs a network")
@@ -107,8 +133,6 @@ class Operator:
                                                    _ptr(z, torch.float32, self.n, "z"), _stream()),
                     "md_precondition_lower")
             return z
-        if order != "upper":
-            raise ValueError("order must be 'upper' or 'lower'")
         L.check(L.load().md_precondition(self._h, net.handle if net is not None else None,
                                          _ptr(r, torch.float32, self.n, "r"), _ptr(z, torch.float32, self.n, "z"),
                                          _stream()), "md_precondition")
@@ -304,6 +328,12 @@ class Batch:
         if order not in ("upper", "lower"):
             raise ValueError("order must be 'upper' or 'lower'")
         L.check(L.load().md_batch_set_prec_order(self._h, 1 if order == "lower" else 0), "md_batch_set_prec_order")
+
+    def set_smoothing(self, nu: int, omega: float = None):
+        """nu damped Jacobi sweeps before and after the network (0: none);
+        omega defaults to SMOOTH_OMEGA."""
+        om = SMOOTH_OMEGA if omega is None else float(omega)
+        L.check(L.load().md_batch_set_smoothing(self._h, int(nu), om), "md_batch_set_smoothing")
 
     def set_profiling(self, enable: bool):
         L.check(L.load().md_batch_set_profiling(self._h, 1 if enable else 0), "md_batch_set_profiling")

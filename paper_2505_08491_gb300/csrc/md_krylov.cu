@@ -68,6 +68,10 @@ struct md_batch {
     int executed_slots = 0;              // slots the last cycle ran
     int prec_order = 0;                  // 0: block upper-triangular (the paper's), 1: lower
     int graph_prec_order = 0;
+    int smooth_nu = 0;                   // Jacobi sweeps before and after the network (0: none)
+    float smooth_omega = 1.f;            // their damping
+    int graph_smooth_nu = 0;
+    float graph_smooth_omega = 1.f;
     unsigned long long graph_cnn_uid = 0;  // network the graph was captured with (0: none)
     bool graph_prof = false;
     int graph_engine = -1;
@@ -602,6 +606,81 @@ __global__ void __launch_bounds__(TREE_TB) k_tree_lift(const InstDesc* __restric
     }
 }
 
+// ---- Jacobi pre- and post-smoothing around the 3D solve (Section 5, 'Effect of
+// pre- and post-smoothing') --------------------------------------------------------
+// The 3D part of Z holds the smoothing iterate x.  Its 1D part holds z1 in the
+// upper order, so the 3D part of A Z is C x - l, and zero in the lower order,
+// where it is C x: in both orders the residual of the 3D solve, b0 - C x, is
+// r0 - (A Z)_0, and one operator apply serves every sweep.
+
+// First sweep from x = 0: x = omega D^{-1} b0 (b0 = r0 + l, or r0 in the lower
+// order, which also clears the 1D part of Z).  Whole-vector segments.
+__global__ void __launch_bounds__(MD_TB) k_smooth_first(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                        const InstDesc* __restrict__ D, const float* __restrict__ v,
+                                                        float* z, const KState* st, float omega, int use_lift) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const InstDesc& d = D[sg.inst];
+    const long long o = off[sg.inst];
+    const int n3 = d.n3;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        if (e < n3) {
+            const float b0 = use_lift ? v[o + e] + d.lift32[e] : v[o + e];
+            z[o + e] = omega * d.dinv32[e] * b0;
+        } else if (!use_lift) {
+            z[o + e] = 0.f;
+        }
+    }
+}
+
+// One sweep x += omega D^{-1} (r0 - (A Z)_0), az = A Z.  3D segments.
+__global__ void __launch_bounds__(MD_TB) k_smooth_sweep(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                        const InstDesc* __restrict__ D, const float* __restrict__ v,
+                                                        const float* __restrict__ az, float* z, const KState* st,
+                                                        float omega) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const long long o = off[sg.inst];
+    const float* dinv = D[sg.inst].dinv32;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x)
+        z[o + e] += omega * dinv[e] * (v[o + e] - az[o + e]);
+}
+
+// Input of the network correction, in place over t = A Z: the 3D residual
+// res = r0 - (A Z)_0 = b0 - C x goes to the network as [(res - l)/s, l/s, d]
+// (the lifted part keeps its own channel; l = 0 in the lower order), with
+// s = ||res||.  3D segments; the last block of an instance stores s.
+__global__ void __launch_bounds__(MD_TB) k_smooth_resid(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                        const long long* __restrict__ off,
+                                                        const InstDesc* __restrict__ D, const float* __restrict__ v,
+                                                        float* t, KState* st, double* part, int use_lift) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    KState& S = st[sg.inst];
+    const InstDesc& d = D[sg.inst];
+    const long long o = off[sg.inst];
+    float a = 0.f;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        const float res = v[o + e] - t[o + e];
+        a = fmaf(res, res, a);
+        t[o + e] = use_lift ? res - d.lift32[e] : res;
+    }
+    double vals[1] = {(double)a};
+    double flag;
+    reduce_values<1>(vals, 1, part, blockIdx.x, rng[sg.inst], &S.counter[5], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) S.s = sh[0] > 0.0 ? sqrt(sh[0]) : 0.0;
+}
+
+// x += the network's correction (3D segments).
+__global__ void __launch_bounds__(MD_TB) k_smooth_add(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                      const float* __restrict__ t, float* z, const KState* st) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const long long o = off[sg.inst];
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) z[o + e] += t[o + e];
+}
+
 // ||v0||^2 of a preconditioner input given from outside the solver
 __global__ void __launch_bounds__(MD_TB) k_norm3(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                  const long long* __restrict__ off, const float* __restrict__ v,
@@ -782,8 +861,48 @@ __global__ void __launch_bounds__(MD_TB) k_cg_final(const Seg* __restrict__ seg,
 
 // ---------------------------------------------------------------------------
 // host side
-static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, cudaStream_t s,
-                                cudaEvent_t e_conv0 = nullptr, cudaEvent_t e_conv1 = nullptr) {
+// The network preconditioner with smoothing (B->smooth_nu > 0):
+//   x = S_J(C, b0, 0, nu);  x += N(b0 - C x);  z0 = S_J(C, b0, x, nu)
+// tmp: a whole-length scratch vector (the apply output and the network's
+// input and output).
+static md_status launch_precond_smoothed(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, float* tmp,
+                                         cudaStream_t s, cudaEvent_t e_conv0, cudaEvent_t e_conv1) {
+    const Tables& T = B->tabs;
+    const size_t smem = (size_t)B->max_n1 * 20;
+    const bool lower = B->prec_order == 1;
+    const float omega = B->smooth_omega;
+    if (!lower) {
+        k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
+        MD_CHECK_LAUNCH();
+    }
+    k_smooth_first<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, omega, !lower);
+    MD_CHECK_LAUNCH();
+    auto sweep = [&]() -> md_status {
+        MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, zout, B->off, tmp, s, B->st, 1));
+        k_smooth_sweep<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->off, B->d, vin, tmp, zout, B->st, omega);
+        MD_CHECK_LAUNCH();
+        return MD_OK;
+    };
+    for (int i = 1; i < B->smooth_nu; ++i) MD_TRY(sweep());
+    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, zout, B->off, tmp, s, B->st, 1));
+    k_smooth_resid<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, B->d, vin, tmp, B->st, B->part,
+                                                   !lower);
+    MD_CHECK_LAUNCH();
+    MD_TRY(cnn_pack_prec(B->cw, B->d, tmp, B->off, B->st, tmp, s, !lower));
+    OutIO io{tmp, B->off, tmp, B->off, B->st, B->d};
+    MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
+    k_smooth_add<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->off, tmp, zout, B->st);
+    MD_CHECK_LAUNCH();
+    for (int i = 0; i < B->smooth_nu; ++i) MD_TRY(sweep());
+    if (lower) {
+        k_lower_1d<<<B->ninst, TREE_TB, smem + (size_t)B->max_nq * 4, s>>>(B->d, B->off, vin, zout, B->st);
+        MD_CHECK_LAUNCH();
+    }
+    return MD_OK;
+}
+
+static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, float* tmp,
+                                cudaStream_t s, cudaEvent_t e_conv0 = nullptr, cudaEvent_t e_conv1 = nullptr) {
     const Tables& T = B->tabs;
     if (!cnn) {
         k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 0);
@@ -795,6 +914,7 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     // instances whose network application broke down continue with Jacobi
     k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 1);
     MD_CHECK_LAUNCH();
+    if (B->smooth_nu > 0) return launch_precond_smoothed(B, cnn, vin, zout, tmp, s, e_conv0, e_conv1);
     const size_t smem = (size_t)B->max_n1 * 20;
     const bool lower = B->prec_order == 1;
     if (lower) {
@@ -831,7 +951,8 @@ static md_status launch_slots(md_batch* B, int j0, int j1, cudaStream_t s) {
         float* Zj = B->Z + (long long)j * tot;
         float* W = B->V + (long long)(j + 1) * tot;
         rec(ev_at(B, j, EV_PRE0), s);
-        MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, s,
+        // W (the next basis vector) is the preconditioner's scratch until the apply below fills it
+        MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, W, s,
                               ev_at(B, j, EV_CONV0), ev_at(B, j, EV_CONV1)));
         rec(ev_at(B, j, EV_APPLY0), s);
         MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
@@ -921,7 +1042,8 @@ static md_status build_graph(md_batch* B) {
     const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
     const bool have = B->solver == MD_SOLVER_CG_JACOBI ? B->graph != nullptr : B->restart_graph != nullptr;
     if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
-        B->graph_prec_order == B->prec_order)
+        B->graph_prec_order == B->prec_order && B->graph_smooth_nu == B->smooth_nu &&
+        B->graph_smooth_omega == B->smooth_omega)
         return MD_OK;
     destroy_graphs(B);
     if (B->profiling && B->ev.empty()) {
@@ -951,6 +1073,8 @@ static md_status build_graph(md_batch* B) {
     }
     B->graph_cnn_uid = uid;
     B->graph_prec_order = B->prec_order;
+    B->graph_smooth_nu = B->smooth_nu;
+    B->graph_smooth_omega = B->smooth_omega;
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
     return MD_OK;
@@ -1299,8 +1423,57 @@ extern "C" md_status md_precondition_lower(const md_op* op, const md_cnn* cnn, c
     const Tables& T = B->tabs;
     k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
     MD_CHECK_LAUNCH();
-    const md_status st = launch_precond(B, cnn, r, z, s);
+    const md_status st = launch_precond(B, cnn, r, z, B->V + B->total, s);
     B->prec_order = keep;
+    return st;
+}
+
+// smoothing limits: sweeps per side, damping range of a convergent damped
+// Jacobi iteration on an SPD matrix with unit-scaled diagonal
+#define MD_SMOOTH_MAX 8
+
+static md_status check_smoothing(int nu, double omega, const char* who) {
+    if (nu < 0 || nu > MD_SMOOTH_MAX || !(omega > 0.0 && omega < 2.0)) {
+        md_set_error("%s: smoothing needs 0 <= nu <= %d and 0 < omega < 2 (got %d, %g)", who, MD_SMOOTH_MAX, nu,
+                     omega);
+        return MD_ERR_ARG;
+    }
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_set_smoothing(md_batch* B, int nu, double omega) {
+    if (!B) { md_set_error("md_batch_set_smoothing: NULL batch"); return MD_ERR_ARG; }
+    MD_TRY(check_smoothing(nu, omega, "md_batch_set_smoothing"));
+    B->smooth_nu = nu;
+    B->smooth_omega = (float)omega;
+    return MD_OK;
+}
+
+extern "C" md_status md_precondition_smoothed(const md_op* op, const md_cnn* cnn, int lower, int nu, double omega,
+                                              const float* r, float* z, md_stream stream) {
+    if (!op || !cnn || !r || !z || (lower != 0 && lower != 1)) {
+        md_set_error("md_precondition_smoothed: bad argument");
+        return MD_ERR_ARG;
+    }
+    MD_TRY(check_smoothing(nu, omega, "md_precondition_smoothed"));
+    cudaStream_t s = (cudaStream_t)stream;
+    md_batch* B = nullptr;
+    MD_TRY(op_batch(op, MD_SOLVER_FGMRES_CNN, 1, cnn, &B));
+    const int keep_order = B->prec_order, keep_nu = B->smooth_nu;
+    const float keep_omega = B->smooth_omega;
+    B->prec_order = lower;
+    B->smooth_nu = nu;
+    B->smooth_omega = (float)omega;
+    // active, not fallen back; the input norm pieces are recomputed
+    k_lift_setup<<<1, 1, 0, s>>>(B->st);
+    const Tables& T = B->tabs;
+    k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
+    md_status st = cudaGetLastError() == cudaSuccess ? MD_OK : MD_ERR_CUDA;
+    if (st != MD_OK) md_set_error("md_precondition_smoothed: launch failed");
+    if (st == MD_OK) st = launch_precond(B, cnn, r, z, B->V + B->total, s);
+    B->prec_order = keep_order;
+    B->smooth_nu = keep_nu;
+    B->smooth_omega = keep_omega;
     return st;
 }
 
@@ -1315,5 +1488,5 @@ extern "C" md_status md_precondition(const md_op* op, const md_cnn* cnn, const f
         k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
         MD_CHECK_LAUNCH();
     }
-    return launch_precond(B, cnn, r, z, s);
+    return launch_precond(B, cnn, r, z, B->V + B->total, s);
 }

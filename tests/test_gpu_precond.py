@@ -124,3 +124,74 @@ def test_lower_order_preconditioner_matches_oracle(case):
     z1_ref = solvers.BlockPreconditioner(p, mode="jacobi").B11_lu.solve(
         r[p.n3:].astype(np.float64) - beta * (p.M01.T @ z[:p.n3].astype(np.float64)))
     assert rel_l2(z[p.n3:], z1_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+@pytest.mark.parametrize("nu", [1, 2])
+@pytest.mark.parametrize("case", instance_cases()[1:3], ids=lambda c: c[0])
+def test_smoothed_preconditioner_matches_oracle(case, nu, order):
+    """md_precondition_smoothed (nu damped Jacobi sweeps of C before and
+    after the network, Section 5) against the oracle's smooth=(nu, omega)
+    with the same BF16 network (the shipped one): the 3D part within 1e-2
+    (the network's BF16 deviation, which the sweeps carry but do not grow:
+    they are contractions on all but the few coupling modes), the 1D part as
+    the unsmoothed preconditioner of the same order (upper: exact tree solve;
+    lower: follows the 3D part), Dirichlet rows equal to the input (C has
+    identity rows there, so smoothing and correction reproduce r0)."""
+    from paper_2505_08491_gb300 import SMOOTH_OMEGA, Network, Operator
+    from paper_2505_08491_gb300.weights import default_network_params
+    name, N, g, beta, _ = case
+    p = fem.Problem(N, g, beta)
+    op = Operator(N, g, beta)
+    flat = default_network_params()
+    layers = [(cnn.round_bf16(W), np.asarray(b, np.float32).astype(np.float64)) for W, b in oracle_layers(flat)]
+    net = Network(flat)
+    r = np.random.default_rng(20 + nu).standard_normal(p.n).astype(np.float32)
+    r[:p.n3][p.bd] = 0.5
+    z = op.precondition(torch.from_numpy(r).cuda(), net, order=order, smooth=(nu, SMOOTH_OMEGA)).cpu().numpy()
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order=order,
+                                    smooth=(nu, SMOOTH_OMEGA))
+    ref = Q(r.astype(np.float64))
+    assert rel_l2(z[:p.n3], ref[:p.n3]) <= 1e-2
+    assert rel_l2(z[p.n3:], ref[p.n3:]) <= (1e-5 if order == "upper" else 1e-2)
+    assert np.allclose(z[:p.n3][p.bd], 0.5, rtol=1e-6, atol=0)
+    # without smoothing the result differs by O(1): the sweeps are applied
+    plain = Q.__class__(p, mode="cnn", params=layers, bf16=True, order=order)(r.astype(np.float64))
+    assert rel_l2(plain[:p.n3], ref[:p.n3]) > 5e-2
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+def test_smoothing_off_is_the_plain_preconditioner(order):
+    """nu = 0 through md_precondition_smoothed runs the unsmoothed launch
+    sequence: bit-identical to md_precondition / md_precondition_lower."""
+    from paper_2505_08491_gb300 import Network, Operator
+    from paper_2505_08491_gb300.weights import default_network_params
+    name, N, g, beta, _ = instance_cases()[1]
+    op = Operator(N, g, beta)
+    net = Network(default_network_params())
+    p = fem.Problem(N, g, beta)
+    r = np.random.default_rng(30).standard_normal(p.n).astype(np.float32)
+    r[:p.n3][p.bd] = 0.0
+    rt = torch.from_numpy(r).cuda()
+    a = op.precondition(rt, net, order=order, smooth=(0, 0.5))
+    b = op.precondition(rt, net, order=order)
+    assert torch.equal(a, b)
+
+
+def test_smoothing_arguments_checked():
+    """nu outside [0, 8] or omega outside (0, 2) is rejected before any launch."""
+    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300._lib import MdError
+    from paper_2505_08491_gb300.weights import default_network_params
+    name, N, g, beta, _ = instance_cases()[1]
+    op = Operator(N, g, beta)
+    net = Network(default_network_params())
+    r = torch.zeros(op.n, dtype=torch.float32, device="cuda")
+    for bad in ((9, 0.5), (-1, 0.5), (1, 0.0), (1, 2.0), (1, float("nan"))):
+        with pytest.raises(MdError):
+            op.precondition(r, net, smooth=bad)
+    B = Batch([op], "fgmres_cnn", net)
+    with pytest.raises(MdError):
+        B.set_smoothing(1, 2.5)
+    B.set_smoothing(2, 0.5)
+    B.close()

@@ -60,3 +60,9 @@ def test_corrupt_network_file(lib, tmp_path):
     q = tmp_path / "good.bin"
     q.write_bytes(good)
     assert np.array_equal(read_network_file(str(q)), vals)
+
+
+def test_smoothing_entries_reject_null_handles(lib):
+    assert lib.md_batch_set_smoothing(None, 1, 0.5) == -1
+    assert lib.md_precondition_smoothed(None, None, 0, 1, 0.5, None, None, None) == -1
+    assert b"md_precondition_smoothed" in lib.md_last_error()
