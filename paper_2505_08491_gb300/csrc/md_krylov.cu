@@ -613,6 +613,11 @@ __global__ void __launch_bounds__(TREE_TB) k_tree_lift(const InstDesc* __restric
 // where it is C x: in both orders the residual of the 3D solve, b0 - C x, is
 // r0 - (A Z)_0, and one operator apply serves every sweep.
 
+// The smoothing kernels stream three or four vectors over the long segments of
+// the Krylov tables: each thread issues the loads of SM_U elements before any
+// arithmetic, so a block keeps SM_U x 256 loads in flight per array.
+#define SM_U 8
+
 // First sweep from x = 0: x = omega D^{-1} b0 (b0 = r0 + l, or r0 in the lower
 // order, which also clears the 1D part of Z).  Whole-vector segments.
 __global__ void __launch_bounds__(MD_TB) k_smooth_first(const Seg* __restrict__ seg, const long long* __restrict__ off,
@@ -623,12 +628,24 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_first(const Seg* __restrict__ 
     const InstDesc& d = D[sg.inst];
     const long long o = off[sg.inst];
     const int n3 = d.n3;
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
-        if (e < n3) {
-            const float b0 = use_lift ? v[o + e] + d.lift32[e] : v[o + e];
-            z[o + e] = omega * d.dinv32[e] * b0;
-        } else if (!use_lift) {
-            z[o + e] = 0.f;
+    const float* vi = v + o;
+    float* zi = z + o;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += SM_U * MD_TB) {
+        float b[SM_U], w[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in3 = e < sg.end && e < n3;
+            b[u] = in3 ? vi[e] : 0.f;
+            w[u] = in3 ? d.dinv32[e] : 0.f;
+            if (in3 && use_lift) b[u] += d.lift32[e];
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e >= sg.end) continue;
+            if (e < n3) zi[e] = omega * w[u] * b[u];
+            else if (!use_lift) zi[e] = 0.f;
         }
     }
 }
@@ -642,8 +659,26 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_sweep(const Seg* __restrict__ 
     if (!cnn_runs(st, sg.inst)) return;
     const long long o = off[sg.inst];
     const float* dinv = D[sg.inst].dinv32;
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x)
-        z[o + e] += omega * dinv[e] * (v[o + e] - az[o + e]);
+    const float* vi = v + o;
+    const float* ai = az + o;
+    float* zi = z + o;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += SM_U * MD_TB) {
+        float r[SM_U], a[SM_U], w[SM_U], x[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in = e < sg.end;
+            r[u] = in ? vi[e] : 0.f;
+            a[u] = in ? ai[e] : 0.f;
+            w[u] = in ? dinv[e] : 0.f;
+            x[u] = in ? zi[e] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) zi[e] = x[u] + omega * w[u] * (r[u] - a[u]);
+        }
+    }
 }
 
 // Input of the network correction, in place over t = A Z: the 3D residual
@@ -660,13 +695,28 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_resid(const Seg* __restrict__ 
     KState& S = st[sg.inst];
     const InstDesc& d = D[sg.inst];
     const long long o = off[sg.inst];
-    float a = 0.f;
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
-        const float res = v[o + e] - t[o + e];
-        a = fmaf(res, res, a);
-        t[o + e] = use_lift ? res - d.lift32[e] : res;
+    const float* vi = v + o;
+    float* ti = t + o;
+    float acc = 0.f;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += SM_U * MD_TB) {
+        float r[SM_U], a[SM_U], l[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in = e < sg.end;
+            r[u] = in ? vi[e] : 0.f;
+            a[u] = in ? ti[e] : 0.f;
+            l[u] = (in && use_lift) ? d.lift32[e] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const float res = r[u] - a[u];
+            acc = fmaf(res, res, acc);
+            if (e < sg.end) ti[e] = res - l[u];
+        }
     }
-    double vals[1] = {(double)a};
+    double vals[1] = {(double)acc};
     double flag;
     reduce_values<1>(vals, 1, part, blockIdx.x, rng[sg.inst], &S.counter[5], &flag, sh);
     if (flag == 1.0 && threadIdx.x == 0) S.s = sh[0] > 0.0 ? sqrt(sh[0]) : 0.0;
@@ -678,7 +728,23 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_add(const Seg* __restrict__ se
     const Seg sg = seg[blockIdx.x];
     if (!cnn_runs(st, sg.inst)) return;
     const long long o = off[sg.inst];
-    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) z[o + e] += t[o + e];
+    const float* ti = t + o;
+    float* zi = z + o;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += SM_U * MD_TB) {
+        float a[SM_U], x[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in = e < sg.end;
+            a[u] = in ? ti[e] : 0.f;
+            x[u] = in ? zi[e] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) zi[e] = x[u] + a[u];
+        }
+    }
 }
 
 // ||v0||^2 of a preconditioner input given from outside the solver
