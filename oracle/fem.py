@@ -228,6 +228,7 @@ class Problem:
         C      3D block K00 + beta Pi^T W Pi (eq. matrixC), Dirichlet-masked
         B11    1D block kappa_L K1 + beta Psi^T W Psi
         M01    -Pi^T W Psi (so the 0-1 block of A is beta * M01)
+        M00    Pi^T W Pi (so C = K00 + beta * M00)
         Pi, Psi, w, K1, kappa, Mass (unmasked Q1 mass), bd, dist, alpha
     """
 
@@ -264,6 +265,7 @@ class Problem:
         self.elem_len = L
         self.kappa = k_lambda * math.pi * float(graph["radius"]) ** 2
         M00 = (self.Pi.T @ W @ self.Pi).tocsr()
+        self.M00 = M00
         self.M01 = (-(self.Pi.T @ W @ self.Psi)).tocsr()
         M11 = (self.Psi.T @ W @ self.Psi).tocsr()
         interior = sp.diags((~self.bd).astype(np.float64))

@@ -166,9 +166,30 @@ def test_fgmres_cnn_preconditioner_converges(tree8):
 
 
 def _smoother(p, omega):
-    """S = I - omega D^{-1} C as a function (D = diag(C))."""
-    dinv = 1.0 / p.C.diagonal()
+    """S = I - omega D_s^{-1} C as a function, D_s^{-1} the smoother's scaling."""
+    dinv = solvers.smoothing_dinv(p)
     return lambda v: v - omega * dinv * (p.C @ v)
+
+
+@pytest.mark.parametrize("beta", [1.0, 10.0, 100.0])
+def test_smoothing_scaling_is_jacobi_on_stencil_rows_and_contracts(beta):
+    """The smoother's scaling: 1/c_ii (plain Jacobi) on every row the
+    coupling does not reach, including rows next to the boundary; at most
+    that elsewhere; and with it the spectrum of D_s^{-1} C lies in (0, 2], so
+    damped sweeps with omega <= 1 never amplify an error mode (the plain
+    diagonal gives eigenvalues near 3 at beta = 100)."""
+    p = fem.Problem(8, mdgen.random_tree(77, 0, depth=3, elems=4), beta=beta)
+    ds = solvers.smoothing_dinv(p)
+    d = p.C.diagonal()
+    touched = np.asarray(p.M00.sum(axis=1)).ravel() > 0
+    assert np.allclose(ds[~touched], 1.0 / d[~touched], rtol=1e-14, atol=0)
+    assert np.all(ds <= 1.0 / d * (1 + 1e-14))
+    sq = np.sqrt(ds)
+    lam = np.linalg.eigvalsh((sp.diags(sq) @ p.C @ sp.diags(sq)).toarray())
+    assert lam.min() > 0 and lam.max() <= 2.0 + 1e-12, (lam.min(), lam.max())
+    plain = np.linalg.eigvalsh((sp.diags(1 / np.sqrt(d)) @ p.C @ sp.diags(1 / np.sqrt(d))).toarray())
+    if beta == 100.0:
+        assert plain.max() > 2.5
 
 
 def test_jacobi_smooth_error_contracts_by_iteration_matrix(tree8):
@@ -180,7 +201,8 @@ def test_jacobi_smooth_error_contracts_by_iteration_matrix(tree8):
     xs = rng.standard_normal(p.n3)
     b = p.C @ xs
     x0 = rng.standard_normal(p.n3)
-    S = _smoother(p, 0.8)
+    dinv = 1.0 / p.C.diagonal()
+    S = lambda v: v - 0.8 * dinv * (p.C @ v)  # noqa: E731
     for nu in (1, 2, 3):
         e = x0 - xs
         for _ in range(nu):
