@@ -9,6 +9,9 @@
 // (kind 1) side by side; launch B adds the Pi^T scatter on the grid nodes the
 // averaging reaches (kind 2) and computes the 1D rows (kind 3).  All sums are
 // in a fixed order, so results are deterministic.
+#include <algorithm>
+#include <cmath>
+
 #include "md_common.cuh"
 
 // y0 over [begin, end) of the grid: Dirichlet nodes copy u, interior nodes
@@ -180,26 +183,54 @@ md_status launch_dist(md_op* op, cudaStream_t s) {
 
 // ---- 1 / diag(A): grid interior c0 (+ beta (Pi^T W Pi)_nn at touched nodes),
 // 1 on Dirichlet nodes, diag(B11) on 1D nodes.  Built on the host once.
-md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_m, const std::vector<double>& d1,
-                           cudaStream_t s) {
+// 1 / diag(A), and the Jacobi smoother's scaling of the 3D rows: rho_i / c_ii
+// with rho_i = min(1, 2 c_ii / S_i), S_i = sum_j |K00_ij| + beta sum_j (Pi^T W Pi)_ij
+// a bound of the absolute row sum of C (Gershgorin): 1 / c_ii on the stencil
+// rows, smaller where the coupling is heavy, so that damped sweeps with
+// omega <= 1 contract on every mode; 1 on Dirichlet rows.
+md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_m, const std::vector<double>& touch_rs,
+                           const std::vector<double>& d1, cudaStream_t s) {
     (void)s;
     const InstDesc& D = op->h;
     const int N = D.N, M = N + 1;
-    std::vector<double> dv((size_t)D.n);
+    std::vector<double> dv((size_t)D.n), kabs((size_t)D.n3, 0.0);
     std::vector<float> fv((size_t)D.n);
+    // |stencil| row sum over the interior neighbours: per axis, n_a of the two
+    // neighbour offsets stay interior; the neighbours of offset class m (m
+    // nonzero offsets) number the t^m coefficient of prod_a (1 + n_a t)
+    const double a0 = std::fabs(D.st64[0]), a1 = std::fabs(D.st64[1]), a2 = std::fabs(D.st64[2]),
+                 a3 = std::fabs(D.st64[3]);
+    auto nside = [&](int c) { return (double)((c - 1 >= 1) + (c + 1 <= N - 1)); };
     for (int k = 0; k < M; ++k)
         for (int j = 0; j < M; ++j)
             for (int i = 0; i < M; ++i) {
-                bool bd = i == 0 || i == N || j == 0 || j == N || k == 0 || k == N;
-                dv[i + M * (j + M * k)] = bd ? 1.0 : 1.0 / D.st64[0];
+                const bool bd = i == 0 || i == N || j == 0 || j == N || k == 0 || k == N;
+                const int n = i + M * (j + M * k);
+                dv[n] = bd ? 1.0 : 1.0 / D.st64[0];
+                if (!bd) {
+                    const double x = nside(i), y = nside(j), z = nside(k);
+                    kabs[n] = a0 + (x + y + z) * a1 + (x * y + x * z + y * z) * a2 + x * y * z * a3;
+                }
             }
     std::vector<int> tn((size_t)D.ntouch);
     if (D.ntouch) MD_CUDA(cudaMemcpy(tn.data(), D.tn_node, sizeof(int) * D.ntouch, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < D.ntouch; ++i) dv[tn[i]] = 1.0 / (D.st64[0] + D.beta * touch_m[i]);
+    std::vector<double> srow((size_t)D.n3, 0.0);  // beta (Pi^T W Pi) row sums
+    for (int i = 0; i < D.ntouch; ++i) {
+        dv[tn[i]] = 1.0 / (D.st64[0] + D.beta * touch_m[i]);
+        srow[tn[i]] = D.beta * touch_rs[i];
+    }
+    std::vector<float> sv((size_t)D.n3);
+    for (int n = 0; n < D.n3; ++n) {
+        if (kabs[n] == 0.0) { sv[n] = 1.f; continue; }   // Dirichlet row
+        const double c = 1.0 / dv[n];
+        const double rho = std::min(1.0, 2.0 * c / (kabs[n] + srow[n]));
+        sv[n] = (float)(rho / c);
+    }
     for (int i = 0; i < D.n1; ++i) dv[D.n3 + i] = 1.0 / d1[i];
     for (size_t i = 0; i < dv.size(); ++i) fv[i] = (float)dv[i];
     MD_CUDA(cudaMemcpy((void*)D.dinv64, dv.data(), sizeof(double) * dv.size(), cudaMemcpyHostToDevice));
     MD_CUDA(cudaMemcpy((void*)D.dinv32, fv.data(), sizeof(float) * fv.size(), cudaMemcpyHostToDevice));
+    MD_CUDA(cudaMemcpy((void*)D.sminv32, sv.data(), sizeof(float) * sv.size(), cudaMemcpyHostToDevice));
     return MD_OK;
 }
 

@@ -201,21 +201,29 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     for (int q = 0; q < nq; ++q)
         for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) te.push_back({pi_col[j], q, pi_val[j] * wq[q]});
     std::sort(te.begin(), te.end(), [](const TE& p, const TE& r) { return p.node != r.node ? p.node < r.node : p.q < r.q; });
+    // row sums of Pi (less than 1 where boundary weights were dropped)
+    std::vector<double> pi_rowsum(nq, 0.0);
+    for (int q = 0; q < nq; ++q)
+        for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) pi_rowsum[q] += pi_val[j];
     std::vector<int> tn_node, tn_ptr(1, 0), tn_q;
-    std::vector<double> tn_v, touch_m;  // touch_m: diag of Pi^T W Pi at the node
+    // touch_m: diag of Pi^T W Pi at the node; touch_rs: its row sum (all entries
+    // are >= 0), sum_q Pi[q,n] w_q sum_j Pi[q,j]
+    std::vector<double> tn_v, touch_m, touch_rs;
     for (size_t i = 0; i < te.size();) {
         size_t j = i;
-        double dm = 0.0;
+        double dm = 0.0, rs = 0.0;
         while (j < te.size() && te[j].node == te[i].node) {
             tn_q.push_back(te[j].q);
             tn_v.push_back(te[j].v);
             // Pi[q,n]^2 w_q = (Pi[q,n] w_q) * Pi[q,n]
             dm += te[j].v * (te[j].v / wq[te[j].q]);
+            rs += te[j].v * pi_rowsum[te[j].q];
             ++j;
         }
         tn_node.push_back(te[i].node);
         tn_ptr.push_back((int)tn_q.size());
         touch_m.push_back(dm);
+        touch_rs.push_back(rs);
         i = j;
     }
     const int ntouch = (int)tn_node.size();
@@ -339,6 +347,7 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         float* p; UP(dev_alloc(&op->allocs, &p, (size_t)n3, false)); D.dist = p;
         double* dp; UP(dev_alloc(&op->allocs, &dp, (size_t)D.n, false)); D.dinv64 = dp;
         UP(dev_alloc(&op->allocs, &p, (size_t)D.n, false)); D.dinv32 = p;
+        UP(dev_alloc(&op->allocs, &p, (size_t)n3, false)); D.sminv32 = p;
         UP(dev_alloc(&op->allocs, &D.t64, (size_t)nq)); UP(dev_alloc(&op->allocs, &D.t32, (size_t)nq));
         UP(dev_alloc(&op->allocs, &D.lift32, (size_t)n3)); UP(dev_alloc(&op->allocs, &D.ltouch32, (size_t)ntouch));
     }
@@ -350,7 +359,7 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         UP(dev_upload(&op->allocs, &op->off0, &z, 1));
     }
     UP(launch_dist(op, 0));
-    UP(launch_dinv_fill(op, touch_m, d1, 0));
+    UP(launch_dinv_fill(op, touch_m, touch_rs, d1, 0));
     {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return fail(md_cuda_status(e, "md_assemble sync", __FILE__, __LINE__));

@@ -58,6 +58,7 @@ struct InstDesc {
     const float* dist;      // n3
     const double* dinv64;   // n, 1 / diag(A)
     const float* dinv32;
+    const float* sminv32;   // n3, the Jacobi smoother's row scaling rho_i / c_ii (md_apply.cu)
     const double* segs;     // nsegs * 6 segment end points (distance field)
     // scratch owned by the op
     double* t64; float* t32;  // nq
@@ -165,8 +166,8 @@ md_status launch_apply(const Tables& T, const InstDesc* d, int ninst, md_prec pr
                        const long long* off, void* y, cudaStream_t s, const KState* st = nullptr, int gate = 0);
 md_status launch_rhs(const md_op* op, const double* f, double g, double* b, cudaStream_t s);
 md_status launch_dist(md_op* op, cudaStream_t s);
-md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_diag, const std::vector<double>& d1,
-                           cudaStream_t s);
+md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_diag, const std::vector<double>& touch_rowsum,
+                           const std::vector<double>& d1, cudaStream_t s);
 
 // Tables (md_tables.cpp)
 // vec_chunk: elements per block of the streaming vector kernels.  The Krylov

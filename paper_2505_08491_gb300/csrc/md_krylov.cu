@@ -618,6 +618,8 @@ __global__ void __launch_bounds__(TREE_TB) k_tree_lift(const InstDesc* __restric
 // arithmetic, so a block keeps SM_U x 256 loads in flight per array.
 #define SM_U 8
 
+// D^{-1} below is the smoother's row scaling rho_i / c_ii (InstDesc::sminv32):
+// 1 / c_ii on the stencil rows, less on rows the coupling makes heavy.
 // First sweep from x = 0: x = omega D^{-1} b0 (b0 = r0 + l, or r0 in the lower
 // order, which also clears the 1D part of Z).  Whole-vector segments.
 __global__ void __launch_bounds__(MD_TB) k_smooth_first(const Seg* __restrict__ seg, const long long* __restrict__ off,
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_first(const Seg* __restrict__ 
             const int e = e0 + u * MD_TB;
             const bool in3 = e < sg.end && e < n3;
             b[u] = in3 ? vi[e] : 0.f;
-            w[u] = in3 ? d.dinv32[e] : 0.f;
+            w[u] = in3 ? d.sminv32[e] : 0.f;
             if (in3 && use_lift) b[u] += d.lift32[e];
         }
 #pragma unroll
@@ -658,7 +660,7 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_sweep(const Seg* __restrict__ 
     const Seg sg = seg[blockIdx.x];
     if (!cnn_runs(st, sg.inst)) return;
     const long long o = off[sg.inst];
-    const float* dinv = D[sg.inst].dinv32;
+    const float* dinv = D[sg.inst].sminv32;
     const float* vi = v + o;
     const float* ai = az + o;
     float* zi = z + o;
