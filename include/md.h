@@ -194,7 +194,9 @@ md_status md_precondition_lower(const md_op* op, const md_cnn* cnn, const float*
  * post-smoothing around its 3D solve (Section 5, 'Effect of pre- and
  * post-smoothing', the relaxation S_J(C, b0, x0, nu)): with b0 the right-hand
  * side of the 3D solve (r0 + l in the upper order, r0 in the lower one) and
- * D = diag(C),
+ * D^{-1} = diag(rho_i / c_ii), rho_i = min(1, 2 c_ii / S_i), S_i = sum_j |K00_ij|
+ * + beta sum_j (Pi^T W Pi)_ij (Jacobi on stencil rows; on rows the coupling
+ * makes heavy, the scaling that keeps every sweep with omega < 1 contracting),
  *     x  = nu damped Jacobi sweeps x <- x + omega D^{-1} (b0 - C x) from 0,
  *     x += N(b0 - C x)   (network input [(b0 - C x - l)/s, l/s, d_h],
  *                         s = ||b0 - C x||, output (s / alpha) N(X),

@@ -117,7 +117,7 @@ def smoothing_dinv(prob) -> np.ndarray:
     S_i bounding the absolute row sum of C (Gershgorin).  On rows of the
     Q1 stencil S_i <= 2 c_ii and rho_i = 1: plain Jacobi.  On rows the coupling
     makes heavy the scaling shrinks so that 2 diag(c_ii / rho_i) - C is
-    diagonally dominant, and every sweep with damping omega <= 1 contracts
+    diagonally dominant, and every sweep with damping omega < 1 contracts
     (without it, beta = 100 puts eigenvalues of D^{-1} C near 3).  Dirichlet
     rows: 1."""
     p = prob

@@ -19,10 +19,9 @@ from . import _lib as L
 # omega = 2/3.  For the Q1 stiffness stencil (centre 8/3, edges -1/6, corners
 # -1/12, times h) the eigenvalues of D^{-1} K are
 # 1 - (c1 c2 + c1 c3 + c2 c3)/4 - c1 c2 c3/4, c_i = cos(theta_i), which span
-# [1/2, 3/2] on the high frequencies: omega = 2/3 damps those by at least 2/3
-# (omega = 1 by 1/2), and the coupling rows, which at beta = 100 raise the top
-# of the spectrum of D^{-1} C to about 3, are amplified by at most ~1.06 per
-# sweep instead of the factor ~2 of omega = 1.
+# [1/2, 3/2] on the high frequencies: omega = 2/3 damps those by at least 2/3.
+# The library scales the rows the coupling makes heavy so that the spectrum
+# of its D^{-1} C stays within (0, 2], where every omega < 1 contracts.
 SMOOTH_OMEGA = 2.0 / 3.0
 
 

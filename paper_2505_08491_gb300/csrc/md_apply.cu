@@ -187,7 +187,7 @@ md_status launch_dist(md_op* op, cudaStream_t s) {
 // with rho_i = min(1, 2 c_ii / S_i), S_i = sum_j |K00_ij| + beta sum_j (Pi^T W Pi)_ij
 // a bound of the absolute row sum of C (Gershgorin): 1 / c_ii on the stencil
 // rows, smaller where the coupling is heavy, so that damped sweeps with
-// omega <= 1 contract on every mode; 1 on Dirichlet rows.
+// omega < 1 contract on every mode; 1 on Dirichlet rows.
 md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_m, const std::vector<double>& touch_rs,
                            const std::vector<double>& d1, cudaStream_t s) {
     (void)s;
