@@ -161,6 +161,13 @@ class BlockPreconditioner:
     first with the 1D part absent from its right-hand side (l = 0, b0 = r0),
     then z1 = B11^{-1} (r1 - beta M10 z0) = B11^{-1} (r1 + beta Psi^T W Pi z0).
 
+    inner=m > 0 replaces the single 3D solve by m steps of flexible GMRES on
+    C z0 = b0 from z0 = 0, right-preconditioned by that solve (Section 6: the
+    3D block of the coupled preconditioner is '3 steps of P-FGMRES'); in the
+    'cnn' mode the first direction is the network on the block's own input
+    [r0/s, l/s, d] and the later ones on [v_j, 0, d] (the unit Krylov
+    vectors carry no separate lifted part).
+
     smooth=(nu, omega) wraps the 3D solve in Jacobi pre- and post-smoothing
     (Section 5, 'Effect of pre- and post-smoothing'), with the row scaling of
     smoothing_dinv:
@@ -172,11 +179,14 @@ class BlockPreconditioner:
     """
 
     def __init__(self, prob, mode: str = "cnn", params=None, bf16: bool = True, order: str = "upper",
-                 smooth: tuple[int, float] = (0, 1.0)):
+                 smooth: tuple[int, float] = (0, 1.0), inner: int = 0):
         if order not in ("upper", "lower"):
             raise ValueError("order must be 'upper' or 'lower'")
         if smooth[0] < 0:
             raise ValueError("smoothing sweeps must be >= 0")
+        if inner < 0 or (inner > 0 and smooth[0] > 0):
+            raise ValueError("inner steps must be >= 0 and are not combined with smoothing")
+        self.inner = int(inner)
         self.p = prob
         self.mode = mode
         self.params = params
@@ -192,7 +202,10 @@ class BlockPreconditioner:
 
     def solve3(self, r0, l):
         """The 3D block solve for right-hand side r0 + l (l = the lifted 1D
-        part), with Jacobi pre- and post-smoothing when nu > 0."""
+        part), with Jacobi pre- and post-smoothing when nu > 0, or as m inner
+        FGMRES steps when inner = m > 0."""
+        if self.inner > 0:
+            return self.inner_fgmres(r0, l)
         if self.nu == 0:
             return self.inner3(r0, l)
         C = self.p.C
@@ -200,6 +213,25 @@ class BlockPreconditioner:
         x = jacobi_smooth(C, b0, np.zeros_like(b0), self.nu, self.omega, self.sm_dinv)
         x = x + self.inner3(b0 - C @ x - l, l)
         return jacobi_smooth(C, b0, x, self.nu, self.omega, self.sm_dinv)
+
+    def inner_fgmres(self, r0, l):
+        """m steps of right-preconditioned flexible GMRES on C z = r0 + l from
+        z = 0 (the `fgmres` of this module, restart m, no early stop): its
+        first basis vector is v0 = (r0 + l)/||r0 + l||, preconditioned with
+        the split (r0, l) scaled alike; later ones as (v, 0)."""
+        b0 = r0 + l
+        nb = float(np.linalg.norm(b0))
+        if nb == 0.0:
+            return self.inner3(r0, l)
+        calls = [0]
+
+        def P(v):
+            calls[0] += 1
+            if calls[0] == 1:
+                return self.inner3(r0 / nb, l / nb)
+            return self.inner3(v, np.zeros_like(v))
+        z, _, _ = fgmres(self.p.C, b0, P, 0.0, restart=self.inner, maxit=self.inner)
+        return z
 
     def inner3(self, r0, l):
         """One application of the 3D solve of `mode` to r0 + l."""

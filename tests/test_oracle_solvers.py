@@ -274,3 +274,69 @@ def test_smoothed_cnn_preconditioner_homogeneous(tree8, order):
     v2 = v.copy()
     v2[:p.n3][p.bd] = 1.25
     assert np.allclose(Q(v2)[:p.n3][p.bd], 1.25, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+def test_inner_fgmres_keeps_exact_block_inverse(tree8, order):
+    """Inner FGMRES steps preconditioned by the exact 3D solve reach C^{-1} b0
+    in the first step; the block preconditioner stays the inverse of the
+    block triangular part."""
+    p = tree8
+    if order == "upper":
+        T = sp.bmat([[p.C, p.beta * p.M01], [None, p.B11]], format="csr")
+    else:
+        T = sp.bmat([[p.C, None], [p.A[p.n3:, :p.n3], p.B11]], format="csr")
+    Q = solvers.BlockPreconditioner(p, mode="exact", order=order, inner=3)
+    x = np.random.default_rng(15).standard_normal(p.n)
+    assert np.linalg.norm(Q(T @ x) - x) / np.linalg.norm(x) < 1e-9
+
+
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_inner_fgmres_with_jacobi_is_minimal_residual(tree8, m):
+    """With the linear Jacobi 3D solve, m inner steps return the minimiser of
+    ||b0 - C x|| over x in D^{-1} K_m(C D^{-1}, b0) (right-preconditioned
+    GMRES): least squares on an explicit orthonormal basis of that space."""
+    p = tree8
+    rng = np.random.default_rng(16)
+    r0 = rng.standard_normal(p.n3)
+    l = rng.standard_normal(p.n3)
+    l[p.bd] = 0.0
+    b0 = r0 + l
+    Q = solvers.BlockPreconditioner(p, mode="jacobi", inner=m)
+    x = Q.solve3(r0, l)
+    dinv = 1.0 / p.C.diagonal()
+    K = [b0 / np.linalg.norm(b0)]
+    for _ in range(m - 1):
+        w = p.C @ (dinv * K[-1])
+        K.append(w / np.linalg.norm(w))
+    Qb, _ = np.linalg.qr(np.array(K).T)
+    CB = p.C @ (dinv[:, None] * Qb)
+    y, *_ = np.linalg.lstsq(CB, b0, rcond=None)
+    ref = dinv * (Qb @ y)
+    assert np.linalg.norm(x - ref) <= 1e-9 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+def test_one_inner_step_is_network_with_minimal_residual_scale(tree8, order):
+    """One inner step with the network: z0 = c N(X) for the block's own
+    input X = [r0/s, l/s, d] (the first direction keeps the split of b0),
+    c = (C z, b0) / ||C z||^2 minimising ||b0 - c C z||; and the inner
+    variant stays positively homogeneous."""
+    p = tree8
+    params = cnn.init_params(6)
+    rng = np.random.default_rng(17)
+    r0 = rng.standard_normal(p.n3)
+    r0[p.bd] = 0.0
+    l = rng.standard_normal(p.n3) if order == "upper" else np.zeros(p.n3)
+    l[p.bd] = 0.0
+    Q1 = solvers.BlockPreconditioner(p, mode="cnn", params=params, bf16=False, order=order, inner=1)
+    Q0 = solvers.BlockPreconditioner(p, mode="cnn", params=params, bf16=False, order=order)
+    z = Q0.solve3(r0, l)
+    Cz = p.C @ z
+    c = float(Cz @ (r0 + l)) / float(Cz @ Cz)
+    assert np.allclose(Q1.solve3(r0, l), c * z, rtol=1e-10, atol=1e-12 * np.abs(z).max())
+    Q3 = solvers.BlockPreconditioner(p, mode="cnn", params=params, bf16=False, order=order, inner=3)
+    v = rng.standard_normal(p.n)
+    v[:p.n3][p.bd] = 0.0
+    zq = Q3(v)
+    assert np.allclose(Q3(2.5 * v), 2.5 * zq, rtol=1e-9, atol=1e-12 * np.abs(zq).max())
