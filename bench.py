@@ -130,7 +130,7 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smooth=(0, 1.0)):
+def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smooth=(0, 1.0), inner=0):
     """Oracle FGMRES(30) + network (FP64 CPU) on one instance.  Returns
     (seconds, iterations, relres, completed)."""
     from oracle import fem, solvers
@@ -138,7 +138,7 @@ def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smo
     layers = [(W, b) for W, b in flat_to_layers(params_flat)]
     p = fem.Problem(inst["N"], inst["graph"], inst["beta"])
     b = p.rhs(p.source(inst["f_seed"]), inst["g"])
-    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order=order, smooth=smooth)
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order=order, smooth=smooth, inner=inner)
     hist = []
     t0 = time.perf_counter()
     if max_seconds is None:
@@ -169,6 +169,7 @@ def bench_config(args, grid_nodes):
             "instances_per_gpu": args.count, "grid_nodes_per_gpu": grid_nodes,
             "prec_order": getattr(args, "prec_order", "upper"),
             "jacobi_smoothing": {"sweeps_before_and_after": args.smooth, "omega": args.omega},
+            "inner_fgmres_steps": args.inner,
             "l2": "working set > L2, 256 MB flush between steps", "precision":
             "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"}
 
@@ -181,11 +182,12 @@ def reference_arm(args):
     params = default_network_params(args.prec_order)
     insts = instances(args.workload, 0, args.count)
     for w in range(args.warmup):
-        oracle_solve_seconds(insts[w % len(insts)], params, order=args.prec_order, smooth=(args.smooth, args.omega))
+        oracle_solve_seconds(insts[w % len(insts)], params, order=args.prec_order, smooth=(args.smooth, args.omega),
+                             inner=args.inner)
     ts, its = [], []
     for k in range(args.steps):
         t, it, rel, done = oracle_solve_seconds(insts[(args.warmup + k) % len(insts)], params, order=args.prec_order,
-                                                smooth=(args.smooth, args.omega))
+                                                smooth=(args.smooth, args.omega), inner=args.inner)
         ts.append(t)
         its.append(it)
     total = sum(ts)
@@ -216,6 +218,8 @@ def main():
     ap.add_argument("--smooth", type=int, default=0,
                     help="damped Jacobi sweeps before and after the network in the 3D solve (0: none)")
     ap.add_argument("--omega", type=float, default=None, help="damping of those sweeps (default: the package's SMOOTH_OMEGA, 2/3)")
+    ap.add_argument("--inner", type=int, default=0,
+                    help="the 3D block solve as this many inner FGMRES steps with the network (0: one application)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     args = ap.parse_args()
@@ -264,6 +268,7 @@ def main():
     B = Batch(ops, "fgmres_cnn", net, restart=restart_of(args.workload))
     B.set_prec_order(args.prec_order)
     B.set_smoothing(args.smooth, args.omega)
+    B.set_inner_iters(args.inner)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -366,7 +371,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         its0 = its_all[-1][0]
         t, it, rel, done = oracle_solve_seconds(insts[0], params, max_seconds=20.0, order=args.prec_order,
-                                                smooth=(args.smooth, args.omega))
+                                                smooth=(args.smooth, args.omega), inner=args.inner)
         per_it = t / max(it, 1)
         cpu = {"value": 1.0 / (per_it * its0), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"instance 0, FP64 oracle FGMRES(30)+network: {it} iterations timed ({t:.1f} s), "

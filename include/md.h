@@ -210,6 +210,22 @@ md_status md_precondition_lower(const md_op* op, const md_cnn* cnn, const float*
 md_status md_precondition_smoothed(const md_op* op, const md_cnn* cnn, int lower, int nu, double omega,
                                    const float* r, float* z, md_stream s);
 
+/* md_precondition_inner -- the network preconditioner whose 3D block solve is
+ * m steps of flexible GMRES on C z0 = b0 from z0 = 0, right-preconditioned by
+ * the network (Section 6: the 3D solve of the block preconditioner as '3
+ * steps of P-FGMRES'): v_0 = b0 / ||b0||, z_0 the network on the block's own
+ * input [r0/s, l/s, d_h] scaled by 1/||b0||, later z_j the network on
+ * [v_j, 0, d_h]; w = C z_j orthogonalised against v_0..v_j (two classical
+ * Gram-Schmidt passes, FP64 sums), v_{j+1} = w / ||w||; then
+ * z0 = sum_j y_j z_j with y the FP64 least-squares solution of
+ * min ||b0|| e_1 - H y||.  z1 as in md_precondition (lower = 0) or
+ * md_precondition_lower (lower = 1).  m in [0, 4] (0: one network
+ * application), else MD_ERR_ARG; cnn must not be NULL.  r, z: device float,
+ * n.  Uses the operator's cached solver scratch (allocated at the first call):
+ * calls on one operator must be ordered.  Asynchronous. */
+md_status md_precondition_inner(const md_op* op, const md_cnn* cnn, int lower, int m, const float* r, float* z,
+                                md_stream s);
+
 /* md_lift -- the 1D part of the preconditioner on its own (Section 3 eqs.
  * (matrixC), (setB)): z1 = B11^{-1} r1 (tree factorisation) and its forcing on
  * the 3D problem l = -beta M01 z1 = beta Pi^T W Psi z1.  With r1 the 1D load
@@ -290,6 +306,11 @@ md_status md_batch_set_prec_order(md_batch* b, int lower);
  * md_precondition_smoothed; 0 (default): no smoothing.  Limits and errors as
  * md_precondition_smoothed. */
 md_status md_batch_set_smoothing(md_batch* b, int nu, double omega);
+/* m > 0: the network-preconditioned batch solves its 3D block by m inner
+ * FGMRES steps, as md_precondition_inner (buffers of 9 vectors of the batch's
+ * length are allocated at the first call); 0 (default): one network
+ * application.  Not combined with smoothing (MD_ERR_ARG). */
+md_status md_batch_set_inner_iters(md_batch* b, int m);
 md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
 md_status md_batch_reset_stats(md_batch* b);
 

@@ -74,6 +74,8 @@ SIGNATURES = {
     "md_batch_set_prec_order": (st, [vp, i32]),
     "md_batch_set_smoothing": (st, [vp, i32, f64]),
     "md_precondition_smoothed": (st, [vp, vp, i32, i32, f64, vp, vp, vp]),
+    "md_batch_set_inner_iters": (st, [vp, i32]),
+    "md_precondition_inner": (st, [vp, vp, i32, i32, vp, vp, vp]),
     "md_solve": (st, [vp, vp, vp, vp, f64, i32, i32, C.POINTER(i32), C.POINTER(f64), vp]),
     "md_batch_create": (st, [i32, C.POINTER(vp), vp, i32, i32, C.POINTER(vp)]),
     "md_batch_destroy": (None, [vp]),

@@ -108,14 +108,24 @@ class Operator:
         return out
 
     def precondition(self, r: torch.Tensor, net: "Network | None" = None, out=None, order: str = "upper",
-                     smooth: tuple[int, float] | None = None) -> torch.Tensor:
+                     smooth: tuple[int, float] | None = None, inner: int | None = None) -> torch.Tensor:
         """z = Q r: block upper-triangular order (the paper's), or order='lower'
         (network first, then the 1D solve); net=None gives Jacobi.
         smooth=(nu, omega): nu damped Jacobi sweeps before and after the
-        network (md_precondition_smoothed)."""
+        network (md_precondition_smoothed).  inner=m: the 3D solve as m
+        inner FGMRES steps preconditioned by the network
+        (md_precondition_inner)."""
         z = torch.empty_like(r) if out is None else out
         if order not in ("upper", "lower"):
             raise ValueError("order must be 'upper' or 'lower'")
+        if inner is not None:
+            if net is None or smooth is not None:
+                raise ValueError("inner steps need a network and exclude smoothing")
+            L.check(L.load().md_precondition_inner(self._h, net.handle, 1 if order == "lower" else 0, int(inner),
+                                                   _ptr(r, torch.float32, self.n, "r"),
+                                                   _ptr(z, torch.float32, self.n, "z"), _stream()),
+                    "md_precondition_inner")
+            return z
         if smooth is not None:
             if net is None:
                 raise ValueError("smoothing wraps the network solve: give a network")
@@ -333,6 +343,10 @@ class Batch:
         omega defaults to SMOOTH_OMEGA."""
         om = SMOOTH_OMEGA if omega is None else float(omega)
         L.check(L.load().md_batch_set_smoothing(self._h, int(nu), om), "md_batch_set_smoothing")
+
+    def set_inner_iters(self, m: int):
+        """The 3D block solve as m inner FGMRES steps (0: one network application)."""
+        L.check(L.load().md_batch_set_inner_iters(self._h, int(m)), "md_batch_set_inner_iters")
 
     def set_profiling(self, enable: bool):
         L.check(L.load().md_batch_set_profiling(self._h, 1 if enable else 0), "md_batch_set_profiling")

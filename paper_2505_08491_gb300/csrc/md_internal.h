@@ -12,6 +12,7 @@
 #define MD_KMAX 64              // largest FGMRES restart length
 #define MD_MAXR (MD_KMAX + 4)   // reduction values per block
 #define MD_TB 256               // threads per block of the streaming kernels
+#define MD_INNER_MAX 4          // most inner FGMRES steps of the 3D block solve
 
 // ---------------------------------------------------------------------------
 // error handling
@@ -140,6 +141,12 @@ struct KState {
     double relres_prev;                  // true relative residual at the previous restart
     int j, m, active, converged, iters, reorth, nan_seen, fallback, maxit, cycle_iters, stalls;
     int fb_iter;                         // iteration at which the Jacobi fallback began
+    // inner FGMRES steps of the 3D block solve: Hessenberg (column j at
+    // iH[j * (MD_INNER_MAX + 1)]), Gram-Schmidt coefficients, solution, ||b0||
+    double iH[(MD_INNER_MAX + 1) * MD_INNER_MAX];
+    double icoef[MD_INNER_MAX + 1];
+    double iy[MD_INNER_MAX];
+    double ib0;
     unsigned int counter[8];             // last-block counters per reduction kernel
 };
 

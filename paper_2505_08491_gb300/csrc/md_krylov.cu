@@ -68,6 +68,9 @@ struct md_batch {
     int executed_slots = 0;              // slots the last cycle ran
     int prec_order = 0;                  // 0: block upper-triangular (the paper's), 1: lower
     int graph_prec_order = 0;
+    int inner_m = 0;                     // inner FGMRES steps of the 3D block solve (0: one network application)
+    int graph_inner_m = 0;
+    float *iV = nullptr, *iZ = nullptr;  // their basis (MD_INNER_MAX + 1) and directions (MD_INNER_MAX), x total
     int smooth_nu = 0;                   // Jacobi sweeps before and after the network (0: none)
     float smooth_omega = 1.f;            // their damping
     int graph_smooth_nu = 0;
@@ -749,6 +752,248 @@ __global__ void __launch_bounds__(MD_TB) k_smooth_add(const Seg* __restrict__ se
     }
 }
 
+// ---- the 3D block solve as m steps of flexible GMRES on C (Section 6: '3 steps
+// of P-FGMRES' as the 3D solve of the block preconditioner) -------------------------
+// Per instance, basis vectors iV_0..iV_m and directions iZ_j = N(iV_j), whole
+// length; the 1D parts of iZ stay zero, so the operator apply gives C iZ_j in
+// the 3D part.  iZ_0 is the network on the block's own input ([r0/s, l/s, d]),
+// iV_0 = b0 / s; W = C iZ_j is orthogonalised against iV_0..iV_j by two
+// classical Gram-Schmidt passes (FP64 sums per instance), iV_{j+1} = W / ||W||,
+// and iZ_{j+1} is the network on [iV_{j+1}, 0, d].  After m steps
+// z0 = sum_j y_j iZ_j, y the FP64 least-squares solution of min ||s e_1 - H y||.
+
+// iV_0 = b0 / s (b0 = r0 + l, or r0 in the lower order), iZ_0 /= s, H = 0.
+__global__ void __launch_bounds__(MD_TB) k_inner_start(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                       const InstDesc* __restrict__ D, const float* __restrict__ v,
+                                                       float* iv0, float* iz0, KState* st, int use_lift) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    KState& S = st[sg.inst];
+    const InstDesc& d = D[sg.inst];
+    const long long o = off[sg.inst];
+    const double s = S.s;
+    const float inv = s > 0.0 ? (float)(1.0 / s) : 0.f;
+    if (sg.begin == 0) {
+        for (int i = threadIdx.x; i < (MD_INNER_MAX + 1) * MD_INNER_MAX; i += blockDim.x) S.iH[i] = 0.0;
+        if (threadIdx.x == 0) S.ib0 = s;
+    }
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += SM_U * MD_TB) {
+        float b[SM_U], z[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            const bool in = e < sg.end;
+            b[u] = in ? v[o + e] : 0.f;
+            z[u] = in ? iz0[o + e] : 0.f;
+            if (in && use_lift) b[u] += d.lift32[e];
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) {
+                iv0[o + e] = b[u] * inv;
+                iz0[o + e] = z[u] * inv;
+            }
+        }
+    }
+}
+
+// (W, iV_i) for i <= j over the 3D part, W = iV_{j+1}; the instance's last
+// block stores them as this pass's coefficients and adds them to column j of H.
+__global__ void __launch_bounds__(MD_TB) k_inner_dots(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                      const long long* __restrict__ off, const float* __restrict__ iV,
+                                                      long long total, int j, KState* st, double* part) {
+    __shared__ double sh[32 * MD_INNER_MAX];
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    KState& S = st[sg.inst];
+    const long long o = off[sg.inst];
+    const float* W = iV + (long long)(j + 1) * total + o;
+    const float* V0 = iV + o;
+    constexpr int U = 2;
+    float acc[MD_INNER_MAX];
+#pragma unroll
+    for (int i = 0; i < MD_INNER_MAX; ++i) acc[i] = 0.f;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += U * MD_TB) {
+        float w[U], x[MD_INNER_MAX][U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * MD_TB;
+            w[u] = e < sg.end ? W[e] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < MD_INNER_MAX; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * MD_TB;
+                x[i][u] = (i <= j && e < sg.end) ? V0[(long long)i * total + e] : 0.f;
+            }
+#pragma unroll
+        for (int i = 0; i < MD_INNER_MAX; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc[i] = fmaf(w[u], x[i][u], acc[i]);
+    }
+    double vals[MD_INNER_MAX];
+#pragma unroll
+    for (int i = 0; i < MD_INNER_MAX; ++i) vals[i] = (double)acc[i];
+    double flag;
+    reduce_values<MD_INNER_MAX>(vals, j + 1, part, blockIdx.x, rng[sg.inst], &S.counter[6], &flag, sh);
+    if (flag == 1.0) {
+        for (int r = threadIdx.x; r <= j; r += blockDim.x) {
+            S.icoef[r] = sh[r];
+            S.iH[(size_t)j * (MD_INNER_MAX + 1) + r] += sh[r];
+        }
+    }
+}
+
+// W -= sum_{i<=j} coef_i iV_i over the 3D part and ||W||^2; after the second
+// pass the last block stores H[j+1, j] = ||W|| and sets the network's input
+// scale to 1 for the normalised iV_{j+1}.
+__global__ void __launch_bounds__(MD_TB) k_inner_update(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                        const long long* __restrict__ off, float* iV, long long total,
+                                                        int j, int pass, KState* st, double* part) {
+    __shared__ double sh[32 * 4];
+    __shared__ float sc[MD_INNER_MAX];
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    KState& S = st[sg.inst];
+    if (threadIdx.x < MD_INNER_MAX) sc[threadIdx.x] = (int)threadIdx.x <= j ? (float)S.icoef[threadIdx.x] : 0.f;
+    __syncthreads();
+    const long long o = off[sg.inst];
+    float* W = iV + (long long)(j + 1) * total + o;
+    const float* V0 = iV + o;
+    constexpr int U = 2;
+    float a = 0.f;
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += U * MD_TB) {
+        float w[U], x[MD_INNER_MAX][U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * MD_TB;
+            w[u] = e < sg.end ? W[e] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < MD_INNER_MAX; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * MD_TB;
+                x[i][u] = (i <= j && e < sg.end) ? V0[(long long)i * total + e] : 0.f;
+            }
+#pragma unroll
+        for (int i = 0; i < MD_INNER_MAX; ++i)
+#pragma unroll
+            for (int u = 0; u < U; ++u) w[u] = fmaf(-sc[i], x[i][u], w[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) {
+                W[e] = w[u];
+                a = fmaf(w[u], w[u], a);
+            }
+        }
+    }
+    double vals[1] = {(double)a};
+    double flag;
+    reduce_values<1>(vals, 1, part, blockIdx.x, rng[sg.inst], &S.counter[7], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0 && pass == 1) {
+        S.iH[(size_t)j * (MD_INNER_MAX + 1) + j + 1] = sqrt(sh[0]);
+        S.s = 1.0;
+    }
+}
+
+// iV_{j+1} = W / H[j+1, j] (zero after a breakdown).
+__global__ void __launch_bounds__(MD_TB) k_inner_scale(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                       float* iV, long long total, int j, const KState* st) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const double h = st[sg.inst].iH[(size_t)j * (MD_INNER_MAX + 1) + j + 1];
+    const float inv = h > 0.0 ? (float)(1.0 / h) : 0.f;
+    float* W = iV + (long long)(j + 1) * total + off[sg.inst];
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += SM_U * MD_TB) {
+        float w[SM_U];
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            w[u] = e < sg.end ? W[e] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < SM_U; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e < sg.end) W[e] = w[u] * inv;
+        }
+    }
+}
+
+// Givens rotations on the (m+1) x m Hessenberg and back substitution for
+// min ||s e_1 - H y||; one thread per instance.
+__global__ void k_inner_lsq(KState* st, int ninst, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst || !cnn_runs(st, i)) return;
+    KState& S = st[i];
+    double H[(MD_INNER_MAX + 1) * MD_INNER_MAX];
+    double g[MD_INNER_MAX + 1], cs[MD_INNER_MAX], sn[MD_INNER_MAX];
+    for (int r = 0; r < (MD_INNER_MAX + 1) * MD_INNER_MAX; ++r) H[r] = S.iH[r];
+    for (int r = 0; r <= MD_INNER_MAX; ++r) g[r] = 0.0;
+    g[0] = S.ib0;
+    for (int j = 0; j < m; ++j) {
+        double* col = H + j * (MD_INNER_MAX + 1);
+        for (int r = 0; r < j; ++r) {
+            const double t = cs[r] * col[r] + sn[r] * col[r + 1];
+            col[r + 1] = -sn[r] * col[r] + cs[r] * col[r + 1];
+            col[r] = t;
+        }
+        const double den = hypot(col[j], col[j + 1]);
+        if (den > 0.0 && isfinite(den)) {
+            cs[j] = col[j] / den;
+            sn[j] = col[j + 1] / den;
+        } else {
+            cs[j] = 1.0;
+            sn[j] = 0.0;
+        }
+        col[j] = cs[j] * col[j] + sn[j] * col[j + 1];
+        col[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        double t = g[r];
+        for (int l = r + 1; l < m; ++l) t -= H[l * (MD_INNER_MAX + 1) + r] * S.iy[l];
+        const double dgl = H[r * (MD_INNER_MAX + 1) + r];
+        S.iy[r] = (dgl != 0.0 && isfinite(t / dgl)) ? t / dgl : 0.0;
+    }
+}
+
+// z0 = sum_j y_j iZ_j (3D part).
+__global__ void __launch_bounds__(MD_TB) k_inner_combine(const Seg* __restrict__ seg, const long long* __restrict__ off,
+                                                         const float* __restrict__ iZ, long long total, float* z,
+                                                         const KState* st, int m) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const KState& S = st[sg.inst];
+    float y[MD_INNER_MAX];
+#pragma unroll
+    for (int j = 0; j < MD_INNER_MAX; ++j) y[j] = j < m ? (float)S.iy[j] : 0.f;
+    const long long o = off[sg.inst];
+    for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += 2 * MD_TB) {
+        float x[MD_INNER_MAX][2];
+#pragma unroll
+        for (int j = 0; j < MD_INNER_MAX; ++j)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = e0 + u * MD_TB;
+                x[j][u] = (j < m && e < sg.end) ? iZ[(long long)j * total + o + e] : 0.f;
+            }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * MD_TB;
+            if (e >= sg.end) continue;
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < MD_INNER_MAX; ++j) acc = fmaf(y[j], x[j][u], acc);
+            z[o + e] = acc;
+        }
+    }
+}
+
 // ||v0||^2 of a preconditioner input given from outside the solver
 __global__ void __launch_bounds__(MD_TB) k_norm3(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                  const long long* __restrict__ off, const float* __restrict__ v,
@@ -969,6 +1214,56 @@ static md_status launch_precond_smoothed(md_batch* B, const md_cnn* cnn, const f
     return MD_OK;
 }
 
+// The network preconditioner with the 3D solve as B->inner_m inner FGMRES
+// steps on C (kernels above).  The conv events bracket the first network
+// application only.
+static md_status launch_precond_inner(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, cudaStream_t s,
+                                      cudaEvent_t e_conv0, cudaEvent_t e_conv1) {
+    const Tables& T = B->tabs;
+    const size_t smem = (size_t)B->max_n1 * 20;
+    const bool lower = B->prec_order == 1;
+    const long long tot = B->total;
+    const int m = B->inner_m;
+    if (lower) {
+        k_lower_setup<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
+    } else {
+        k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
+    }
+    MD_CHECK_LAUNCH();
+    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, B->iZ, s, !lower));
+    OutIO io0{B->iZ, B->off, vin, B->off, B->st, B->d};
+    MD_TRY(cnn_forward_layers(cnn, B->cw, io0, CONV_PREC, s, e_conv0, e_conv1));
+    k_inner_start<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->off, B->d, vin, B->iV, B->iZ, B->st, !lower);
+    MD_CHECK_LAUNCH();
+    for (int j = 0; j < m; ++j) {
+        float* Zj = B->iZ + (long long)j * tot;
+        float* W = B->iV + (long long)(j + 1) * tot;
+        MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
+        for (int pass = 0; pass < 2; ++pass) {
+            k_inner_dots<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, B->iV, tot, j, B->st, B->part);
+            k_inner_update<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, B->iV, tot, j, pass, B->st,
+                                                           B->part);
+            MD_CHECK_LAUNCH();
+        }
+        k_inner_scale<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->off, B->iV, tot, j, B->st);
+        MD_CHECK_LAUNCH();
+        if (j + 1 < m) {
+            float* Zn = B->iZ + (long long)(j + 1) * tot;
+            MD_TRY(cnn_pack_prec(B->cw, B->d, W, B->off, B->st, Zn, s, false));
+            OutIO io{Zn, B->off, W, B->off, B->st, B->d};
+            MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s));
+        }
+    }
+    k_inner_lsq<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst, m);
+    k_inner_combine<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->off, B->iZ, tot, zout, B->st, m);
+    MD_CHECK_LAUNCH();
+    if (lower) {
+        k_lower_1d<<<B->ninst, TREE_TB, smem + (size_t)B->max_nq * 4, s>>>(B->d, B->off, vin, zout, B->st);
+        MD_CHECK_LAUNCH();
+    }
+    return MD_OK;
+}
+
 static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, float* tmp,
                                 cudaStream_t s, cudaEvent_t e_conv0 = nullptr, cudaEvent_t e_conv1 = nullptr) {
     const Tables& T = B->tabs;
@@ -982,6 +1277,7 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     // instances whose network application broke down continue with Jacobi
     k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 1);
     MD_CHECK_LAUNCH();
+    if (B->inner_m > 0) return launch_precond_inner(B, cnn, vin, zout, s, e_conv0, e_conv1);
     if (B->smooth_nu > 0) return launch_precond_smoothed(B, cnn, vin, zout, tmp, s, e_conv0, e_conv1);
     const size_t smem = (size_t)B->max_n1 * 20;
     const bool lower = B->prec_order == 1;
@@ -1111,7 +1407,7 @@ static md_status build_graph(md_batch* B) {
     const bool have = B->solver == MD_SOLVER_CG_JACOBI ? B->graph != nullptr : B->restart_graph != nullptr;
     if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
         B->graph_prec_order == B->prec_order && B->graph_smooth_nu == B->smooth_nu &&
-        B->graph_smooth_omega == B->smooth_omega)
+        B->graph_smooth_omega == B->smooth_omega && B->graph_inner_m == B->inner_m)
         return MD_OK;
     destroy_graphs(B);
     if (B->profiling && B->ev.empty()) {
@@ -1143,6 +1439,7 @@ static md_status build_graph(md_batch* B) {
     B->graph_prec_order = B->prec_order;
     B->graph_smooth_nu = B->smooth_nu;
     B->graph_smooth_omega = B->smooth_omega;
+    B->graph_inner_m = B->inner_m;
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
     return MD_OK;
@@ -1512,6 +1809,10 @@ static md_status check_smoothing(int nu, double omega, const char* who) {
 extern "C" md_status md_batch_set_smoothing(md_batch* B, int nu, double omega) {
     if (!B) { md_set_error("md_batch_set_smoothing: NULL batch"); return MD_ERR_ARG; }
     MD_TRY(check_smoothing(nu, omega, "md_batch_set_smoothing"));
+    if (nu > 0 && B->inner_m > 0) {
+        md_set_error("md_batch_set_smoothing: not combined with inner FGMRES steps");
+        return MD_ERR_ARG;
+    }
     B->smooth_nu = nu;
     B->smooth_omega = (float)omega;
     return MD_OK;
@@ -1529,19 +1830,23 @@ extern "C" md_status md_precondition_smoothed(const md_op* op, const md_cnn* cnn
     MD_TRY(op_batch(op, MD_SOLVER_FGMRES_CNN, 1, cnn, &B));
     const int keep_order = B->prec_order, keep_nu = B->smooth_nu;
     const float keep_omega = B->smooth_omega;
+    const int keep_m = B->inner_m;
     B->prec_order = lower;
     B->smooth_nu = nu;
     B->smooth_omega = (float)omega;
+    B->inner_m = 0;
     // active, not fallen back; the input norm pieces are recomputed
     k_lift_setup<<<1, 1, 0, s>>>(B->st);
     const Tables& T = B->tabs;
     k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
-    md_status st = cudaGetLastError() == cudaSuccess ? MD_OK : MD_ERR_CUDA;
-    if (st != MD_OK) md_set_error("md_precondition_smoothed: launch failed");
+    md_status st = MD_OK;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = md_cuda_status(e, "md_precondition_smoothed", __FILE__, __LINE__);
     if (st == MD_OK) st = launch_precond(B, cnn, r, z, B->V + B->total, s);
     B->prec_order = keep_order;
     B->smooth_nu = keep_nu;
     B->smooth_omega = keep_omega;
+    B->inner_m = keep_m;
     return st;
 }
 
@@ -1557,4 +1862,65 @@ extern "C" md_status md_precondition(const md_op* op, const md_cnn* cnn, const f
         MD_CHECK_LAUNCH();
     }
     return launch_precond(B, cnn, r, z, B->V + B->total, s);
+}
+
+// Inner FGMRES buffers of a network-preconditioned batch, allocated once at
+// the largest step count (their addresses are baked into captured graphs).
+static md_status ensure_inner(md_batch* B) {
+    if (B->iV) return MD_OK;
+    if (B->solver != MD_SOLVER_FGMRES_CNN || !B->cw) {
+        md_set_error("inner FGMRES steps need a network-preconditioned batch");
+        return MD_ERR_ARG;
+    }
+    MD_TRY(dev_alloc(&B->allocs, &B->iV, (size_t)(MD_INNER_MAX + 1) * B->total));
+    MD_TRY(dev_alloc(&B->allocs, &B->iZ, (size_t)MD_INNER_MAX * B->total));
+    return MD_OK;
+}
+
+static md_status check_inner(int m, const char* who) {
+    if (m < 0 || m > MD_INNER_MAX) {
+        md_set_error("%s: inner steps must be in [0, %d] (got %d)", who, MD_INNER_MAX, m);
+        return MD_ERR_ARG;
+    }
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_set_inner_iters(md_batch* B, int m) {
+    if (!B) { md_set_error("md_batch_set_inner_iters: NULL batch"); return MD_ERR_ARG; }
+    MD_TRY(check_inner(m, "md_batch_set_inner_iters"));
+    if (m > 0 && B->smooth_nu > 0) {
+        md_set_error("md_batch_set_inner_iters: not combined with smoothing");
+        return MD_ERR_ARG;
+    }
+    if (m > 0) MD_TRY(ensure_inner(B));
+    B->inner_m = m;
+    return MD_OK;
+}
+
+extern "C" md_status md_precondition_inner(const md_op* op, const md_cnn* cnn, int lower, int m, const float* r,
+                                           float* z, md_stream stream) {
+    if (!op || !cnn || !r || !z || (lower != 0 && lower != 1)) {
+        md_set_error("md_precondition_inner: bad argument");
+        return MD_ERR_ARG;
+    }
+    MD_TRY(check_inner(m, "md_precondition_inner"));
+    cudaStream_t s = (cudaStream_t)stream;
+    md_batch* B = nullptr;
+    MD_TRY(op_batch(op, MD_SOLVER_FGMRES_CNN, 1, cnn, &B));
+    MD_TRY(ensure_inner(B));
+    const int keep_order = B->prec_order, keep_m = B->inner_m, keep_nu = B->smooth_nu;
+    B->prec_order = lower;
+    B->inner_m = m;
+    B->smooth_nu = 0;
+    k_lift_setup<<<1, 1, 0, s>>>(B->st);
+    const Tables& T = B->tabs;
+    k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, B->off, r, B->st, B->part);
+    md_status st = MD_OK;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = md_cuda_status(e, "md_precondition_inner", __FILE__, __LINE__);
+    if (st == MD_OK) st = launch_precond(B, cnn, r, z, B->V + B->total, s);
+    B->prec_order = keep_order;
+    B->inner_m = keep_m;
+    B->smooth_nu = keep_nu;
+    return st;
 }

@@ -135,3 +135,34 @@ def test_smoothed_solve_matches_oracle_iterations(setup, order):
     _, it_o, rel_o = solvers.fgmres(p.A, b, Q, 1e-8, restart=30, maxit=500)
     assert rel_o <= 1e-8
     assert its[0] <= 1.2 * it_o + 2 and it_o <= 1.2 * its[0] + 2, (its[0], it_o)
+
+
+@pytest.mark.parametrize("order", ["upper", "lower"])
+def test_inner_fgmres_solve_matches_oracle_iterations(setup, order):
+    """FGMRES(30) whose 3D block solve is three inner FGMRES steps with the
+    network (Section 6) in the batched solve: converges on the benchmark
+    instances to the true residual 1e-8, and on instance 0 needs the
+    oracle's FP64 FGMRES iterations with the same inner steps, order and
+    weights within 1.2x + 2."""
+    from paper_2505_08491_gb300 import Batch, Network
+    from paper_2505_08491_gb300.weights import default_network_params, flat_to_layers
+    insts, ops, b_all = setup
+    params = default_network_params(order)
+    net = Network(params)
+    B = Batch(ops, "fgmres_cnn", net, restart=30)
+    B.set_prec_order(order)
+    B.set_inner_iters(3)
+    x = torch.zeros_like(b_all)
+    its, rels, ok = B.solve(b_all, x, tol=1e-8, maxit=2000)
+    assert ok and max(rels) <= 1e-8
+    assert B.stats()["fallback_instances"] == 0
+    w = insts[0]
+    p = fem.Problem(w["N"], w["graph"], w["beta"])
+    b = p.rhs(p.source(w["f_seed"]), w["g"])
+    xs = x[:p.n].cpu().numpy()
+    assert np.linalg.norm(b - p.A @ xs) / np.linalg.norm(b) <= 1.01e-8
+    layers = [(cnn.round_bf16(W), np.asarray(bb, np.float32).astype(np.float64)) for W, bb in flat_to_layers(params)]
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order=order, inner=3)
+    _, it_o, rel_o = solvers.fgmres(p.A, b, Q, 1e-8, restart=30, maxit=500)
+    assert rel_o <= 1e-8
+    assert its[0] <= 1.2 * it_o + 2 and it_o <= 1.2 * its[0] + 2, (its[0], it_o)

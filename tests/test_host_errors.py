@@ -66,3 +66,9 @@ def test_smoothing_entries_reject_null_handles(lib):
     assert lib.md_batch_set_smoothing(None, 1, 0.5) == -1
     assert lib.md_precondition_smoothed(None, None, 0, 1, 0.5, None, None, None) == -1
     assert b"md_precondition_smoothed" in lib.md_last_error()
+
+
+def test_inner_entries_reject_null_handles(lib):
+    assert lib.md_batch_set_inner_iters(None, 1) == -1
+    assert lib.md_precondition_inner(None, None, 0, 1, None, None, None) == -1
+    assert b"md_precondition_inner" in lib.md_last_error()
