@@ -1750,7 +1750,12 @@ md_status launch_prec_input(const Tables& T, const InstDesc* d, const long long*
 }
 
 // Standalone preconditioner application (one instance).
-__global__ void k_prec_setup(KState* st) { st[0].active = 1; }
+// a standalone application runs the network whatever an earlier solve with the
+// operator's cached batch left behind
+__global__ void k_prec_setup(KState* st) {
+    st[0].active = 1;
+    st[0].fallback = 0;
+}
 __global__ void k_lift_setup(KState* st) {
     st[0].active = 1;
     st[0].fallback = 0;
