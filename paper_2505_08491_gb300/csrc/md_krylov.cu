@@ -1872,13 +1872,13 @@ extern "C" md_status md_precondition(const md_op* op, const md_cnn* cnn, const f
 // Inner FGMRES buffers of a network-preconditioned batch, allocated once at
 // the largest step count (their addresses are baked into captured graphs).
 static md_status ensure_inner(md_batch* B) {
-    if (B->iV) return MD_OK;
     if (B->solver != MD_SOLVER_FGMRES_CNN || !B->cw) {
         md_set_error("inner FGMRES steps need a network-preconditioned batch");
         return MD_ERR_ARG;
     }
-    MD_TRY(dev_alloc(&B->allocs, &B->iV, (size_t)(MD_INNER_MAX + 1) * B->total));
-    MD_TRY(dev_alloc(&B->allocs, &B->iZ, (size_t)MD_INNER_MAX * B->total));
+    // each buffer on its own, so that a failed allocation is retried by the next call
+    if (!B->iV) MD_TRY(dev_alloc(&B->allocs, &B->iV, (size_t)(MD_INNER_MAX + 1) * B->total));
+    if (!B->iZ) MD_TRY(dev_alloc(&B->allocs, &B->iZ, (size_t)MD_INNER_MAX * B->total));
     return MD_OK;
 }
 
