@@ -248,7 +248,9 @@ md_status md_lift(const md_op* op, const float* r, float* z1, float* l, md_strea
  * b: device FP64 (n); x: device FP64 (n), in: initial guess, out: solution.
  * maxit bounds the total iterations.  *iters and *relres (host) receive the
  * iterations done and the final true relative residual.  Synchronises s.
- * Returns MD_NOT_CONVERGED when maxit is reached above tol. */
+ * Returns MD_NOT_CONVERGED when maxit is reached above tol.  b = 0: the
+ * relative residual is taken as 0 and the solve returns at once with x as
+ * given (the zero solution when started from x = 0). */
 md_status md_solve(const md_op* op, const md_cnn* cnn, const double* b, double* x,
                    double tol, int restart, int maxit, int* iters, double* relres, md_stream s);
 
