@@ -14,7 +14,10 @@
  * GMRES (Section 4) right-preconditioned by the block upper-triangular
  * preconditioner of eq. (twosteps): an exact 1D solve followed by a
  * convolutional network standing in for the inverse of the 3D block
- * C = K00 + beta M00 (eq. (decoupled_3d_problem), (matrixC)).
+ * C = K00 + beta M00 (eq. (decoupled_3d_problem), (matrixC)).  Variants
+ * declared below: the block lower-triangular order, Jacobi pre- and
+ * post-smoothing around the network (Section 5), and the 3D solve as inner
+ * FGMRES steps with the network as their preconditioner (Section 6).
  *
  * Conventions shared by every entry point
  *   - Vectors are DEVICE pointers owned by the caller, laid out as
