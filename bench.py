@@ -154,6 +154,23 @@ def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smo
     return time.perf_counter() - t0, it, rel, rel <= TOL
 
 
+def oracle_other_solvers(inst, direct: bool):
+    """The oracle's other solvers on one instance, for context beside the
+    network-preconditioned one: FP64 Jacobi-CG to the same tolerance and,
+    when asked, the sparse direct solve (seconds per solve)."""
+    from oracle import fem, solvers
+    p = fem.Problem(inst["N"], inst["graph"], inst["beta"])
+    b = p.rhs(p.source(inst["f_seed"]), inst["g"])
+    t0 = time.perf_counter()
+    _, it, rel = solvers.jacobi_cg(p.A, b, TOL)
+    out = {"jacobi_cg": {"s_per_solve": time.perf_counter() - t0, "iterations": it, "relres": rel}}
+    if direct:
+        t0 = time.perf_counter()
+        solvers.direct_solve(p.A, b)
+        out["sparse_direct"] = {"s_per_solve": time.perf_counter() - t0}
+    return out
+
+
 def by_group(keys, its):
     """Mean iterations per distinct key (beta or N), keys rounded for beta log-uniform draws."""
     groups = {}
@@ -200,7 +217,8 @@ def reference_arm(args):
             "config": bench_config(args, sum((w["N"] + 1) ** 3 for w in insts)),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": f"one instance of the workload per step ({args.steps} full FP64 oracle "
-                                       f"solves, iterations {its}; numpy BLAS threads: default)"},
+                                       f"solves, iterations {its}; numpy BLAS threads: default)",
+                             "other_oracle_solvers": oracle_other_solvers(insts[0], direct=True)},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -375,7 +393,8 @@ def main():
         per_it = t / max(it, 1)
         cpu = {"value": 1.0 / (per_it * its0), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"instance 0, FP64 oracle FGMRES(30)+network: {it} iterations timed ({t:.1f} s), "
-                         f"scaled to the {its0} iterations its solve takes"}
+                         f"scaled to the {its0} iterations its solve takes",
+               "other_oracle_solvers": oracle_other_solvers(insts[0], direct=False)}
 
     line = {"metric": METRIC, "value": value,
             "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,

@@ -29,6 +29,9 @@ def test_reference_arm_prints_one_contract_line():
     assert d["warmup"] >= 3 and d["steps"] == 1 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    other = d["cpu_baseline"]["other_oracle_solvers"]
+    assert other["jacobi_cg"]["relres"] <= 1e-8 and other["jacobi_cg"]["iterations"] > 0
+    assert other["sparse_direct"]["s_per_solve"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("tree15_32")
     assert d["config"]["jacobi_smoothing"]["sweeps_before_and_after"] == 0 and d["config"]["inner_fgmres_steps"] == 0
