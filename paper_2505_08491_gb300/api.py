@@ -338,7 +338,7 @@ class Batch:
             raise ValueError("order must be 'upper' or 'lower'")
         L.check(L.load().md_batch_set_prec_order(self._h, 1 if order == "lower" else 0), "md_batch_set_prec_order")
 
-    def set_smoothing(self, nu: int, omega: float = None):
+    def set_smoothing(self, nu: int, omega: float | None = None):
         """nu damped Jacobi sweeps before and after the network (0: none);
         omega defaults to SMOOTH_OMEGA."""
         om = SMOOTH_OMEGA if omega is None else float(omega)
