@@ -159,18 +159,27 @@ WORKLOADS = {
     "batch256_mixed": dict(N=(32, 48, 64), beta="loguniform", kind="tree", depth=(3, 8), elems=8,
                            radius=(0.01, 0.03), f="normal", g=1.0, tol=1e-8, restart=30,
                            seed=3_000_000, count=256),
+    # the paper's own setting (Section 2 eq. (problem), Section 5.1): 21^3 grid nodes, natural
+    # conditions on the cube faces, k_Omega = sigma_Omega = 1e-3, eps = 1e-3 (coupling 2 pi eps,
+    # vessel radius eps), u_Lambda = 1 at the tree's root, no source; trees of 1-127 segments;
+    # FGMRES(20) to 1e-15 (Section 6)
+    "paper_21": dict(N=20, beta=2.0 * np.pi * 1e-3, kind="tree", depth=(1, 7), elems=8, radius=(1e-3, 1e-3),
+                     f="zero", g=0.0, tol=1e-15, restart=20, seed=5_000_000,
+                     physics=dict(k_omega=1e-3, sigma_omega=1e-3, dirichlet=False, dirichlet_1d=(0,), u_d=1.0)),
 }
 
 
 def workload_instance(name: str, i: int = 0) -> dict:
     """Problem instance i of a named workload: graph, N, beta, f-recipe.
 
-    Returns dict(N, beta, graph, f_seed or None, g, instance).
+    Returns dict(N, beta, graph, f_seed or None, g, instance, physics); physics
+    holds the coefficients and boundary conditions of workloads that differ
+    from the defaults (keyword arguments of the oracle's Problem), else {}.
     """
     w = WORKLOADS[name]
     if w["kind"] == "segment":
         g = straight_segment(w["p0"], w["p1"], w["elems"], w["radius"])
-        return dict(N=w["N"], beta=w["beta"], graph=g, f_seed=None, g=w["g"], instance=i)
+        return dict(N=w["N"], beta=w["beta"], graph=g, f_seed=None, g=w["g"], instance=i, physics={})
     seed = w["seed"] + i
     rng = rng_for(seed, 1)  # parameter stream, separate from the graph stream
     dlo, dhi = w["depth"]
@@ -185,4 +194,5 @@ def workload_instance(name: str, i: int = 0) -> dict:
         beta = float(w["beta"])
     graph = random_tree(seed, 0, depth, elems=w["elems"], radius_range=w["radius"])
     f_seed = seed if w["f"] == "normal" else None
-    return dict(N=N, beta=beta, graph=graph, f_seed=f_seed, g=w["g"], instance=i)
+    return dict(N=N, beta=beta, graph=graph, f_seed=f_seed, g=w["g"], instance=i,
+                physics=dict(w.get("physics", {})))

@@ -230,10 +230,19 @@ class Problem:
         M01    -Pi^T W Psi (so the 0-1 block of A is beta * M01)
         M00    Pi^T W Pi (so C = K00 + beta * M00)
         Pi, Psi, w, K1, kappa, Mass (unmasked Q1 mass), bd, dist, alpha
+        d1     1D Dirichlet mask (n1), u_D its value
+
+    dirichlet=False gives the natural (Neumann) condition on the cube faces of
+    eq. (problem).  dirichlet_1d lists graph nodes carrying u_Lambda = u_D
+    (the subset dLambda_D of eq. (problem)); those unknowns are eliminated
+    symmetrically: their rows and columns of B11 become the identity, their
+    columns of M01 zero, and their known value moves to the right-hand side
+    (`rhs`).
     """
 
     def __init__(self, N: int, graph: dict, beta: float, *, k_omega: float = 1.0,
-                 sigma_omega: float = 0.0, k_lambda: float = 1.0, dirichlet: bool = True):
+                 sigma_omega: float = 0.0, k_lambda: float = 1.0, dirichlet: bool = True,
+                 dirichlet_1d=None, u_d: float = 1.0):
         self.N = N
         self.h = 1.0 / N
         self.n3 = (N + 1) ** 3
@@ -266,13 +275,26 @@ class Problem:
         self.kappa = k_lambda * math.pi * float(graph["radius"]) ** 2
         M00 = (self.Pi.T @ W @ self.Pi).tocsr()
         self.M00 = M00
-        self.M01 = (-(self.Pi.T @ W @ self.Psi)).tocsr()
+        M01_full = (-(self.Pi.T @ W @ self.Psi)).tocsr()
         M11 = (self.Psi.T @ W @ self.Psi).tocsr()
+        # 1D Dirichlet nodes: eliminated (identity rows/columns), their value
+        # enters the right-hand side through the columns kept here
+        self.d1 = np.zeros(n1, dtype=bool)
+        if dirichlet_1d is not None:
+            self.d1[np.asarray(dirichlet_1d, dtype=np.int64)] = True
+        self.u_d = float(u_d)
+        keep1 = sp.diags((~self.d1).astype(np.float64))
+        self.M01 = (M01_full @ keep1).tocsr()
         interior = sp.diags((~self.bd).astype(np.float64))
         K00m = (interior @ K00 @ interior + sp.diags(self.bd.astype(np.float64))).tocsr()
         self.K00 = K00m
         self.C = (K00m + self.beta * M00).tocsr()
-        self.B11 = (self.kappa * self.K1 + self.beta * M11).tocsr()
+        B11_full = (self.kappa * self.K1 + self.beta * M11).tocsr()
+        self.B11 = (keep1 @ B11_full @ keep1 + sp.diags(self.d1.astype(np.float64))).tocsr()
+        # what the fixed values contribute: b0 -= beta M01[:, D] u_D, b1[F] -= B11[F, D] u_D
+        uD = self.u_d * self.d1.astype(np.float64)
+        self._lift0 = -self.beta * (M01_full @ uD)
+        self._lift1 = -(keep1 @ (B11_full @ uD)) + uD
         self.A = sp.bmat([[self.C, self.beta * self.M01],
                           [self.beta * self.M01.T, self.B11]], format="csr")
         self.n = self.n3 + self.n1
@@ -285,11 +307,16 @@ class Problem:
         np.add.at(self.load1, eb, L / 2)
 
     def rhs(self, f: np.ndarray | None, g: float) -> np.ndarray:
-        """b = [M_Omega f ; g * int psi_i ds] with b0 = 0 on Dirichlet nodes.
-        f: nodal source on the grid (None -> 0)."""
+        """b = [M_Omega f ; g * int psi_i ds] with b0 = 0 on Dirichlet nodes,
+        plus, with 1D Dirichlet nodes, the lifting of their value u_D
+        (b1 = u_D on those nodes).  f: nodal source on the grid (None -> 0)."""
         b0 = np.zeros(self.n3) if f is None else self.Mass @ f
+        b1 = g * self.load1
+        b1[self.d1] = 0.0
+        b0 = b0 + self._lift0
+        b1 = b1 + self._lift1
         b0[self.bd] = 0.0
-        return np.concatenate([b0, g * self.load1])
+        return np.concatenate([b0, b1])
 
     def source(self, seed: int | None) -> np.ndarray | None:
         """Nodal f ~ N(0,1) on interior nodes, 0 on the boundary."""

@@ -52,3 +52,24 @@ def test_workload_instances():
     assert s["graph"]["elems"] == 32 and s["f_seed"] is None
     v1 = mdgen.normal_vector(5, 1, 100)
     assert np.array_equal(v1, mdgen.normal_vector(5, 1, 100))
+
+
+def test_paper_workload_recipe():
+    """The paper's setting (Section 2 eq. (problem), Section 5.1): 21^3 grid
+    nodes, k = sigma = 1e-3, coupling 2 pi eps with eps = 1e-3 also the vessel
+    radius, natural conditions on the cube, u_Lambda = 1 at the root; the
+    oracle solves it and holds the root at exactly 1."""
+    import numpy as np
+    from oracle import fem, solvers
+    w = mdgen.workload_instance("paper_21", 2)
+    assert w["N"] == 20 and abs(w["beta"] - 2 * np.pi * 1e-3) < 1e-15
+    assert w["graph"]["radius"] == 1e-3 and w["f_seed"] is None and w["g"] == 0.0
+    ph = w["physics"]
+    assert ph["dirichlet"] is False and tuple(ph["dirichlet_1d"]) == (0,)
+    assert ph["k_omega"] == ph["sigma_omega"] == 1e-3
+    assert mdgen.workload_instance("tree15_32", 0)["physics"] == {}
+    p = fem.Problem(w["N"], w["graph"], w["beta"], **ph)
+    b = p.rhs(None, w["g"])
+    x, it, rel = solvers.fgmres(p.A, b, solvers.BlockPreconditioner(p, mode="exact"), 1e-13, restart=20)
+    assert rel <= 1e-13
+    assert x[p.n3 + 0] == 1.0 or abs(x[p.n3 + 0] - 1.0) < 1e-12

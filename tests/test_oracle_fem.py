@@ -6,6 +6,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 import mdgen
@@ -254,3 +255,54 @@ def test_distance_field_against_sampling():
     p = fem.distance_field(16, seg_graph())
     assert p[fem.node_index(8, 8, 8, 16)] == 0.0
     assert p[fem.node_index(8, 10, 8, 16)] == pytest.approx(2 / 16, abs=1e-15)
+
+
+def _tree_problem(**kw):
+    g = mdgen.random_tree(303, 0, depth=3, elems=3)
+    return fem.Problem(6, g, kw.pop("beta", 1.0), **kw)
+
+
+def test_neumann_cube_with_1d_dirichlet_reproduces_constants():
+    """Natural conditions on the cube faces, sigma = 0, no source, u_Lambda = 1
+    on one graph end (eq. (problem)): the stiffness, the 1D stiffness and the
+    coupling all annihilate constants (Pi and Psi are partitions of unity when
+    no boundary weight is dropped), so the discrete solution is exactly 1 on
+    every grid and graph node."""
+    p = _tree_problem(beta=3.0, dirichlet=False, dirichlet_1d=[0], u_d=1.0)
+    assert not p.bd.any() and p.d1.sum() == 1
+    assert np.allclose(np.asarray(p.Pi.sum(axis=1)).ravel(), 1.0, atol=1e-14)
+    b = p.rhs(None, 0.0)
+    x = sp.linalg.spsolve(p.A.tocsc(), b)
+    assert np.abs(x - 1.0).max() < 1e-10
+    assert np.abs(p.A @ np.ones(p.n) - b).max() < 1e-12
+
+
+def test_1d_dirichlet_without_coupling():
+    """beta = 0: the graph problem alone with u = u_D on one end, natural
+    conditions elsewhere and no load is u = u_D; the cube problem (sigma > 0,
+    no source) is u = 0."""
+    p = _tree_problem(beta=0.0, sigma_omega=0.5, dirichlet=False, dirichlet_1d=[0], u_d=2.5)
+    x = sp.linalg.spsolve(p.A.tocsc(), p.rhs(None, 0.0))
+    assert np.abs(x[p.n3:] - 2.5).max() < 1e-10
+    assert np.abs(x[:p.n3]).max() < 1e-12
+
+
+def test_neumann_1d_dirichlet_system_is_spd_and_matches_elimination():
+    """The eliminated system is symmetric positive definite, and its solution
+    restricted to the free unknowns equals the solution of the full system
+    with the Dirichlet rows replaced by u = u_D (unsymmetric elimination)."""
+    p = _tree_problem(beta=2.0, k_omega=1e-3, sigma_omega=1e-3, dirichlet=False, dirichlet_1d=[0, 2], u_d=1.0)
+    A = p.A.toarray()
+    assert np.abs(A - A.T).max() < 1e-14
+    assert np.linalg.eigvalsh(A).min() > 0
+    q = _tree_problem(beta=2.0, k_omega=1e-3, sigma_omega=1e-3, dirichlet=False)
+    Af = q.A.toarray()
+    rows = q.n3 + np.flatnonzero(p.d1)
+    bf = q.rhs(None, 0.0)
+    Af[rows, :] = 0.0
+    Af[rows, rows] = 1.0
+    bf[rows] = 1.0
+    bf[q.n3:][~p.d1] = 0.0
+    xf = np.linalg.solve(Af, bf)
+    x = np.linalg.solve(A, p.rhs(None, 0.0))
+    assert np.abs(x - xf).max() < 1e-10 * np.abs(xf).max()
