@@ -154,6 +154,24 @@ def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smo
     return time.perf_counter() - t0, it, rel, rel <= TOL
 
 
+def oracle_threads() -> int:
+    """Threads the oracle runs on: its network and Krylov arithmetic are numpy
+    and scipy calls, whose BLAS uses its thread pool (the core count unless an
+    environment variable caps it)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [int(i.get("num_threads", 0)) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and max(n) > 0:
+            return max(n)
+    except ImportError:
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        v = os.environ.get(var, "")
+        if v.isdigit() and int(v) > 0:
+            return int(v)
+    return os.cpu_count() or 1
+
+
 def oracle_other_solvers(inst, direct: bool):
     """The oracle's other solvers on one instance, for context beside the
     network-preconditioned one: FP64 Jacobi-CG to the same tolerance and,
@@ -209,7 +227,7 @@ def reference_arm(args):
         its.append(it)
     total = sum(ts)
     value = args.steps / total
-    cores = os.cpu_count()
+    cores = oracle_threads()
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -217,7 +235,7 @@ def reference_arm(args):
             "config": bench_config(args, sum((w["N"] + 1) ** 3 for w in insts)),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": f"one instance of the workload per step ({args.steps} full FP64 oracle "
-                                       f"solves, iterations {its}; numpy BLAS threads: default)",
+                                       f"solves, iterations {its}; BLAS threads: {cores})",
                              "other_oracle_solvers": oracle_other_solvers(insts[0], direct=True)},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -391,7 +409,7 @@ def main():
         t, it, rel, done = oracle_solve_seconds(insts[0], params, max_seconds=20.0, order=args.prec_order,
                                                 smooth=(args.smooth, args.omega), inner=args.inner)
         per_it = t / max(it, 1)
-        cpu = {"value": 1.0 / (per_it * its0), "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": 1.0 / (per_it * its0), "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
                "sample": f"instance 0, FP64 oracle FGMRES(30)+network: {it} iterations timed ({t:.1f} s), "
                          f"scaled to the {its0} iterations its solve takes",
                "other_oracle_solvers": oracle_other_solvers(insts[0], direct=False)}
