@@ -306,3 +306,30 @@ def test_neumann_1d_dirichlet_system_is_spd_and_matches_elimination():
     xf = np.linalg.solve(Af, bf)
     x = np.linalg.solve(A, p.rhs(None, 0.0))
     assert np.abs(x - xf).max() < 1e-10 * np.abs(xf).max()
+
+
+@pytest.mark.parametrize("N,k_omega,sigma", [(4, 1.0, 0.0), (7, 2.5, 0.0), (10, 1.0, 3.0)])
+def test_alpha_without_coupling_is_the_stencil_centre(N, k_omega, sigma):
+    """alpha (Section 5.1: ||diag C|| / sqrt(N_h) over the unknown grid nodes)
+    at beta = 0: every interior diagonal of C is the closed-form stencil centre
+    k h 8/3 + sigma h^3 8/27, so alpha equals it whatever the graph."""
+    gold = json.load(open(os.path.join(GOLD, "q1_stencil.json")))
+    g = mdgen.random_tree(31, 0, depth=2, elems=3)
+    p = fem.Problem(N, g, beta=0.0, k_omega=k_omega, sigma_omega=sigma)
+    h = 1.0 / N
+    centre = k_omega * h * gold["stiffness_over_h"]["centre"] + sigma * h ** 3 * gold["mass_over_h3"]["centre"]
+    assert p.alpha == pytest.approx(centre, rel=1e-13)
+
+
+def test_alpha_counts_interior_nodes_only():
+    """With coupling, alpha^2 is the mean of c_ii^2 over the (N-1)^3 interior
+    nodes: the Dirichlet rows (identity) do not enter.  Checked on N = 2,
+    whose single interior node makes alpha its own diagonal, read off the
+    operator by probing with the unit vector."""
+    g = mdgen.straight_segment((0.3, 0.5, 0.5), (0.7, 0.5, 0.5), 4, 0.1)
+    p = fem.Problem(2, g, beta=7.0)
+    e = np.zeros(p.n)
+    e[fem.node_index(1, 1, 1, 2)] = 1.0
+    c = float(e @ (p.A @ e))
+    assert c > 8.0 / 3.0 * 0.5  # the coupling adds to the stencil centre
+    assert p.alpha == pytest.approx(c, rel=1e-14)

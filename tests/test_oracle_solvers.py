@@ -340,3 +340,30 @@ def test_one_inner_step_is_network_with_minimal_residual_scale(tree8, order):
     v[:p.n3][p.bd] = 0.0
     zq = Q3(v)
     assert np.allclose(Q3(2.5 * v), 2.5 * zq, rtol=1e-9, atol=1e-12 * np.abs(zq).max())
+
+
+def test_training_loss_is_the_coupled_residual_of_the_upper_preconditioner(tree8):
+    """The training loss (Section 3.2 eq. (risk), the squared norm of Section
+    5.1) against the coupled system itself: for the block upper-triangular
+    preconditioner z = Q(r) (z1 = B11^{-1} r1, l = -beta M01 z1, z0 the
+    network on b0 = r0 + l), the 3D rows of A z - r are
+    C z0 + beta M01 z1 - r0 = C z0 - b0.  So the loss equals
+    ||(A Q(r) - r)_0||^2 / ||b0||^2 over the interior grid rows, computed here
+    from the full matrix A and the preconditioner, with no reference to the
+    loss's own b0, s or alpha handling."""
+    p = tree8
+    rng = np.random.default_rng(42)
+    params = cnn.init_params(5)
+    r = rng.standard_normal(p.n)
+    r[:p.n3][p.bd] = 0.0
+    Q = solvers.BlockPreconditioner(p, mode="cnn", params=params, bf16=False, order="upper")
+    z = Q(r)
+    e = (p.A @ z - r)[:p.n3][~p.bd]
+    z1 = z[p.n3:]
+    b0 = r[:p.n3] - p.beta * (p.M01 @ z1)
+    want = float(e @ e) / float(b0 @ b0)
+    l = Q.lift(z1)
+    got = solvers.training_loss(p, r[:p.n3], l, params)
+    assert got == pytest.approx(want, rel=1e-10)
+    # the lifted part matters at this coupling: the loss of r0 alone differs
+    assert abs(solvers.training_loss(p, r[:p.n3], 0.0 * l, params) - want) > 1e-3 * want
