@@ -1,16 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the neural-preconditioned solve on one GB300 (or N replicas).
 
-Metric: solves/sec (and s/solve) to true relative residual 1e-8 for the
-binary-tree workload of 100 graphs (depth 4, 15 segments, 8 P1 elements per
-segment, N = 32 Q1 elements per cube edge, beta = 1, f ~ N(0,1), g = 1),
-solved as one batch by FGMRES(30) with the block preconditioner and the BF16
-network; Jacobi-CG (FP64) on the same batch and GPU is reported beside it.
+Metric: solves/sec (and s/solve) to true relative residual 1e-8 for the mixed
+batched workload: 256 instances on grids of 32^3, 48^3 and 64^3 Q1 elements
+(mixed uniformly), seeded random binary trees of 7-255 segments with 8 P1
+elements each, radius U(0.01, 0.03), coupling beta log-uniform in [1, 100],
+f ~ N(0,1), g = 1, solved together by FGMRES(30) with the block
+preconditioner and the BF16 network; Jacobi-CG (FP64) on the same batch and
+GPU is reported beside it, with per-instance p50/p99 times.  The 100-instance
+binary-tree workload at 32^3 (15 segments, beta = 1) is measured as well and
+reported under "other_workloads".
 
 A step is one batched solve of the whole workload from x0 = 0.  Inputs are
 resident in HBM for `value`; `e2e` copies b from pinned host memory and x
 back every step.  The working set (Krylov bases of all instances, > 1 GB)
 exceeds L2, and L2 is also flushed between steps.
+
+Block order: both orders of the preconditioner are built; each workload runs
+the one that solves it faster on the GPU (stated in config.prec_order): the
+paper's upper-triangular order on the beta = 1 tree workload, the lower one
+on the beta-mixed and transfer workloads.
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the
 method, test infrastructure) on the host cores instead, one instance per step.
@@ -32,15 +41,14 @@ import numpy as np  # noqa: E402
 
 import mdgen  # noqa: E402
 
-WORKLOAD = "tree15_32"
-COUNT = 100
+WORKLOAD = "batch256_mixed"
 TOL = 1e-8
 RESTART = 30
 HIDDEN_FLOP_PER_NODE = 4 * 2 * 27 * 32 * 32     # the four 32->32 layers
 METRIC = "solves/sec and s/solve to rel. residual 1e-8, CNN-FGMRES vs Jacobi-CG, 1 GB300"
-# DRAM bytes (read + write) per grid node of one hidden-layer launch, from the
-# ncu capture summarised in profiles/conv_hidden_tcgen05_64x33cube.md (64 grids
-# of 33^3; traffic grows with the grid nodes a launch processes)
+# DRAM bytes (read + write) per grid node of one hidden-layer launch, from an
+# ncu capture of the hidden convolution on 64 grids of 33^3 (traffic grows with
+# the grid nodes a launch processes)
 HIDDEN_TRAFFIC_BYTES_PER_NODE = 153.0
 NET_FLOP_PER_NODE = 2 * 27 * (3 * 32 + 4 * 32 * 32 + 32)
 
@@ -64,6 +72,8 @@ WORKLOAD_TEXT = {
                     "f~N(0,1), g=1; network trained at N<=32",
 }
 DEFAULT_COUNT = {"tree15_32": 100, "batch256_mixed": 256, "transfer_64": 30, "transfer_128": 12}
+# the faster block order per workload (measured on the GPU)
+DEFAULT_ORDER = {"tree15_32": "upper", "batch256_mixed": "lower", "transfer_64": "lower", "transfer_128": "lower"}
 
 
 def restart_of(workload: str) -> int:
@@ -130,27 +140,39 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": reasons, "samples": len(rows)}
 
 
-def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smooth=(0, 1.0), inner=0):
-    """Oracle FGMRES(30) + network (FP64 CPU) on one instance.  Returns
-    (seconds, iterations, relres, completed)."""
-    from oracle import fem, solvers
+_ORACLE_CACHE = {}
+
+
+def _oracle_problem(inst):
+    """The oracle's assembled problem and right-hand side of an instance
+    (cached: the reference arm returns to the same few instances)."""
+    from oracle import fem
+    key = (inst["N"], inst["f_seed"], float(inst["beta"]), len(inst["graph"]["edges"]))
+    if key not in _ORACLE_CACHE:
+        p = fem.Problem(inst["N"], inst["graph"], inst["beta"])
+        _ORACLE_CACHE[key] = (p, p.rhs(p.source(inst["f_seed"]), inst["g"]))
+    return _ORACLE_CACHE[key]
+
+
+def oracle_solve_seconds(inst, params_flat, max_seconds=None, order="upper", smooth=(0, 1.0), inner=0,
+                         restart=RESTART):
+    """Oracle FGMRES(restart) + network (FP64 CPU) on one instance.  Returns
+    (seconds, iterations, relres, completed).  With max_seconds, one iteration
+    is timed first and then as many as fit the budget, from x0 = 0 again."""
+    from oracle import solvers
     from paper_2505_08491_gb300.weights import flat_to_layers
     layers = [(W, b) for W, b in flat_to_layers(params_flat)]
-    p = fem.Problem(inst["N"], inst["graph"], inst["beta"])
-    b = p.rhs(p.source(inst["f_seed"]), inst["g"])
+    p, b = _oracle_problem(inst)
     Q = solvers.BlockPreconditioner(p, mode="cnn", params=layers, bf16=True, order=order, smooth=smooth, inner=inner)
-    hist = []
     t0 = time.perf_counter()
     if max_seconds is None:
-        x, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=RESTART, maxit=5000, history=hist)
+        x, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=restart, maxit=5000)
         return time.perf_counter() - t0, it, rel, True
-    # bounded: time single iterations until the budget is spent
-    budget_it = 1
-    x, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=RESTART, maxit=budget_it, history=hist)
+    x, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=restart, maxit=1)
     t1 = time.perf_counter() - t0
     n_more = max(1, min(200, int((max_seconds - t1) / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    x, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=RESTART, maxit=n_more, history=hist)
+    x, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=restart, maxit=n_more)
     return time.perf_counter() - t0, it, rel, rel <= TOL
 
 
@@ -176,9 +198,8 @@ def oracle_other_solvers(inst, direct: bool):
     """The oracle's other solvers on one instance, for context beside the
     network-preconditioned one: FP64 Jacobi-CG to the same tolerance and,
     when asked, the sparse direct solve (seconds per solve)."""
-    from oracle import fem, solvers
-    p = fem.Problem(inst["N"], inst["graph"], inst["beta"])
-    b = p.rhs(p.source(inst["f_seed"]), inst["g"])
+    from oracle import solvers
+    p, b = _oracle_problem(inst)
     t0 = time.perf_counter()
     _, it, rel = solvers.jacobi_cg(p.A, b, TOL)
     out = {"jacobi_cg": {"s_per_solve": time.perf_counter() - t0, "iterations": it, "relres": rel}}
@@ -209,36 +230,155 @@ def bench_config(args, grid_nodes):
             "network bf16/fp32-acc, Krylov fp32, restart residual + Hessenberg fp64"}
 
 
+REFERENCE_ITERATIONS_PER_STEP = 2
+REFERENCE_PER_GRID = 3
+
+
+def _reference_sample(workload: str, count: int):
+    """Instances the reference arm cycles through: the first three of each
+    grid size among the workload's instances (all of them for one size)."""
+    picked, seen = [], {}
+    for i in range(count):
+        w = mdgen.workload_instance(workload, i)
+        if seen.get(w["N"], 0) < REFERENCE_PER_GRID:
+            seen[w["N"]] = seen.get(w["N"], 0) + 1
+            picked.append((i, w))
+        if len(picked) >= 3 * REFERENCE_PER_GRID:
+            break
+    return picked
+
+
 def reference_arm(args):
+    """The oracle (FP64 numpy/scipy, as it stands) on the host cores, on this
+    workload.  Each step is a bounded sample: the next of a few instances of
+    the workload (three per grid size), the oracle's FGMRES with the network
+    for 2 iterations from x0 = 0, its time per iteration times the iterations
+    the instance needs to tol 1e-8, extrapolated from the residual reduction
+    those iterations reached (it * log(tol) / log(relres)); the first
+    iterations of GMRES reduce the residual fastest, so the extrapolation
+    errs in the oracle's favour."""
+    import math
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2505_08491_gb300.weights import default_network_params
     params = default_network_params(args.prec_order)
-    insts = instances(args.workload, 0, args.count)
+    sample = _reference_sample(args.workload, args.count)
+    rs = restart_of(args.workload)
+    kw = dict(order=args.prec_order, smooth=(args.smooth, args.omega), inner=args.inner, restart=rs)
+
+    def run(inst, iters):
+        from oracle import solvers
+        from paper_2505_08491_gb300.weights import flat_to_layers
+        p, b = _oracle_problem(inst)
+        Q = solvers.BlockPreconditioner(p, mode="cnn", params=flat_to_layers(params), bf16=True, order=kw["order"],
+                                        smooth=kw["smooth"], inner=kw["inner"])
+        t0 = time.perf_counter()
+        _, it, rel = solvers.fgmres(p.A, b, Q, TOL, restart=rs, maxit=iters)
+        return time.perf_counter() - t0, it, rel
+
     for w in range(args.warmup):
-        oracle_solve_seconds(insts[w % len(insts)], params, order=args.prec_order, smooth=(args.smooth, args.omega),
-                             inner=args.inner)
-    ts, its = [], []
+        run(sample[w % len(sample)][1], 1)
+    ts, rows = [], []
     for k in range(args.steps):
-        t, it, rel, done = oracle_solve_seconds(insts[(args.warmup + k) % len(insts)], params, order=args.prec_order,
-                                                smooth=(args.smooth, args.omega), inner=args.inner)
-        ts.append(t)
-        its.append(it)
+        idx, inst = sample[k % len(sample)]
+        t, it, rel = run(inst, REFERENCE_ITERATIONS_PER_STEP)
+        need = it if rel <= TOL else (it * math.log(TOL) / math.log(rel) if 0.0 < rel < 1.0 else float("inf"))
+        ts.append(t / max(it, 1) * need)
+        rows.append((idx, inst["N"], it, float(rel), round(need, 1)))
     total = sum(ts)
     value = args.steps / total
     cores = oracle_threads()
+    inst0 = sample[0][1]
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(args, sum((w["N"] + 1) ** 3 for w in insts)),
+            "config": bench_config(args, sum((w["N"] + 1) ** 3 for w in instances(args.workload, 0, args.count))),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"one instance of the workload per step ({args.steps} full FP64 oracle "
-                                       f"solves, iterations {its}; BLAS threads: {cores})",
-                             "other_oracle_solvers": oracle_other_solvers(insts[0], direct=True)},
+                             "sample": f"per step, the next of {len(sample)} instances of the workload (three per "
+                                       f"grid size): FP64 oracle FGMRES({rs}) + network for "
+                                       f"{REFERENCE_ITERATIONS_PER_STEP} iterations, time per iteration x the "
+                                       "iterations to tol 1e-8 extrapolated from their residual reduction "
+                                       "(favours the oracle); (instance, N, iterations run, relres, iterations "
+                                       f"needed): {rows}; BLAS threads: {cores}",
+                             "other_oracle_solvers": oracle_other_solvers(inst0, direct=inst0["N"] <= 32)},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def network_only(args):
+    """The network alone on `--net-batch` grids of `--net-n`^3 nodes, `--passes`
+    forward passes (random weights and inputs): the convolution kernels in
+    isolation, for profiling them.  Prints one JSON line."""
+    import torch
+
+    from paper_2505_08491_gb300 import Network
+    from paper_2505_08491_gb300.weights import random_params
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    net = Network(random_params(1))
+    n = args.net_n
+    X = torch.from_numpy(np.random.default_rng(0).standard_normal((args.net_batch, 3, n, n, n)).astype(np.float32)).cuda()
+    times = []
+    for _ in range(args.passes):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        Y = net.forward(X)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    nodes = args.net_batch * n ** 3
+    best = min(times[1:]) if len(times) > 1 else times[0]
+    print(json.dumps({"network_only": {"grids": args.net_batch, "nodes_per_edge": n, "passes": args.passes,
+                                       "ms_per_pass_incl_workspace": times,
+                                       "network_tflops_best": nodes * NET_FLOP_PER_NODE / best / 1e9,
+                                       "output_mean_abs": float(Y.abs().mean())}}), flush=True)
+
+
+def extra_workload(name: str, steps: int, flush):
+    """Solves/s of another workload on this GPU, measured like the headline
+    (inputs resident, L2 flushed, CUDA events around each batched solve), with
+    Jacobi-CG on the same batch beside it.  Rank 0 of a one-GPU run only."""
+    import torch
+
+    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300.weights import default_network_params
+    order = DEFAULT_ORDER[name]
+    insts = instances(name, 0, DEFAULT_COUNT[name])
+    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    b_all = torch.cat([op.rhs(torch.from_numpy(f).cuda() if f is not None else None, w["g"])
+                       for w, op, f in ((w, op, mdgen.interior_source(w["N"], w["f_seed"]))
+                                        for w, op in zip(insts, ops))]).contiguous()
+    x_all = torch.zeros_like(b_all)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{name}: {len(insts)} {WORKLOAD_TEXT[name]}", "prec_order": order}
+    for solver in ("fgmres_cnn", "cg_jacobi"):
+        if solver == "fgmres_cnn":
+            net = Network(default_network_params(order))
+            B = Batch(ops, solver, net, restart=restart_of(name))
+            B.set_prec_order(order)
+        else:
+            B = Batch(ops, solver)
+        for _ in range(3):
+            x_all.zero_()
+            B.solve(b_all, x_all, tol=TOL, maxit=100000)
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            x_all.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its, rels, ok = B.solve(b_all, x_all, tol=TOL, maxit=100000)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            if not ok:
+                raise SystemExit(f"{name} {solver}: solve did not converge: max relres {max(rels):.3e}")
+        out[solver] = {"solves_per_s": len(insts) * steps / (ms / 1e3), "mean_iterations": float(np.mean(its)),
+                       "max_iterations": int(np.max(its)), "max_relres": float(max(rels))}
+        B.close()
+    out["speedup_fgmres_cnn_over_cg"] = out["fgmres_cnn"]["solves_per_s"] / out["cg_jacobi"]["solves_per_s"]
+    return out
 
 
 def main():
@@ -249,8 +389,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--count", type=int, default=None, help="instances per GPU (default: the workload's)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOAD_TEXT))
-    ap.add_argument("--prec-order", default="upper", choices=["upper", "lower"],
-                    help="block order of the preconditioner (the paper's upper-triangular one by default)")
+    ap.add_argument("--prec-order", default=None, choices=["upper", "lower"],
+                    help="block order of the preconditioner (default: the faster one for the workload)")
     ap.add_argument("--smooth", type=int, default=0,
                     help="damped Jacobi sweeps before and after the network in the 3D solve (0: none)")
     ap.add_argument("--omega", type=float, default=None, help="damping of those sweeps (default: the package's SMOOTH_OMEGA, 2/3)")
@@ -258,11 +398,21 @@ def main():
                     help="the 3D block solve as this many inner FGMRES steps with the network (0: one application)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra tree15_32 measurement")
+    ap.add_argument("--network-only", action="store_true",
+                    help="run only the network's forward pass (profiling the convolutions)")
+    ap.add_argument("--net-batch", type=int, default=16, help="--network-only: grids per pass")
+    ap.add_argument("--net-n", type=int, default=33, help="--network-only: grid nodes per edge")
+    ap.add_argument("--passes", type=int, default=4, help="--network-only: forward passes")
     args = ap.parse_args()
+    if args.network_only:
+        return network_only(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.count is None:
         args.count = DEFAULT_COUNT[args.workload]
+    if args.prec_order is None:
+        args.prec_order = DEFAULT_ORDER[args.workload]
     if args.omega is None:
         from paper_2505_08491_gb300 import SMOOTH_OMEGA
         args.omega = SMOOTH_OMEGA
@@ -387,6 +537,10 @@ def main():
               "speedup_fgmres_cnn_over_cg": value / world / cg_value}
         Bc.close()
 
+    other = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload != "tree15_32":
+        other = {"tree15_32": extra_workload("tree15_32", max(1, min(args.steps, 5)), flush)}
+
     pk = peaks()
     launches = stats["conv_hidden_launches"]
     nodes_total = sum(op.n3 for op in ops)
@@ -407,10 +561,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         its0 = its_all[-1][0]
         t, it, rel, done = oracle_solve_seconds(insts[0], params, max_seconds=20.0, order=args.prec_order,
-                                                smooth=(args.smooth, args.omega), inner=args.inner)
+                                                smooth=(args.smooth, args.omega), inner=args.inner,
+                                                restart=restart_of(args.workload))
         per_it = t / max(it, 1)
         cpu = {"value": 1.0 / (per_it * its0), "unit": "solves/s", "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"instance 0, FP64 oracle FGMRES(30)+network: {it} iterations timed ({t:.1f} s), "
+               "sample": f"instance 0 (N={insts[0]['N']}), FP64 oracle FGMRES({restart_of(args.workload)})+network: "
+                         f"{it} iterations timed ({t:.1f} s), "
                          f"scaled to the {its0} iterations its solve takes",
                "other_oracle_solvers": oracle_other_solvers(insts[0], direct=False)}
 
@@ -430,6 +586,7 @@ def main():
             "s_per_solve_with_assembly": ms_per_step / 1e3 / args.count + assembly_s,
             "jacobi_fallback_instances": int(stats["fallback_instances"]) // args.steps,
             "jacobi_cg": cg,
+            "other_workloads": other,
             "roofline": roofline, "time_breakdown_ms": breakdown,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(b_all.numel() * 8),
                     "d2h_bytes_per_step": int(x_all.numel() * 8)},

@@ -202,7 +202,6 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     long long rx = CNN_MARGIN_ROWS, rab = CNN_MARGIN_ROWS, nodes = 0;
     std::vector<Seg> segs;
     std::vector<InstRange> ranges;
-    std::vector<TcUnit> units;
     int pd_max = 0;
     for (int n : Ns) pd_max = std::max(pd_max, n + 3);
     w->tps = 2;
@@ -214,12 +213,14 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
         if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
             w->nsm = nsm;
     }
-    // columns of tps*126 in-plane rows, each walked over the N+1 padded planes
-    // [1, N+2) that hold grid nodes
-    struct Column { int inst, s0, nz; };
-    std::vector<Column> cols;
+    // per instance: columns of tps*126 in-plane rows, each walked over the N+1
+    // padded planes [1, N+2) that hold grid nodes (the step order TcSched
+    // describes); the schedule of a pass over every instance
+    std::vector<long long> steps_i, all_pre;
+    std::vector<int> all_inst;
     long long steps = 0;
     const int CH = 512;
+    all_pre.push_back(0);
     for (int i = 0; i < w->ninst; ++i) {
         long long Pd = Ns[i] + 3, P = Pd * Pd * Pd;
         if (Pd + 1 + 256 + 8 > CNN_MARGIN_ROWS) { delete w; md_set_error("grid too large for the network workspace"); return MD_ERR_ARG; }
@@ -232,41 +233,27 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
         ranges.push_back({(int)segs.size(), 0});
         for (int b = 0; b < n3; b += CH) segs.push_back({i, 0, b, std::min(n3, b + CH)});
         ranges.back().count = (int)segs.size() - ranges.back().first;
-        for (long long s0 = 0; s0 < Pd * Pd; s0 += 126 * w->tps) {
-            cols.push_back({i, (int)s0, Ns[i] + 1});
-            steps += Ns[i] + 1;
-        }
+        const long long cols = (Pd * Pd + 126LL * w->tps - 1) / (126LL * w->tps);
+        steps_i.push_back(cols * (Ns[i] + 1));
+        steps += steps_i.back();
+        all_inst.push_back(i);
+        all_pre.push_back(steps);
     }
-    // one CTA per SM, each given a contiguous run of plane steps of equal
-    // length (columns split between CTAs where a run ends)
-    std::vector<int> ubeg;
     w->ngroups = (int)std::max(1LL, std::min<long long>(w->nsm, steps));
-    {
-        size_t ci = 0;
-        int zdone = 0;
-        ubeg.push_back(0);
-        for (int b = 0; b < w->ngroups; ++b) {
-            long long need = steps * (b + 1) / w->ngroups - steps * b / w->ngroups;
-            while (need > 0 && ci < cols.size()) {
-                const int take = (int)std::min<long long>(need, cols[ci].nz - zdone);
-                units.push_back({cols[ci].inst, cols[ci].s0, 1 + zdone, 1 + zdone + take});
-                zdone += take;
-                need -= take;
-                if (zdone == cols[ci].nz) { ++ci; zdone = 0; }
-            }
-            ubeg.push_back((int)units.size());
-        }
-    }
     rx += CNN_MARGIN_ROWS;
     rab += CNN_MARGIN_ROWS;
     w->total_nodes = nodes;
-    w->nunits = (int)units.size();
     md_status st = MD_OK;
     auto chk = [&](md_status s) { if (st == MD_OK) st = s; };
     chk(tc_prepare(w->W, w->tps));
     chk(dev_upload(&w->allocs, &w->N, Ns.data(), Ns.size()));
-    chk(dev_upload(&w->allocs, &w->units, units.data(), units.size()));
-    chk(dev_upload(&w->allocs, &w->ubeg, ubeg.data(), ubeg.size()));
+    chk(dev_upload(&w->allocs, &w->steps, steps_i.data(), steps_i.size()));
+    chk(dev_upload(&w->allocs, &w->all_inst, all_inst.data(), all_inst.size()));
+    chk(dev_upload(&w->allocs, &w->all_pre, all_pre.data(), all_pre.size()));
+    chk(dev_upload(&w->allocs, &w->all_count, &w->ninst, 1));
+    chk(dev_alloc(&w->allocs, &w->run_inst, (size_t)w->ninst));
+    chk(dev_alloc(&w->allocs, &w->run_pre, (size_t)w->ninst + 1));
+    chk(dev_alloc(&w->allocs, &w->run_count, 1));
     chk(dev_alloc(&w->allocs, &w->err, 1));
     chk(dev_upload(&w->allocs, &w->off_x0, w->h_off_x0.data(), w->h_off_x0.size()));
     chk(dev_upload(&w->allocs, &w->off_ab, w->h_off_ab.data(), w->h_off_ab.size()));
@@ -394,14 +381,76 @@ static md_status launch_conv(const __nv_bfloat16* in, const long long* in_off, _
     return MD_OK;
 }
 
+// The plane steps of the instances that run the network in this application
+// (cnn_runs), in instance order, for the tensor-core launches (TcSched): one
+// block scans the per-instance step counts.  Instance i is handled by thread
+// i / per, per = ceil(ninst / blockDim.x).
+__global__ void __launch_bounds__(1024) k_conv_sched(const KState* __restrict__ st, int ninst,
+                                                     const long long* __restrict__ steps, int* __restrict__ act_inst,
+                                                     long long* __restrict__ act_pre, int* __restrict__ count) {
+    __shared__ int wn[32];
+    __shared__ long long ws[32];
+    const int per = (ninst + blockDim.x - 1) / blockDim.x;
+    const int i0 = min(ninst, (int)threadIdx.x * per), i1 = min(ninst, i0 + per);
+    int n = 0;
+    long long sum = 0;
+    for (int i = i0; i < i1; ++i)
+        if (cnn_runs(st, i)) { ++n; sum += steps[i]; }
+    // inclusive scan of (n, sum) over the block: within warps, then over warp totals
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int xn = n;
+    long long xs = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int yn = __shfl_up_sync(0xffffffffu, xn, o);
+        const long long ys = __shfl_up_sync(0xffffffffu, xs, o);
+        if (lane >= o) { xn += yn; xs += ys; }
+    }
+    if (lane == 31) { wn[warp] = xn; ws[warp] = xs; }
+    __syncthreads();
+    if (warp == 0) {
+        int tn = lane < nw ? wn[lane] : 0;
+        long long ts = lane < nw ? ws[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yn = __shfl_up_sync(0xffffffffu, tn, o);
+            const long long ys = __shfl_up_sync(0xffffffffu, ts, o);
+            if (lane >= o) { tn += yn; ts += ys; }
+        }
+        if (lane < nw) { wn[lane] = tn; ws[lane] = ts; }
+    }
+    __syncthreads();
+    // exclusive offsets of this thread's instances
+    int a = xn - n + (warp > 0 ? wn[warp - 1] : 0);
+    long long p = xs - sum + (warp > 0 ? ws[warp - 1] : 0);
+    for (int i = i0; i < i1; ++i)
+        if (cnn_runs(st, i)) {
+            act_inst[a] = i;
+            act_pre[a] = p;
+            ++a;
+            p += steps[i];
+        }
+    if (threadIdx.x == blockDim.x - 1) {
+        act_pre[a] = p;  // a = the count of running instances, p = their steps
+        *count = a;
+    }
+}
+
 static md_status tc_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
                                    cudaEvent_t e_hidden0, cudaEvent_t e_hidden1) {
-    const int grid = w->ngroups;
     TcArgs a{};
+    int grid = w->ngroups;
+    if (io.st) {
+        // inside a solve: only the instances still running the network, spread
+        // over one CTA per SM
+        k_conv_sched<<<1, 1024, 0, s>>>(io.st, w->ninst, w->steps, w->run_inst, w->run_pre, w->run_count);
+        MD_CHECK_LAUNCH();
+        a.sched = TcSched{w->run_inst, w->run_pre, w->run_count};
+        grid = w->nsm;
+    } else {
+        a.sched = TcSched{w->all_inst, w->all_pre, w->all_count};
+    }
     a.Ns = w->N;
-    a.units = w->units;
-    a.ubeg = w->ubeg;
-    a.nunits = w->nunits;
     a.W = w->W;
     a.NS = w->NS;
     a.io = io;
@@ -438,7 +487,7 @@ md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A
         const bool last = l == MD_CNN_LAYERS - 1;
         if (c->engine == 0) {
             TcArgs a{};
-            a.Ns = w->N; a.units = w->units; a.ubeg = w->ubeg; a.nunits = w->nunits; a.W = w->W; a.NS = w->NS; a.err = w->err;
+            a.Ns = w->N; a.sched = TcSched{w->all_inst, w->all_pre, w->all_count}; a.W = w->W; a.NS = w->NS; a.err = w->err;
             a.io = io; a.mode = CONV_RAW;
             a.in = src; a.in_off = src_off;
             a.out = last ? nullptr : A[l + 1]; a.out_off = w->off_ab;

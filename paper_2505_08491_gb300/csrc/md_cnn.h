@@ -10,18 +10,26 @@
 // CNN_MARGIN_ROWS rows before the first and after the last instance, which
 // the tensor-core windows of halo-only tiles may read.
 #define CNN_MARGIN_ROWS 8192
-struct TcUnit;
 struct CnnWork {
     int ninst = 0;
     std::vector<void*> allocs;
     std::vector<int> hN;
     int* N = nullptr;              // device, per instance
-    // tensor-core path: z-walking work units of tps*128 in-plane rows,
-    // window rows W, NS ring slots; CTA b of a launch runs units
-    // [ubeg[b], ubeg[b+1]), ngroups CTAs with equal plane-step counts
-    TcUnit* units = nullptr;
-    int* ubeg = nullptr;
-    int nunits = 0, ngroups = 1, tps = 2, W = 0, NS = 0, nsm = 148;
+    // tensor-core path: z-walking work units of tps*126 in-plane rows,
+    // window rows W, NS ring slots.  The plane steps of a launch are split
+    // evenly over its CTAs (TcSched): every instance (all_*, ngroups CTAs) for
+    // a pass without solver state, or the instances that still run the
+    // network (run_*, written on the device before each application, nsm
+    // CTAs), so that a solve whose instances have mostly converged still
+    // spreads the rest over every SM.
+    long long* steps = nullptr;    // device, per instance: plane steps (columns x (N+1))
+    int* all_inst = nullptr;
+    long long* all_pre = nullptr;
+    int* all_count = nullptr;
+    int* run_inst = nullptr;
+    long long* run_pre = nullptr;
+    int* run_count = nullptr;
+    int ngroups = 1, tps = 2, W = 0, NS = 0, nsm = 148;
     int* err = nullptr;            // set by a timed-out wait in a conv kernel
     __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
     __nv_bfloat16* a = nullptr;    // 4 chunks

@@ -16,7 +16,8 @@
 //
 // Pipeline (one CTA per SM, persistent over work units; a unit is a column
 // of TPS x 128 in-plane rows walked along z, so the window copied for plane
-// z serves planes z-1, z and z+1):
+// z serves planes z-1, z and z+1; each CTA takes an equal share of the plane
+// steps of the instances that run, TcSched):
 //   warp 0      producer: per plane window and chunk one bulk async copy
 //               (TMA, cp.async.bulk) of the TPS*128 + 2(Pd+1) + 8 contiguous
 //               rows the taps read, into a ring of NS shared-memory slots,
@@ -172,6 +173,50 @@ __device__ inline uint4 pack8(const float* v) {
     return r;
 }
 
+// The units of this CTA (TcSched): its share [S b / G, S (b + 1) / G) of
+// the launch's plane steps, walked in order and cut at column ends.  Every
+// role of the CTA walks the same sequence.
+struct TcWalk {
+    long long pos, end;
+    int a;
+};
+
+__device__ __forceinline__ TcWalk walk_begin(const TcSched& sc) {
+    const int A = *sc.count;
+    const long long S = sc.act_pre[A];
+    const long long G = gridDim.x, b = blockIdx.x;
+    TcWalk w;
+    w.pos = S * b / G;
+    w.end = S * (b + 1) / G;
+    // the running instance holding step pos: the last a with act_pre[a] <= pos
+    int lo = 0, hi = A > 0 ? A - 1 : 0;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sc.act_pre[mid] <= w.pos) lo = mid;
+        else hi = mid - 1;
+    }
+    w.a = lo;
+    return w;
+}
+
+template <int TPS>
+__device__ __forceinline__ bool walk_next(const TcSched& sc, const int* Ns, TcWalk& w, TcUnit& U) {
+    if (w.pos >= w.end) return false;
+    while (w.pos >= sc.act_pre[w.a + 1]) ++w.a;
+    const int inst = sc.act_inst[w.a];
+    const int nz = Ns[inst] + 1;
+    const long long t = w.pos - sc.act_pre[w.a];
+    const int col = (int)(t / nz);
+    const int z = (int)(t - (long long)col * nz);
+    const int take = (int)min((long long)(nz - z), w.end - w.pos);
+    U.inst = inst;
+    U.s0 = col * 126 * TPS;
+    U.z0 = 1 + z;
+    U.z1 = 1 + z + take;
+    w.pos += take;
+    return true;
+}
+
 }  // namespace
 
 // KIND 0: hidden 32 -> 32; KIND 1: first 3(8) -> 32; KIND 2: last 32 -> 1.
@@ -218,12 +263,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     float* xch = reinterpret_cast<float*>(bars + 2 * NS + 2 * TC_NBUF_MAX + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // inside a solve most late iteration slots have no active instance: leave
-    // before any set-up when none of this CTA's units runs (uniform decision)
-    if (a.io.st) {
-        bool any = false;
-        for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && !any; ++un) any = cnn_runs(a.io.st, a.units[un].inst);
-        if (!any) return;
+    // a CTA without plane steps (fewer steps than CTAs, or no instance running
+    // the network in this application) leaves before any set-up
+    {
+        const TcWalk w0 = walk_begin(a.sched);
+        if (w0.pos >= w0.end) return;
     }
 
     for (int i = threadIdx.x; i < WIMG / 16; i += blockDim.x)
@@ -257,9 +301,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         if (lane == 0) {
             int g = 0;
             bool ok = true;
-            for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
-                const TcUnit U = a.units[un];
-                if (!cnn_runs(a.io.st, U.inst)) continue;
+            TcWalk wk = walk_begin(a.sched);
+            TcUnit U;
+            while (ok && walk_next<TPS>(a.sched, a.Ns, wk, U)) {
                 const long long Pd = a.Ns[U.inst] + 3, P = Pd * Pd * Pd;
                 const int wl = tc_window_load_rows(TPS, (int)Pd);
                 const __nv_bfloat16* base = a.in + a.in_off[U.inst];
@@ -308,9 +352,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 s_ += n;
                 while (s_ >= NS) { s_ -= NS; ++q_; }
             };
-            for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
-                const TcUnit U = a.units[un];
-                if (!cnn_runs(a.io.st, U.inst)) continue;
+            TcWalk wk = walk_begin(a.sched);
+            TcUnit U;
+            while (ok && walk_next<TPS>(a.sched, a.Ns, wk, U)) {
                 const uint32_t pdu = (uint32_t)(a.Ns[U.inst] + 3);  // one grid row of Pd nodes, in 16-byte rows
                 const uint64_t a_lbo_pd = (uint64_t)(pdu & 0x3FFF) << 16;
                 // A offsets of the (dy, K-half) combinations, in 16-byte rows
@@ -447,9 +491,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         // the last layer's single output channel is handled by channel group 0
         // alone; the other epilogue warps go straight to the end
         bool ok = KIND != 2 || cg == 0;
-        for (int un = a.ubeg[blockIdx.x]; un < a.ubeg[blockIdx.x + 1] && ok; ++un) {
-            const TcUnit U = a.units[un];
-            if (!cnn_runs(a.io.st, U.inst)) continue;
+        TcWalk wk = walk_begin(a.sched);
+        TcUnit U;
+        while (ok && walk_next<TPS>(a.sched, a.Ns, wk, U)) {
             const int N = a.Ns[U.inst], M = N + 1;
             const int Pd = N + 3, P2 = Pd * Pd, P = P2 * Pd;
             // in-plane row of this lane in each tile, and whether it is a grid row

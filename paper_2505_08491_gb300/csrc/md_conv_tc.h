@@ -9,6 +9,20 @@
 // yielding 126 rows).
 struct TcUnit { int inst, s0, z0, z1; };
 
+// The plane steps one launch works on.  The instances that run are listed in
+// instance order, act_inst[a] for a < *count; instance act_inst[a] owns the
+// steps [act_pre[a], act_pre[a + 1]): its columns of TPS*126 in-plane rows in
+// order (column c starts at in-plane row c TPS 126), each walked over the N+1
+// padded planes [1, N+2) that hold grid nodes.  CTA b of a grid of G takes
+// the steps [S b / G, S (b + 1) / G), S = act_pre[*count], cut at column
+// ends into units, so every CTA walks the same number of plane steps
+// whichever instances run.
+struct TcSched {
+    const int* act_inst;
+    const long long* act_pre;
+    const int* count;
+};
+
 #define TC_EPI_CH 8                          // output channels per epilogue thread
 #define TC_EPI_GROUPS (32 / TC_EPI_CH)       // channel groups
 #define TC_EPI_WARPS (4 * TC_EPI_GROUPS)     // epilogue warps: 4 TMEM lane quarters x channel groups
@@ -24,9 +38,7 @@ struct TcArgs {
     __nv_bfloat16* out;          // next activation buffer (hidden layers)
     const long long* out_off;
     const int* Ns;               // per instance grid size N
-    const TcUnit* units;
-    const int* ubeg;             // CTA b runs units [ubeg[b], ubeg[b + 1]); the grid has one CTA per range
-    int nunits;
+    TcSched sched;               // the plane steps of this launch and their split over the CTAs
     int W;                       // rows per (window, chunk) region in shared memory
     int NS;                      // ring slots
     const __nv_bfloat16* wimg;   // weight image in operand layout

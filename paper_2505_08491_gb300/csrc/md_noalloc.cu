@@ -12,8 +12,9 @@
 // library holds until the process exits.
 //
 // Set-up: the first call on a device (with that device current) looks up the
-// array's device address with cudaGetSymbolAddress and caches it; that first
-// call should come before any stream capture.  All calls share the array and
+// array's device address with cudaGetSymbolAddress and caches it for the life
+// of the process (a cudaDeviceReset invalidates it); that first call should
+// come before any stream capture.  All calls share the array and
 // it keeps the last call's contents, so calls that overlap on the GPU (two
 // streams, two threads) race with each other: order them.
 #include <cstring>
@@ -49,6 +50,11 @@ static md_status noalloc_base(void** out) {
     return MD_OK;
 }
 
+// The descriptor is passed by value (a kernel parameter) and written into the
+// array's descriptor slot on the caller's stream, so the call copies nothing
+// from host memory.
+__global__ void k_noalloc_desc(InstDesc d, InstDesc* dst) { *dst = d; }
+
 extern "C" md_status md_apply_noalloc(const md_op* op, md_prec prec, const void* u, void* y, md_stream s) {
     if (!op || !u || !y) { md_set_error("md_apply_noalloc: NULL argument"); return MD_ERR_ARG; }
     if (prec != MD_FP32 && prec != MD_FP64) { md_set_error("md_apply_noalloc: bad precision"); return MD_ERR_ARG; }
@@ -64,6 +70,7 @@ extern "C" md_status md_apply_noalloc(const md_op* op, md_prec prec, const void*
     unsigned char* t = static_cast<unsigned char*>(base) + MD_NOALLOC_DESC_BYTES;
     d.t64 = reinterpret_cast<double*>(t);
     d.t32 = reinterpret_cast<float*>(t);
-    MD_CUDA(cudaMemcpyAsync(base, &d, sizeof(InstDesc), cudaMemcpyHostToDevice, (cudaStream_t)s));
+    k_noalloc_desc<<<1, 1, 0, (cudaStream_t)s>>>(d, static_cast<InstDesc*>(base));
+    MD_CHECK_LAUNCH();
     return launch_apply(op->tabs, static_cast<const InstDesc*>(base), 1, prec, u, op->off0, y, (cudaStream_t)s);
 }

@@ -29,6 +29,13 @@ def test_network_forward_matches_oracle(n):
         ref64 = cnn.forward(X[s].astype(np.float64), layers, bf16=False)
         assert rel_l2(Y[s], ref16) <= 1e-2  # BF16 rounding-boundary flips, see test_gpu_conv_tc
         assert rel_l2(Y[s], ref64) <= 3e-2
+        # node by node: a flip moves a node by a few BF16 units of the
+        # activations feeding it, well inside 5% of the output's RMS (the bound
+        # of the full-size sampled test), while a fault confined to a few rows
+        # (a tile edge, one lane of a 126-row tile) moves those rows by O(RMS)
+        rms = float(np.sqrt(np.mean(ref16 ** 2)))
+        worst = float(np.max(np.abs(Y[s].astype(np.float64) - ref16)))
+        assert worst <= 5e-2 * rms, (n, s, worst / rms)
 
 
 def test_identity_pair_network_is_near_identity():
