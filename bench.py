@@ -591,6 +591,10 @@ def main():
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(b_all.numel() * 8),
                     "d2h_bytes_per_step": int(x_all.numel() * 8)},
             "gpu_launches": int(stats["kernel_launches"]),
+            "launches_per_solve": {"host_graph_launches": stats["graph_launches"] / args.steps,
+                                   "kernels_run": stats["kernel_launches"] / args.steps,
+                                   "note": "each batched solve is one CUDA graph launch; its restart cycles and "
+                                           "iteration slots are conditional nodes decided on the device"},
             "clocks": clk, "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -264,9 +264,13 @@ typedef enum {
 } md_solver;
 
 /* md_batch -- many instances solved together, one launch per kernel across
- * all instances (the ensembled stacking of Section 5.7), every restart cycle
- * replayed as one CUDA graph; instances stop independently on their own
- * convergence.  Vectors of the batch are concatenated: instance i occupies
+ * all instances (the ensembled stacking of Section 5.7); instances stop
+ * independently on their own convergence.  A solve is one launch of a CUDA
+ * graph captured at the first solve (again when the network, block order,
+ * smoothing, inner steps or profiling change): its restart cycles run under
+ * a conditional WHILE node and each iteration slot under a conditional IF
+ * node, both decided on the device, so the host waits once per solve.
+ * Vectors of the batch are concatenated: instance i occupies
  * [offset[i], offset[i] + n_i) of a batched vector.
  * The batch borrows ops and cnn: they must not be destroyed before the
  * batch (its captured graph reads their device buffers at every solve). */
@@ -283,14 +287,16 @@ md_status md_batch_solve(md_batch* b, const double* b_all, double* x_all, double
  * last md_batch_solve, relative to its start; host array of n_ops. */
 md_status md_batch_times(const md_batch* b, double* seconds);
 
-/* Instrumentation.  With profiling on, every captured restart cycle records
- * CUDA events around each preconditioner application, around its four
- * hidden 32->32 convolutions, around the operator apply and around the
- * Arnoldi/Givens kernels; md_batch_stats returns totals since the last
- * reset (device time, ms, summed over launches) and the number of kernel
- * launches the batch issued.  Timing events add no work to the kernels. */
+/* Instrumentation.  With profiling on, the solve graph takes device
+ * timestamps (the global nanosecond timer, from one-thread kernels between
+ * the sections) around each preconditioner application, around its four
+ * hidden 32->32 convolutions, around the operator apply, around the
+ * Arnoldi/Givens kernels and around each restart; md_batch_stats returns
+ * totals since the last reset (device time, ms, summed over the slots that
+ * ran), the kernels the solves ran and their graph launches.  The timestamp
+ * kernels add no work to the others. */
 typedef struct {
-    long long kernel_launches;   /* kernels launched by md_batch_solve calls */
+    long long kernel_launches;   /* kernels run by md_batch_solve calls (graph nodes executed) */
     long long cycles;            /* restart cycles (CG: chunks of 25 iterations) */
     long long iterations;        /* sum over instances of Krylov iterations */
     long long precond_nodes;     /* sum over instances of network-preconditioned iterations x grid nodes */
@@ -301,6 +307,7 @@ typedef struct {
     double arnoldi_ms;           /* dots, updates, Givens */
     double restart_ms;           /* least squares, x update, FP64 residual */
     long long fallback_instances; /* network solves whose instance switched to Jacobi */
+    long long graph_launches;    /* host launches: one graph per md_batch_solve */
 } md_batch_stats_t;
 md_status md_batch_set_profiling(md_batch* b, int enable);
 /* lower = 1: the network-preconditioned batch uses md_precondition_lower's

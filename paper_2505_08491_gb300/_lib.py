@@ -33,7 +33,7 @@ class MdBatchStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_longlong), ("cycles", C.c_longlong), ("iterations", C.c_longlong),
                 ("precond_nodes", C.c_longlong), ("prec_ms", C.c_double), ("conv_hidden_ms", C.c_double),
                 ("conv_hidden_launches", C.c_longlong), ("apply_ms", C.c_double), ("arnoldi_ms", C.c_double),
-                ("restart_ms", C.c_double), ("fallback_instances", C.c_longlong)]
+                ("restart_ms", C.c_double), ("fallback_instances", C.c_longlong), ("graph_launches", C.c_longlong)]
 
 
 class MdTrainCfg(C.Structure):

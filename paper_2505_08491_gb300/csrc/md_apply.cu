@@ -5,45 +5,14 @@
 //   y1   = kappa K1 u1 - beta Psi^T W t                   1D nodes
 //
 // since M [u0; u1] = [Pi^T W (Pi u0 - Psi u1); -Psi^T W (Pi u0 - Psi u1)].
-// Launch A runs the 27-point Q1 stencil (kind 0) and the averaging gather
-// (kind 1) side by side; launch B adds the Pi^T scatter on the grid nodes the
-// averaging reaches (kind 2) and computes the 1D rows (kind 3).  All sums are
+// Launch A runs the averaging gather t (kind 1); launch B runs the 27-point
+// Q1 stencil tile by tile with the Pi^T W t rows of each tile's nodes added
+// before the tile is stored (kind 4), and the 1D rows (kind 3).  All sums are
 // in a fixed order, so results are deterministic.
 #include <algorithm>
 #include <cmath>
 
 #include "md_common.cuh"
-
-// y0 over [begin, end) of the grid: Dirichlet nodes copy u, interior nodes
-// take the stencil with boundary neighbours treated as zero (eliminated
-// columns).  Offset class c = |dx|+|dy|+|dz| selects the coefficient.
-template <typename T>
-__device__ inline T stencil_node(const InstDesc& d, const T* __restrict__ u, int n, bool& boundary) {
-    const int N = d.N, M = N + 1;
-    const int i = n % M, r = n / M, j = r % M, k = r / M;
-    boundary = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
-    if (boundary) return u[n];
-    const bool xm = i >= 2, xp = i <= N - 2;
-    const bool ym = j >= 2, yp = j <= N - 2;
-    const bool zm = k >= 2, zp = k <= N - 2;
-    T s[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {
-        const bool mz = dz < 0 ? zm : (dz > 0 ? zp : true);
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const bool my = dy < 0 ? ym : (dy > 0 ? yp : true);
-            if (!(mz && my)) continue;
-            const int base = n + dy * M + dz * M * M;
-            const int cls = (dy != 0) + (dz != 0);
-            T b = u[base];
-            T ac = (xm ? u[base - 1] : T(0)) + (xp ? u[base + 1] : T(0));
-            s[cls] += b;
-            s[cls + 1] += ac;
-        }
-    }
-    return Pr<T>::st(d, 0) * s[0] + Pr<T>::st(d, 1) * s[1] + Pr<T>::st(d, 2) * s[2] + Pr<T>::st(d, 3) * s[3];
-}
 
 template <typename T>
 __device__ inline T gather_q(const InstDesc& d, const T* __restrict__ u0, const T* __restrict__ u1, int q) {
@@ -58,23 +27,139 @@ __device__ inline bool gate_skip(const KState* st, int gate, int inst) {
     return gate == 1 ? !st[inst].active : st[inst].t_done != 0ULL;
 }
 
+// a / (N+1) for 0 <= a < 2^20 (InstDesc::mdiv)
+__device__ __forceinline__ int div_m(unsigned int a, unsigned int mdiv) { return (int)__umulhi(a, mdiv); }
+
+// Launch A: t_q = (Pi u0)(q) - (Psi u1)(q) at the quadrature points (kind 1).
 template <typename T>
 __global__ void __launch_bounds__(MD_TB) k_apply_a(const InstDesc* __restrict__ D, const Seg* __restrict__ seg,
                                                    const long long* __restrict__ off, const T* __restrict__ u,
-                                                   T* __restrict__ y, const KState* __restrict__ st, int gate) {
+                                                   const KState* __restrict__ st, int gate) {
     const Seg sg = seg[blockIdx.x];
     if (gate_skip(st, gate, sg.inst)) return;
     const InstDesc& d = D[sg.inst];
     const T* ui = u + off[sg.inst];
-    T* yi = y + off[sg.inst];
-    if (sg.kind == 0) {
-        for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
-            bool bd;
-            yi[n] = stencil_node<T>(d, ui, n, bd);
+    T* t = Pr<T>::t(d);
+    for (int q = sg.begin + threadIdx.x; q < sg.end; q += blockDim.x) t[q] = gather_q<T>(d, ui, ui + d.n3, q);
+}
+
+// Launch B, kind 4: one stencil tile -- planes [z0, z0 + nz), rows [y0, y0 + ny),
+// all N+1 columns -- of y0 = K00 u0 + beta Pi^T W t.
+//  1. The tile and a one-node halo in y and z are copied into shared memory,
+//     Dirichlet nodes as zero (their columns are eliminated): each plane's
+//     rows are one contiguous range of the grid, read with consecutive
+//     threads on consecutive nodes.
+//  2. Each thread owns one column (x, y) of the tile and walks z.  With
+//     plane sums at (x, y) of plane p -- P0 = u, P1 = the 4 in-plane face
+//     neighbours, P2 = the 4 in-plane corner neighbours -- the 27-point Q1
+//     stencil by offset class is
+//       centre P0(z); face P1(z) + P0(z-1) + P0(z+1);
+//       edge P2(z) + P1(z-1) + P1(z+1); corner P2(z-1) + P2(z+1),
+//     so every plane's sums serve three output planes.  Dirichlet nodes
+//     copy u.  Results go to a shared output tile.
+//  3. The rows of Pi^T W of the tile's touched nodes (grouped by tile at
+//     assembly) add beta sum_q (Pi^T W)_{n,q} t_q to their nodes.
+//  4. The output tile is stored plane by plane, each plane one contiguous
+//     range.  So y0 is written once, without a read-modify-write.
+// Kind 3: the 1D rows y1 = kappa K1 u1 - beta Psi^T W t.
+template <typename T>
+__device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __restrict__ ui, T* __restrict__ yi,
+                                    T* s_in) {
+    const int N = d.N, M = N + 1, TY = d.ty;
+    const unsigned int mdiv = d.mdiv;
+    const int zt = tile / d.nyt, yt = tile - zt * d.nyt;
+    const int z0 = zt * d.tz, y0 = yt * TY;
+    const int nz = min(d.tz, M - z0), ny = min(TY, M - y0);
+    const int rows_in = ny + 2, slab_in = rows_in * M;  // one halo-padded plane of the tile
+    T* s_out = s_in + (size_t)(nz + 2) * slab_in;
+    // 1. input tile: planes z0-1 .. z0+nz, rows y0-1 .. y0+ny (out-of-grid rows
+    // zero).  Element e of the tile is plane e / slab_in, row r, column x of it;
+    // each thread issues APPLY_LU loads before storing any (the loads then
+    // overlap instead of each store waiting on its own load).
+    {
+        constexpr int APPLY_LU = 8;
+        const int total_in = (nz + 2) * slab_in;
+        const unsigned int sdiv = 0xFFFFFFFFu / (unsigned int)slab_in + 1u;  // ceil(2^32 / slab_in)
+        for (int e0 = threadIdx.x; e0 < total_in; e0 += APPLY_LU * blockDim.x) {
+            T v[APPLY_LU];
+#pragma unroll
+            for (int k = 0; k < APPLY_LU; ++k) {
+                const int e = e0 + k * blockDim.x;
+                v[k] = T(0);
+                if (e < total_in) {
+                    const int pz = (int)__umulhi((unsigned int)e, sdiv), er = e - pz * slab_in;
+                    const int r = div_m((unsigned int)er, mdiv), x = er - r * M;
+                    const int z = z0 - 1 + pz, y = y0 - 1 + r;
+                    if (z >= 1 && z <= N - 1 && y >= 1 && y <= N - 1 && x >= 1 && x <= N - 1)
+                        v[k] = ui[((long long)z * M + y) * M + x];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < APPLY_LU; ++k) {
+                const int e = e0 + k * blockDim.x;
+                if (e < total_in) s_in[e] = v[k];
+            }
         }
-    } else {
-        T* t = Pr<T>::t(d);
-        for (int q = sg.begin + threadIdx.x; q < sg.end; q += blockDim.x) t[q] = gather_q<T>(d, ui, ui + d.n3, q);
+    }
+    __syncthreads();
+    // 2. stencil, one column per thread
+    const T c0 = Pr<T>::st(d, 0), c1 = Pr<T>::st(d, 1), c2 = Pr<T>::st(d, 2), c3 = Pr<T>::st(d, 3);
+    for (int c = threadIdx.x; c < ny * M; c += blockDim.x) {
+        const int r = div_m((unsigned int)c, mdiv), x = c - r * M, y = y0 + r;
+        T* so = s_out + c;
+        const bool col_bd = x == 0 || x == N || y == 0 || y == N;
+        if (col_bd) {
+            for (int zz = 0; zz < nz; ++zz) so[(size_t)zz * ny * M] = ui[((long long)(z0 + zz) * M + y) * M + x];
+            continue;
+        }
+        // plane sums of input plane pz at this column
+        const T* base = s_in + (size_t)(r + 1) * M + x;
+        auto sums = [&](int pz, T& p0, T& p1, T& p2) {
+            const T* b = base + (size_t)pz * slab_in;
+            const T l = b[-1], rr = b[1], up = b[M], dn = b[-M];
+            const T ul = b[M - 1], ur = b[M + 1], dl = b[-M - 1], dr = b[-M + 1];
+            p0 = b[0];
+            p1 = (l + rr) + (up + dn);
+            p2 = (ul + ur) + (dl + dr);
+        };
+        T a0, a1, a2, b0, b1, b2, f0, f1, f2;
+        sums(0, a0, a1, a2);
+        sums(1, b0, b1, b2);
+        for (int zz = 0; zz < nz; ++zz) {
+            sums(zz + 2, f0, f1, f2);
+            const int z = z0 + zz;
+            T v;
+            if (z == 0 || z == N) {
+                v = ui[((long long)z * M + y) * M + x];
+            } else {
+                const T face = b1 + (a0 + f0);
+                const T edge = b2 + (a1 + f1);
+                const T corner = a2 + f2;
+                v = c0 * b0 + c1 * face + c2 * edge + c3 * corner;
+            }
+            so[(size_t)zz * ny * M] = v;
+            a0 = b0; a1 = b1; a2 = b2;
+            b0 = f0; b1 = f1; b2 = f2;
+        }
+    }
+    __syncthreads();
+    // 3. coupling rows of the tile's touched nodes
+    const T* tv = Pr<T>::tn(d);
+    const T* tq = Pr<T>::t(d);
+    const T beta = (T)d.beta;
+    for (int idx = d.tile_tptr[tile] + threadIdx.x; idx < d.tile_tptr[tile + 1]; idx += blockDim.x) {
+        T acc = T(0);
+        for (int jj = d.tn_ptr[idx]; jj < d.tn_ptr[idx + 1]; ++jj) acc += tv[jj] * tq[d.tn_q[jj]];
+        const int n = d.tn_node[idx];
+        const int zy = n / M, x = n - zy * M, z = zy / M, y = zy - z * M;
+        s_out[((size_t)(z - z0) * ny + (y - y0)) * M + x] += beta * acc;
+    }
+    __syncthreads();
+    // 4. store, plane by plane
+    for (int zz = 0; zz < nz; ++zz) {
+        T* gp = yi + ((long long)(z0 + zz) * M + y0) * M;
+        const T* sp = s_out + (size_t)zz * ny * M;
+        for (int e = threadIdx.x; e < ny * M; e += blockDim.x) gp[e] = sp[e];
     }
 }
 
@@ -82,43 +167,49 @@ template <typename T>
 __global__ void __launch_bounds__(MD_TB) k_apply_b(const InstDesc* __restrict__ D, const Seg* __restrict__ seg,
                                                    const long long* __restrict__ off, const T* __restrict__ u,
                                                    T* __restrict__ y, const KState* __restrict__ st, int gate) {
+    extern __shared__ __align__(16) unsigned char apply_smem[];
     const Seg sg = seg[blockIdx.x];
     if (gate_skip(st, gate, sg.inst)) return;
     const InstDesc& d = D[sg.inst];
     const T* ui = u + off[sg.inst];
     T* yi = y + off[sg.inst];
+    if (sg.kind == 4) {
+        stencil_tile<T>(d, sg.begin, ui, yi, reinterpret_cast<T*>(apply_smem));
+        return;
+    }
     const T* t = Pr<T>::t(d);
     const T beta = (T)d.beta;
-    if (sg.kind == 2) {
-        const T* tv = Pr<T>::tn(d);
-        for (int idx = sg.begin + threadIdx.x; idx < sg.end; idx += blockDim.x) {
-            T acc = T(0);
-            for (int jj = d.tn_ptr[idx]; jj < d.tn_ptr[idx + 1]; ++jj) acc += tv[jj] * t[d.tn_q[jj]];
-            yi[d.tn_node[idx]] += beta * acc;
-        }
-    } else {
-        const T* u1 = ui + d.n3;
-        T* y1 = yi + d.n3;
-        const T* kv = Pr<T>::k1(d);
-        const T* pv = Pr<T>::pw(d);
-        for (int i = sg.begin + threadIdx.x; i < sg.end; i += blockDim.x) {
-            T a1 = T(0), a2 = T(0);
-            for (int jj = d.k1_ptr[i]; jj < d.k1_ptr[i + 1]; ++jj) a1 += kv[jj] * u1[d.k1_col[jj]];
-            for (int jj = d.pw_ptr[i]; jj < d.pw_ptr[i + 1]; ++jj) a2 += pv[jj] * t[d.pw_q[jj]];
-            y1[i] = a1 - beta * a2;
-        }
+    const T* u1 = ui + d.n3;
+    T* y1 = yi + d.n3;
+    const T* kv = Pr<T>::k1(d);
+    const T* pv = Pr<T>::pw(d);
+    for (int i = sg.begin + threadIdx.x; i < sg.end; i += blockDim.x) {
+        T a1 = T(0), a2 = T(0);
+        for (int jj = d.k1_ptr[i]; jj < d.k1_ptr[i + 1]; ++jj) a1 += kv[jj] * u1[d.k1_col[jj]];
+        for (int jj = d.pw_ptr[i]; jj < d.pw_ptr[i + 1]; ++jj) a2 += pv[jj] * t[d.pw_q[jj]];
+        y1[i] = a1 - beta * a2;
     }
+}
+
+// Dynamic shared memory of the stencil tiles, set when a launch table is built
+// (with its device current, outside any stream capture).
+md_status apply_prepare(int smem32, int smem64) {
+    if (smem32 > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_apply_b<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32));
+    if (smem64 > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_apply_b<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem64));
+    return MD_OK;
 }
 
 md_status launch_apply(const Tables& T, const InstDesc* d, int ninst, md_prec prec, const void* u,
                        const long long* off, void* y, cudaStream_t s, const KState* st, int gate) {
     (void)ninst;
     if (prec == MD_FP32) {
-        k_apply_a<float><<<T.apply_a.nblocks, MD_TB, 0, s>>>(d, T.apply_a.seg, off, (const float*)u, (float*)y, st, gate);
-        k_apply_b<float><<<T.apply_b.nblocks, MD_TB, 0, s>>>(d, T.apply_b.seg, off, (const float*)u, (float*)y, st, gate);
+        k_apply_a<float><<<T.apply_a.nblocks, MD_TB, 0, s>>>(d, T.apply_a.seg, off, (const float*)u, st, gate);
+        k_apply_b<float><<<T.apply_b.nblocks, MD_TB, T.apply_b.smem32, s>>>(d, T.apply_b.seg, off, (const float*)u,
+                                                                          (float*)y, st, gate);
     } else {
-        k_apply_a<double><<<T.apply_a.nblocks, MD_TB, 0, s>>>(d, T.apply_a.seg, off, (const double*)u, (double*)y, st, gate);
-        k_apply_b<double><<<T.apply_b.nblocks, MD_TB, 0, s>>>(d, T.apply_b.seg, off, (const double*)u, (double*)y, st, gate);
+        k_apply_a<double><<<T.apply_a.nblocks, MD_TB, 0, s>>>(d, T.apply_a.seg, off, (const double*)u, st, gate);
+        k_apply_b<double><<<T.apply_b.nblocks, MD_TB, T.apply_b.smem64, s>>>(d, T.apply_b.seg, off, (const double*)u,
+                                                                           (double*)y, st, gate);
     }
     MD_CHECK_LAUNCH();
     return MD_OK;

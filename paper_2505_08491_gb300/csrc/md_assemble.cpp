@@ -200,7 +200,19 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     te.reserve(pi_col.size());
     for (int q = 0; q < nq; ++q)
         for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) te.push_back({pi_col[j], q, pi_val[j] * wq[q]});
-    std::sort(te.begin(), te.end(), [](const TE& p, const TE& r) { return p.node != r.node ? p.node < r.node : p.q < r.q; });
+    // rows grouped by the apply's stencil tile, by node within a tile
+    int ty = 1, tz = 1;
+    apply_tile_shape(N, &ty, &tz);
+    const int nyt = (N + 1 + ty - 1) / ty, nzt = (N + 1 + tz - 1) / tz;
+    auto tile_of = [&](int node) {
+        const int M = N + 1, z = node / (M * M), y = (node / M) % M;
+        return (z / tz) * nyt + y / ty;
+    };
+    std::sort(te.begin(), te.end(), [&](const TE& p, const TE& r) {
+        const int tp = tile_of(p.node), tr = tile_of(r.node);
+        if (tp != tr) return tp < tr;
+        return p.node != r.node ? p.node < r.node : p.q < r.q;
+    });
     // row sums of Pi (less than 1 where boundary weights were dropped)
     std::vector<double> pi_rowsum(nq, 0.0);
     for (int q = 0; q < nq; ++q)
@@ -227,6 +239,9 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         i = j;
     }
     const int ntouch = (int)tn_node.size();
+    std::vector<int> tile_tptr((size_t)nyt * nzt + 1, 0);
+    for (int i = 0; i < ntouch; ++i) tile_tptr[tile_of(tn_node[i]) + 1] += 1;
+    for (size_t b = 1; b < tile_tptr.size(); ++b) tile_tptr[b] += tile_tptr[b - 1];
 
     // ---- 1D operators
     const double kappa = k_lambda * M_PI * radius * radius;
@@ -281,6 +296,38 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     for (int i = 0; i < n1; ++i) tdinv[i] = 1.0 / dd[i];
     std::vector<int> tr_order = order, tr_parent(n1);
     for (int i = 0; i < n1; ++i) tr_parent[i] = parent[i];
+    // level schedule: height (leaves 0) from the children-first order, depth
+    // (roots 0) from the reverse order; children lists in elimination order
+    std::vector<int> hgt(n1, 0), dep(n1, 0), ch_ptr(n1 + 1, 0), ch_idx;
+    for (int idx = 0; idx < n1; ++idx) {
+        const int i = order[idx], p = parent[i];
+        if (p >= 0) { hgt[p] = std::max(hgt[p], hgt[i] + 1); ch_ptr[p + 1] += 1; }
+    }
+    for (int idx = n1 - 1; idx >= 0; --idx) {
+        const int i = order[idx], p = parent[i];
+        dep[i] = p >= 0 ? dep[p] + 1 : 0;
+    }
+    for (int i = 0; i < n1; ++i) ch_ptr[i + 1] += ch_ptr[i];
+    ch_idx.assign((size_t)ch_ptr[n1], 0);
+    {
+        std::vector<int> fill(ch_ptr.begin(), ch_ptr.end() - 1);
+        for (int idx = 0; idx < n1; ++idx) {
+            const int i = order[idx], p = parent[i];
+            if (p >= 0) ch_idx[fill[p]++] = i;
+        }
+    }
+    auto levels = [&](const std::vector<int>& key, std::vector<int>& ptr, std::vector<int>& nodes) {
+        const int nl = n1 ? *std::max_element(key.begin(), key.end()) + 1 : 0;
+        ptr.assign((size_t)nl + 1, 0);
+        for (int i = 0; i < n1; ++i) ptr[key[i] + 1] += 1;
+        for (int l = 0; l < nl; ++l) ptr[l + 1] += ptr[l];
+        nodes.assign((size_t)n1, 0);
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int idx = 0; idx < n1; ++idx) nodes[fill[key[order[idx]]]++] = order[idx];
+        return nl;
+    };
+    std::vector<int> lvu_ptr, lv_up, lvd_ptr, lv_dn;
+    const int nlvu = levels(hgt, lvu_ptr, lv_up), nlvd = levels(dep, lvd_ptr, lv_dn);
 
     // ---- stencils and diagonal
     // Q1 stencil by offset class |dx|+|dy|+|dz| (h-scaled): stiffness {8/3, 0, -1/6, -1/12} h,
@@ -294,6 +341,8 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     D.N = N; D.n3 = n3; D.n1 = n1; D.nq = nq; D.ntouch = ntouch; D.nsegs = E;
     D.n = (long long)n3 + n1;
     D.h = h; D.beta = beta;
+    D.ty = ty; D.tz = tz; D.nyt = nyt; D.ntiles = nyt * nzt;
+    D.mdiv = (unsigned int)((((unsigned long long)1 << 32) + (unsigned long long)N) / (unsigned long long)(N + 1));
     for (int c = 0; c < 4; ++c) {
         D.st64[c] = k_omega * Kst[c] + sigma_omega * Mst[c];
         D.st32[c] = (float)D.st64[c];
@@ -324,7 +373,7 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     UP(upi(&D.pi_ptr, pi_ptr)); UP(upi(&D.pi_col, pi_col)); UP(up64(&D.pi_v64, pi_val)); UP(up32(&D.pi_v32, pi_val));
     UP(upi(&D.qa, qa)); UP(upi(&D.qb, qb));
     UP(up64(&D.psa64, psa)); UP(up64(&D.psb64, psb)); UP(up32(&D.psa32, psa)); UP(up32(&D.psb32, psb));
-    UP(upi(&D.tn_node, tn_node)); UP(upi(&D.tn_ptr, tn_ptr)); UP(upi(&D.tn_q, tn_q));
+    UP(upi(&D.tn_node, tn_node)); UP(upi(&D.tn_ptr, tn_ptr)); UP(upi(&D.tn_q, tn_q)); UP(upi(&D.tile_tptr, tile_tptr));
     UP(up64(&D.tn_v64, tn_v)); UP(up32(&D.tn_v32, tn_v));
     UP(upi(&D.k1_ptr, k1_ptr)); UP(upi(&D.k1_col, k1_col)); UP(up64(&D.k1_v64, k1_v)); UP(up32(&D.k1_v32, k1_v));
     UP(upi(&D.pw_ptr, pw_ptr)); UP(upi(&D.pw_q, pw_q)); UP(up64(&D.pw_v64, pw_v)); UP(up32(&D.pw_v32, pw_v));
@@ -333,6 +382,9 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         std::vector<double> lo(n1), dio(n1);
         for (int i = 0; i < n1; ++i) { lo[i] = tl[i]; dio[i] = tdinv[i]; }
         UP(upi(&D.tr_order, tr_order)); UP(upi(&D.tr_parent, tr_parent));
+        D.nlvu = nlvu; D.nlvd = nlvd;
+        UP(upi(&D.lvu_ptr, lvu_ptr)); UP(upi(&D.lv_up, lv_up)); UP(upi(&D.ch_ptr, ch_ptr)); UP(upi(&D.ch_idx, ch_idx));
+        UP(upi(&D.lvd_ptr, lvd_ptr)); UP(upi(&D.lv_dn, lv_dn));
         UP(up64(&D.tr_l64, lo)); UP(up64(&D.tr_dinv64, dio)); UP(up32(&D.tr_l32, lo)); UP(up32(&D.tr_dinv32, dio));
     }
     {

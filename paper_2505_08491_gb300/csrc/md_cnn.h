@@ -60,7 +60,7 @@ struct OutIO {
 };
 
 md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvOut last, cudaStream_t s,
-                             cudaEvent_t e_hidden0 = nullptr, cudaEvent_t e_hidden1 = nullptr);
+                             unsigned long long* stamp0 = nullptr, unsigned long long* stamp1 = nullptr);
 md_status cnn_forward_train(const md_cnn* c, CnnWork* w, __nv_bfloat16* const* A, __nv_bfloat16* const* Z,
                             const OutIO& io, cudaStream_t s);
 md_status cnn_upload(md_cnn* c);

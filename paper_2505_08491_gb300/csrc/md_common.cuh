@@ -187,3 +187,8 @@ __device__ inline unsigned long long globaltimer() {
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
+
+// Device timestamp of a point in a stream (or captured graph): the global
+// nanosecond timer when the kernel runs, i.e. after everything before it on
+// the stream has finished.  One per translation unit (internal linkage).
+static __global__ void k_stamp(unsigned long long* at) { *at = globaltimer(); }

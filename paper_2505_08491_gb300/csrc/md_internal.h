@@ -46,14 +46,29 @@ struct InstDesc {
     // per quadrature point: 1D element end nodes and P1 values there
     const int* qa; const int* qb;
     const double* psa64; const double* psb64; const float* psa32; const float* psb32;
-    // Pi^T W, row per touched grid node: entries (q, Pi[q,n] w_q)
+    // Pi^T W, row per touched grid node: entries (q, Pi[q,n] w_q); rows ordered
+    // by stencil tile (below), and by node within a tile
     const int* tn_node; const int* tn_ptr; const int* tn_q; const double* tn_v64; const float* tn_v32;
+    // stencil tiles of the operator apply: tz planes x ty rows x all N+1
+    // columns of the grid, numbered zt * nyt + yt (ntiles of them); the rows
+    // of Pi^T W of tile b are tile_tptr[b] .. tile_tptr[b+1] - 1.  mdiv =
+    // ceil(2^32 / (N+1)) divides by N+1 with one multiply-high (exact for
+    // dividends below 2^20).
+    int ty, tz, nyt, ntiles;
+    unsigned int mdiv;
+    const int* tile_tptr;
     // 1D rows: kappa K1 (CSR) and Psi^T W (entries (q, psi w_q))
     const int* k1_ptr; const int* k1_col; const double* k1_v64; const float* k1_v32;
     const int* pw_ptr; const int* pw_q; const double* pw_v64; const float* pw_v32;
     const double* load1;
     // tree LDL^T of B11 in elimination order (children before parents)
     const int* tr_order; const int* tr_parent;
+    // level schedule of its sweeps: nodes by height above the leaves in
+    // lv_up[lvu_ptr[h] .. lvu_ptr[h+1]) (a node's children are lower), the
+    // children of node i in ch_idx[ch_ptr[i] .. ch_ptr[i+1]); nodes by depth
+    // below the roots in lv_dn[lvd_ptr[k] .. lvd_ptr[k+1])
+    int nlvu, nlvd;
+    const int* lvu_ptr; const int* lv_up; const int* ch_ptr; const int* ch_idx; const int* lvd_ptr; const int* lv_dn;
     const double* tr_l64; const double* tr_dinv64; const float* tr_l32; const float* tr_dinv32;
     // per grid / per dof
     const float* dist;      // n3
@@ -77,12 +92,13 @@ struct Table {
     InstRange* range = nullptr; // device, per instance
     int nblocks = 0;
     std::vector<InstRange> hrange;
+    int smem32 = 0, smem64 = 0; // dynamic shared memory of its launch (stencil tiles), FP32 / FP64
 };
 
 // Tables for the launches of a set of instances.
 struct Tables {
-    Table apply_a;   // kind 0: stencil over n3 ; kind 1: gather over nq
-    Table apply_b;   // kind 2: Pi^T scatter over touched ; kind 3: 1D rows over n1
+    Table apply_a;   // kind 1: averaging gather t = Pi u0 - Psi u1 over nq
+    Table apply_b;   // kind 4: stencil tile with its Pi^T W t rows ; kind 3: 1D rows over n1
     Table vec;       // kind 0: ranges over n (whole instance vector)
     Table n3;        // kind 0: ranges over n3
     Table touch;     // kind 0: ranges over ntouch
@@ -147,7 +163,7 @@ struct KState {
     double icoef[MD_INNER_MAX + 1];
     double iy[MD_INNER_MAX];
     double ib0;
-    unsigned int counter[8];             // last-block counters per reduction kernel
+    unsigned int counter[12];            // last-block counters per reduction kernel
 };
 
 // Per-instance results written when an instance finishes: iterations,
@@ -165,6 +181,13 @@ struct ResOut {
 __host__ __device__ inline bool cnn_runs(const KState* st, int inst) {
     return !st || (st[inst].active && !st[inst].fallback);
 }
+
+// Stencil tile shape of the operator apply for grid N: ty rows of all N+1
+// columns (at most 256 columns, one per thread) and tz planes, such that the
+// FP64 input tile with its halo and the output tile fit 64 KB of shared memory.
+void apply_tile_shape(int N, int* ty, int* tz);
+int apply_tile_smem(int N, int ty, int tz, int elem_bytes);
+md_status apply_prepare(int smem32, int smem64);
 
 // Problem-size independent kernel launches (md_apply.cu)
 struct KState;

@@ -31,6 +31,21 @@
 // elements per thread and loop trip of the CG streaming kernels
 #define CG_U 4
 
+// Control block of one batched solve, on the device: the limits the host
+// writes before launching the solve graph, what the graph counts while it
+// runs, and (when profiling) the summed device time of its sections.
+struct SolveCtl {
+    double tol;
+    int maxit;
+    int max_cycles;
+    int cycles;                        // restart cycles (CG: chunks of iterations) run
+    int pad;
+    unsigned long long kernels;        // kernels run by the loop (slots, restarts, chunks)
+    unsigned long long t_prec, t_conv, t_apply, t_arn, t_restart;  // ns summed over slots / restarts
+    unsigned long long slots, conv_groups;
+    unsigned long long stamp[8];
+};
+
 struct md_batch {
     int ninst = 0;
     md_solver solver = MD_SOLVER_FGMRES_JACOBI;
@@ -52,20 +67,15 @@ struct md_batch {
     ResOut res{};
     int max_n1 = 0, max_nq = 0;
     CnnWork* cw = nullptr;
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph = nullptr;     // CG: one chunk of iterations
-    // FGMRES: the iteration slots of a restart cycle in parts [part_end[p-1],
-    // part_end[p]), each a graph ending with a flag "some instance still
-    // iterates", and the restart step as its own graph; a cycle launches the
-    // next part only while the flag is set
-    std::vector<cudaGraphExec_t> parts;
-    std::vector<int> part_end;
-    std::vector<long long> part_kernels;
-    cudaGraphExec_t restart_graph = nullptr;
-    long long restart_kernels = 0;
-    int* d_any = nullptr;
-    int* h_any = nullptr;                // pinned host copy
-    int executed_slots = 0;              // slots the last cycle ran
+    // the whole solve as one executable graph, driven on the device: the
+    // set-up kernels, then a WHILE node over restart cycles (CG: chunks of
+    // iterations) whose body, for FGMRES, runs every iteration slot under an
+    // IF node that skips it once no instance iterates in the cycle
+    cudaStream_t cap = nullptr, cap_body = nullptr, cap_slot = nullptr;  // capture streams
+    cudaGraphExec_t solve_graph = nullptr;
+    long long init_kernels = 0;          // kernels of the set-up part (the rest are counted on the device)
+    SolveCtl* ctl = nullptr;             // device: limits of this solve, counters, profile sums
+    SolveCtl* h_ctl = nullptr;           // pinned host copy
     int prec_order = 0;                  // 0: block upper-triangular (the paper's), 1: lower
     int graph_prec_order = 0;
     int inner_m = 0;                     // inner FGMRES steps of the 3D block solve (0: one network application)
@@ -82,24 +92,19 @@ struct md_batch {
     std::vector<double> last_times;
     // instrumentation
     bool profiling = false;
-    std::vector<cudaEvent_t> ev;   // per iteration slot j: 6 events, then 2 for the restart
     md_batch_stats_t stats{};
 };
 
-enum { EV_PRE0 = 0, EV_CONV0, EV_CONV1, EV_APPLY0, EV_APPLY1, EV_ARN1, EV_PER_J };
+// Device timestamps of the profiled sections (SolveCtl::stamp): per iteration
+// slot (reused by every slot, which run in order), then the restart.
+enum { ST_PRE0 = 0, ST_CONV0, ST_CONV1, ST_APPLY0, ST_APPLY1, ST_ARN1, ST_REST0, ST_REST1, ST_COUNT };
 
-static cudaEvent_t ev_at(md_batch* B, int j, int which) {
+static unsigned long long* stamp_at(md_batch* B, int which) {
     if (!B->profiling) return nullptr;
-    return B->ev[(size_t)j * EV_PER_J + which];
+    return &B->ctl->stamp[which];
 }
-static cudaEvent_t ev_restart(md_batch* B, int which) {
-    if (!B->profiling) return nullptr;
-    return B->ev[(size_t)B->k * EV_PER_J + which];
-}
-// Inside stream capture an event must be recorded as an external event node
-// to be readable after the graph runs.
-static void rec(cudaEvent_t e, cudaStream_t s) {
-    if (e) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+static void stamp(unsigned long long* at, cudaStream_t s) {
+    if (at) k_stamp<<<1, 1, 0, s>>>(at);
 }
 
 // ---------------------------------------------------------------------------
@@ -133,18 +138,56 @@ __device__ inline void reduce_values(double* vals, int count, double* part, int 
 }
 
 // ---------------------------------------------------------------------------
-__global__ void k_init_state(KState* st, int ninst, double tol, int maxit, int* ndone) {
+__global__ void k_init_state(KState* st, int ninst, const SolveCtl* ctl, int* ndone) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *ndone = 0;
     if (i >= ninst) return;
     KState& S = st[i];
-    S.tol = tol; S.maxit = maxit; S.iters = 0; S.converged = 0; S.active = 0; S.j = 0; S.m = 0;
+    S.tol = ctl->tol; S.maxit = ctl->maxit; S.iters = 0; S.converged = 0; S.active = 0; S.j = 0; S.m = 0;
     S.reorth = 0; S.nan_seen = 0; S.fallback = 0; S.bnorm = 0; S.relres = 1; S.cycle_iters = -1; S.stalls = 0;
     S.fb_iter = 0; S.relres_prev = 1.0;
     S.inner_tol = INNER_REL;
     S.t_start = globaltimer();
     S.t_done = 0;
-    for (int c = 0; c < 8; ++c) S.counter[c] = 0;
+    for (int c = 0; c < 12; ++c) S.counter[c] = 0;
+}
+
+// ---- the solve loop's conditions, set on the device (conditional graph nodes)
+// WHILE over cycles: another restart cycle (CG: chunk) while an instance is
+// unfinished and the cycle limit is not reached.  At the end of a cycle
+// (end_of_cycle = 1) it also counts the cycle, the nk kernels of the loop
+// body outside the iteration slots and, when profiling, the restart's time.
+__global__ void k_loop_cond(SolveCtl* ctl, const int* ndone, int ninst, cudaGraphConditionalHandle hw,
+                            unsigned long long nk, int end_of_cycle, int prof) {
+    if (end_of_cycle) {
+        ctl->cycles += 1;
+        ctl->kernels += nk;
+        if (prof) ctl->t_restart += ctl->stamp[ST_REST1] - ctl->stamp[ST_REST0];
+    }
+    cudaGraphSetConditional(hw, (*ndone < ninst && ctl->cycles < ctl->max_cycles) ? 1u : 0u);
+}
+
+// IF over one iteration slot: the next slot runs while some instance still
+// iterates in this cycle.  After a slot (nk > 0: its kernel count) it also
+// counts the slot and, when profiling, adds the slot's section times.
+__global__ void k_slot_cond(const KState* st, int ninst, cudaGraphConditionalHandle hi, SolveCtl* ctl,
+                            unsigned long long nk, int prof) {
+    int a = 0;
+    for (int i = threadIdx.x; i < ninst; i += blockDim.x) a |= st[i].active;
+    a = __syncthreads_or(a);
+    if (threadIdx.x != 0) return;
+    cudaGraphSetConditional(hi, a ? 1u : 0u);
+    if (nk) {
+        ctl->kernels += nk;
+        ctl->slots += 1;
+        if (prof) {
+            const unsigned long long* t = ctl->stamp;
+            ctl->t_prec += t[ST_APPLY0] - t[ST_PRE0];
+            ctl->t_conv += t[ST_CONV1] - t[ST_CONV0];
+            ctl->t_apply += t[ST_APPLY1] - t[ST_APPLY0];
+            ctl->t_arn += t[ST_ARN1] - t[ST_APPLY1];
+        }
+    }
 }
 
 // sum of b^2 -> bnorm ; kind: FP64 batched vector
@@ -312,11 +355,19 @@ __global__ void __launch_bounds__(MD_TB) k_dots(const Seg* __restrict__ seg, con
 
 // W -= sum_i coef_i V_i ; ||W||^2, ||W_3D||^2.  As k_dots: the basis length is
 // bounded by JB at compile time so the loads of all V_i are issued together.
+// In the first pass the same trip also forms the dots (W_new, V_i) of the
+// second, re-orthogonalising pass from the V_i already in registers, so that
+// pass needs no separate multi-dot over the basis: when ||W|| dropped below
+// half of its length before the pass (the CGS2 condition), the last block
+// adds them to column j of H and makes them the second pass's coefficients;
+// otherwise it ends the step (H[j+1][j], sig_{j+1}).  The second pass
+// (pass = 1, only where the condition fired) applies them and ends the step.
 template <int JB>
 __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                   const long long* __restrict__ off, const InstDesc* __restrict__ D,
                                                   float* V, long long total, int j, int pass, KState* st, double* part) {
-    __shared__ double sh[32 * 4];
+    constexpr int NW = MD_TB / 32;
+    __shared__ double sh[(JB + 2) * NW];
     __shared__ float sc[JB];
     const Seg sg = seg[blockIdx.x];
     KState& S = st[sg.inst];
@@ -328,7 +379,11 @@ __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, c
     float* W = V + (long long)(j + 1) * total + o;
     const float* V0 = V + o;
     constexpr int U = JB <= 8 ? 4 : (JB <= 16 ? 2 : 1);
+    const bool dots2 = pass == 0;
     float a = 0.f, a3 = 0.f;
+    float acc[JB];
+#pragma unroll
+    for (int i = 0; i < JB; ++i) acc[i] = 0.f;
     for (int e0 = sg.begin + threadIdx.x; e0 < sg.end; e0 += U * MD_TB) {
         float w[U];
 #pragma unroll
@@ -357,38 +412,84 @@ __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, c
                 if (e < n3) a3 = fmaf(w[u], w[u], a3);
             }
         }
+        if (dots2) {
+            // out-of-range lanes hold w = x = 0 and add nothing
+#pragma unroll
+            for (int i = 0; i < JB; ++i)
+#pragma unroll
+                for (int u = 0; u < U; ++u) acc[i] = fmaf(w[u], x[i][u], acc[i]);
+        }
     }
-    double v[2] = {(double)a, (double)a3};
-    double flag;
-    reduce_values<2>(v, 2, part, blockIdx.x, rng[sg.inst], &S.counter[3], &flag, sh);
-    if (flag == 1.0 && threadIdx.x == 0) {
-        const double wn2 = sh[0];
-        if (pass == 0 && wn2 < 0.25 * S.wn2_before && wn2 > 0.0) {
+    // block sums: slots 0, 1 = ||W||^2, ||W_3D||^2; 2 + i = (W, V_i), i <= j
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cnt = dots2 ? j + 3 : 2;
+    {
+        const double x0 = warp_sum((double)a), x1 = warp_sum((double)a3);
+        if (lane == 0) { sh[warp] = x0; sh[NW + warp] = x1; }
+    }
+    if (dots2) {
+#pragma unroll
+        for (int i = 0; i < JB; ++i) {
+            if (i <= j) {
+                const double x = warp_sum((double)acc[i]);
+                if (lane == 0) sh[(2 + i) * NW + warp] = x;
+            }
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < cnt; r += blockDim.x) {
+        double sum = 0.0;
+        for (int w2 = 0; w2 < NW; ++w2) sum += sh[r * NW + w2];
+        part[(size_t)blockIdx.x * MD_MAXR + r] = sum;
+    }
+    const InstRange rg = rng[sg.inst];
+    if (!last_block_arrive(&S.counter[3], rg.count)) return;
+    __shared__ double tot[2];
+    for (int r = threadIdx.x; r < 2; r += blockDim.x) {
+        double sum = 0.0;
+        for (int b2 = rg.first; b2 < rg.first + rg.count; ++b2) sum += part[(size_t)b2 * MD_MAXR + r];
+        tot[r] = sum;
+    }
+    __syncthreads();
+    const double wn2 = tot[0];
+    if (dots2 && wn2 < 0.25 * S.wn2_before && wn2 > 0.0) {
+        // second pass: its dots are this launch's (W_new, V_i)
+        double* H = S.H + (size_t)j * (MD_KMAX + 1);
+        for (int r = 2 + threadIdx.x; r < cnt; r += blockDim.x) {
+            double sum = 0.0;
+            for (int b2 = rg.first; b2 < rg.first + rg.count; ++b2) sum += part[(size_t)b2 * MD_MAXR + r];
+            const int i = r - 2;
+            H[i] += S.sig[j] * S.sig[i] * sum;
+            S.coef[i] = S.sig[i] * S.sig[i] * sum;
+        }
+        if (threadIdx.x == 0) {
             S.reorth = 1;
             S.wn2_before = wn2;
-        } else {
-            S.reorth = 0;
-            S.H[(size_t)j * (MD_KMAX + 1) + j + 1] = S.sig[j] * sqrt(wn2);
-            S.sig[j + 1] = wn2 > 0.0 ? 1.0 / sqrt(wn2) : 0.0;
-            S.v3n2 = sh[1];
         }
+    } else if (threadIdx.x == 0) {
+        S.reorth = 0;
+        S.H[(size_t)j * (MD_KMAX + 1) + j + 1] = S.sig[j] * sqrt(wn2);
+        S.sig[j + 1] = wn2 > 0.0 ? 1.0 / sqrt(wn2) : 0.0;
+        S.v3n2 = tot[1];
     }
 }
 
-// One Gram-Schmidt pass of Arnoldi step j, with the basis-length bound that
-// covers j + 1 vectors.
+// One Arnoldi step's Gram-Schmidt with the basis-length bound that covers
+// j + 1 vectors: the multi-dot, the update (with the second pass's dots), and
+// the second pass's update where the re-orthogonalisation condition fired.
 template <int JB>
-static void launch_gs_pass(md_batch* B, int j, int pass, cudaStream_t s) {
+static void launch_gs_step(md_batch* B, int j, cudaStream_t s) {
     const Tables& T = B->tabs;
-    k_dots<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, B->total, j, pass, B->st, B->part);
-    k_update<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, B->total, j, pass, B->st,
-                                                 B->part);
+    k_dots<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, B->total, j, 0, B->st, B->part);
+    for (int pass = 0; pass < 2; ++pass)
+        k_update<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, B->total, j, pass,
+                                                     B->st, B->part);
 }
-static void launch_gs(md_batch* B, int j, int pass, cudaStream_t s) {
-    if (j < 8) launch_gs_pass<8>(B, j, pass, s);
-    else if (j < 16) launch_gs_pass<16>(B, j, pass, s);
-    else if (j < 32) launch_gs_pass<32>(B, j, pass, s);
-    else launch_gs_pass<MD_KMAX>(B, j, pass, s);
+static void launch_gs(md_batch* B, int j, cudaStream_t s) {
+    if (j < 8) launch_gs_step<8>(B, j, s);
+    else if (j < 16) launch_gs_step<16>(B, j, s);
+    else if (j < 32) launch_gs_step<32>(B, j, s);
+    else launch_gs_step<MD_KMAX>(B, j, s);
 }
 
 // Givens rotations, residual estimate, cycle exit; one thread per instance
@@ -475,26 +576,72 @@ __global__ void __launch_bounds__(MD_TB) k_jacobi(const Seg* __restrict__ seg, c
     for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) z[o + e] = dinv[e] * v[o + e];
 }
 
-// Tree LDL^T solve in place on y (length n1, shared memory): forward sweep
-// leaves-to-root, diagonal scaling, backward sweep root-to-leaves.
-__device__ inline void tree_solve_smem(float* y, const float* sl, const float* sdi, const int* sord, const int* spar,
-                                       int n1) {
-    if (threadIdx.x == 0) {
-        for (int idx = 0; idx < n1; ++idx) {
-            const int i = sord[idx], p = spar[i];
-            if (p >= 0) y[p] -= sl[i] * y[i];
-        }
+// Shared memory of the tree kernels for n1 1D nodes: y, the factor l and
+// 1/d (floats), the parents and the level schedule (ints): 10 n1 + 3 words.
+__host__ __device__ inline size_t tree_smem_bytes(int n1) { return (10 * (size_t)n1 + 3) * 4; }
+
+struct TreeSm {
+    float *y, *sl, *sdi;
+    int *spar, *lv_up, *ch_ptr, *ch_idx, *lv_dn, *lvu_ptr, *lvd_ptr;
+};
+
+// Carve the tree arrays out of `raw` and copy the factor and its schedule in.
+__device__ inline TreeSm tree_load(unsigned char* raw, const InstDesc& d) {
+    const int n1 = d.n1;
+    TreeSm t;
+    t.y = reinterpret_cast<float*>(raw);
+    t.sl = t.y + n1;
+    t.sdi = t.sl + n1;
+    t.spar = reinterpret_cast<int*>(t.sdi + n1);
+    t.lv_up = t.spar + n1;
+    t.ch_ptr = t.lv_up + n1;
+    t.ch_idx = t.ch_ptr + n1 + 1;
+    t.lv_dn = t.ch_idx + n1;
+    t.lvu_ptr = t.lv_dn + n1;
+    t.lvd_ptr = t.lvu_ptr + n1 + 1;
+    const int nch = d.ch_ptr[n1];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        t.sl[i] = d.tr_l32[i];
+        t.sdi[i] = d.tr_dinv32[i];
+        t.spar[i] = d.tr_parent[i];
+        t.lv_up[i] = d.lv_up[i];
+        t.lv_dn[i] = d.lv_dn[i];
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) y[i] *= sdi[i];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int idx = n1 - 1; idx >= 0; --idx) {
-            const int i = sord[idx], p = spar[i];
-            if (p >= 0) y[i] -= sl[i] * y[p];
+    for (int i = threadIdx.x; i <= n1; i += blockDim.x) t.ch_ptr[i] = d.ch_ptr[i];
+    for (int i = threadIdx.x; i < nch; i += blockDim.x) t.ch_idx[i] = d.ch_idx[i];
+    for (int i = threadIdx.x; i <= d.nlvu; i += blockDim.x) t.lvu_ptr[i] = d.lvu_ptr[i];
+    for (int i = threadIdx.x; i <= d.nlvd; i += blockDim.x) t.lvd_ptr[i] = d.lvd_ptr[i];
+    return t;
+}
+
+// Tree LDL^T solve in place on t.y (length n1, shared memory), level by
+// level so that the whole block works on every sweep: forward (leaves to
+// roots) by height, each node taking y_i -= sum over its children c of
+// l_c y_c once all of them are final; the diagonal scaling; backward (roots
+// to leaves) by depth, y_i -= l_i y_parent(i).  The caller synchronises the
+// block after writing y.
+__device__ inline void tree_solve_levels(const InstDesc& d, const TreeSm& t) {
+    for (int h = 0; h < d.nlvu; ++h) {
+        for (int k = t.lvu_ptr[h] + threadIdx.x; k < t.lvu_ptr[h + 1]; k += blockDim.x) {
+            const int i = t.lv_up[k];
+            float acc = t.y[i];
+            for (int c = t.ch_ptr[i]; c < t.ch_ptr[i + 1]; ++c) {
+                const int ch = t.ch_idx[c];
+                acc -= t.sl[ch] * t.y[ch];
+            }
+            t.y[i] = acc;
         }
+        __syncthreads();
     }
+    for (int i = threadIdx.x; i < d.n1; i += blockDim.x) t.y[i] *= t.sdi[i];
     __syncthreads();
+    for (int k = 1; k < d.nlvd; ++k) {
+        for (int e = t.lvd_ptr[k] + threadIdx.x; e < t.lvd_ptr[k + 1]; e += blockDim.x) {
+            const int i = t.lv_dn[e];
+            t.y[i] -= t.sl[i] * t.y[t.spar[i]];
+        }
+        __syncthreads();
+    }
 }
 
 // Lower block order: the network input scale is s = ||v0|| (no lifted 1D part).
@@ -507,9 +654,26 @@ __global__ void k_lower_setup(KState* st, int ninst) {
     S.s = S.v3n2 > 0.0 ? sqrt(S.v3n2) : 0.0;
 }
 
+// Lower block order, the averaging of the network's output at the quadrature
+// points, t_q = (Pi z0)(q), into the instance's t scratch: one thread per
+// point over the whole batch (the quadrature-point table of the apply).
+__global__ void __launch_bounds__(MD_TB) k_gather_z0(const InstDesc* __restrict__ D, const Seg* __restrict__ seg,
+                                                     const long long* __restrict__ off, const float* __restrict__ z,
+                                                     const KState* st) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const InstDesc& d = D[sg.inst];
+    const float* z0 = z + off[sg.inst];
+    for (int q = sg.begin + threadIdx.x; q < sg.end; q += blockDim.x) {
+        float a = 0.f;
+        for (int jj = d.pi_ptr[q]; jj < d.pi_ptr[q + 1]; ++jj) a += d.pi_v32[jj] * z0[d.pi_col[jj]];
+        d.t32[q] = a;
+    }
+}
+
 // Lower block order, 1D part after the network: z1 = B11^{-1} (v1 + beta Psi^T W Pi z0),
-// i.e. v1 minus the 1-0 block of A applied to z0 (Pi at the quadrature
-// points in shared memory, then the Psi^T W rows, then the tree solve).
+// i.e. v1 minus the 1-0 block of A applied to z0 (Pi z0 from k_gather_z0,
+// then the Psi^T W rows, then the tree solve in shared memory).
 __global__ void __launch_bounds__(TREE_TB) k_lower_1d(const InstDesc* __restrict__ D, const long long* __restrict__ off,
                                                       const float* __restrict__ v, float* z, const KState* st) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -517,27 +681,11 @@ __global__ void __launch_bounds__(TREE_TB) k_lower_1d(const InstDesc* __restrict
     const KState& S = st[inst];
     if (!S.active || S.fallback) return;
     const InstDesc& d = D[inst];
-    const int n1 = d.n1, nq = d.nq;
-    float* y = reinterpret_cast<float*>(smraw);
-    float* sl = y + n1;
-    float* sdi = sl + n1;
-    int* sord = reinterpret_cast<int*>(sdi + n1);
-    int* spar = sord + n1;
-    float* t = reinterpret_cast<float*>(spar + n1);
+    const int n1 = d.n1;
+    const TreeSm tr = tree_load(smraw, d);
+    float* y = tr.y;
+    const float* t = d.t32;  // (Pi z0)(q), k_gather_z0
     const long long o = off[inst];
-    const float* z0 = z + o;
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-        float a = 0.f;
-        for (int jj = d.pi_ptr[q]; jj < d.pi_ptr[q + 1]; ++jj) a += d.pi_v32[jj] * z0[d.pi_col[jj]];
-        t[q] = a;
-    }
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
-        sl[i] = d.tr_l32[i];
-        sdi[i] = d.tr_dinv32[i];
-        sord[i] = d.tr_order[i];
-        spar[i] = d.tr_parent[i];
-    }
-    __syncthreads();
     const float beta = (float)d.beta;
     const float* v1 = v + o + d.n3;
     for (int i = threadIdx.x; i < n1; i += blockDim.x) {
@@ -546,68 +694,93 @@ __global__ void __launch_bounds__(TREE_TB) k_lower_1d(const InstDesc* __restrict
         y[i] = v1[i] + beta * a;
     }
     __syncthreads();
-    tree_solve_smem(y, sl, sdi, sord, spar, n1);
+    tree_solve_levels(d, tr);
     float* z1 = z + o + d.n3;
     for (int i = threadIdx.x; i < n1; i += blockDim.x) z1[i] = y[i];
 }
 
-// 1D block solve z1 = B11^{-1} v1 (tree LDL^T sweeps in shared memory), the
-// lift l = beta Pi^T W Psi z1 on the touched grid nodes, and the input norm
-// s = ||v0 + l|| from ||v0||^2 (st.v3n2) and the touched-node correction.
-__global__ void __launch_bounds__(TREE_TB) k_tree_lift(const InstDesc* __restrict__ D, const long long* __restrict__ off,
-                                                   const float* __restrict__ v, float* z, KState* st) {
+// 1D block solve z1 = B11^{-1} v1 (tree LDL^T sweeps in shared memory), one
+// block per instance.  It also sets the network's input scale to
+// s = ||v0||, which k_lift then corrects for the lifted part.
+__global__ void __launch_bounds__(TREE_TB) k_tree_1d(const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                                                 const float* __restrict__ v, float* z, KState* st) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double sh[32];
     const int inst = blockIdx.x;
     KState& S = st[inst];
     if (!S.active || S.fallback) return;
     const InstDesc& d = D[inst];
     const int n1 = d.n1;
-    float* y = reinterpret_cast<float*>(smraw);
-    float* sl = y + n1;
-    float* sdi = sl + n1;
-    int* sord = reinterpret_cast<int*>(sdi + n1);
-    int* spar = sord + n1;
+    const TreeSm tr = tree_load(smraw, d);
+    float* y = tr.y;
     const long long o = off[inst];
     const float* v1 = v + o + d.n3;
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
-        y[i] = v1[i];
-        sl[i] = d.tr_l32[i];
-        sdi[i] = d.tr_dinv32[i];
-        sord[i] = d.tr_order[i];
-        spar[i] = d.tr_parent[i];
-    }
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) y[i] = v1[i];
     __syncthreads();
-    tree_solve_smem(y, sl, sdi, sord, spar, n1);
+    tree_solve_levels(d, tr);
     float* z1 = z + o + d.n3;
     for (int i = threadIdx.x; i < n1; i += blockDim.x) z1[i] = y[i];
-    const float beta = (float)d.beta;
+    if (threadIdx.x == 0) {
+        S.s2_touch = 0.0;
+        S.s = S.v3n2 > 0.0 ? sqrt(S.v3n2) : 0.0;
+    }
+}
+
+// The lift l = beta Pi^T W Psi z1 on the grid nodes the averaging reaches
+// (z1 in z's 1D part), one thread per node over the whole batch (the
+// touched-node table), into the instance's lift buffers; and the network's
+// input scale s = ||v0 + l||: ||v0||^2 (st.v3n2) plus sum (2 v0 l + l^2)
+// over those nodes, the last block of an instance storing s.
+__global__ void __launch_bounds__(MD_TB) k_lift(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
+                                                const long long* __restrict__ off, const InstDesc* __restrict__ D,
+                                                const float* __restrict__ v, const float* __restrict__ z, KState* st,
+                                                double* part) {
+    __shared__ double sh[32 * 4];
+    const Seg sg = seg[blockIdx.x];
+    KState& S = st[sg.inst];
+    if (!S.active || S.fallback) return;
+    const InstDesc& d = D[sg.inst];
+    const long long o = off[sg.inst];
+    const float* z1 = z + o + d.n3;
     const float* v0 = v + o;
-    double part = 0.0;
-    for (int idx = threadIdx.x; idx < d.ntouch; idx += blockDim.x) {
+    const float beta = (float)d.beta;
+    double vals[1] = {0.0};
+    for (int idx = sg.begin + threadIdx.x; idx < sg.end; idx += blockDim.x) {
         float acc = 0.f;
         for (int jj = d.tn_ptr[idx]; jj < d.tn_ptr[idx + 1]; ++jj) {
             const int q = d.tn_q[jj];
-            acc += d.tn_v32[jj] * (d.psa32[q] * y[d.qa[q]] + d.psb32[q] * y[d.qb[q]]);
+            acc += d.tn_v32[jj] * (d.psa32[q] * z1[d.qa[q]] + d.psb32[q] * z1[d.qb[q]]);
         }
         const float l = beta * acc;
         const int node = d.tn_node[idx];
         d.ltouch32[idx] = l;
         d.lift32[node] = l;
         const float vv = v0[node];
-        part += (double)(2.f * vv * l + l * l);
+        vals[0] += (double)(2.f * vv * l + l * l);
     }
-    double x = warp_sum(part);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-        S.s2_touch = s;
-        const double s2 = S.v3n2 + s;
+    double flag;
+    reduce_values<1>(vals, 1, part, blockIdx.x, rng[sg.inst], &S.counter[8], &flag, sh);
+    if (flag == 1.0 && threadIdx.x == 0) {
+        S.s2_touch = sh[0];
+        const double s2 = S.v3n2 + sh[0];
         S.s = s2 > 0.0 ? sqrt(s2) : 0.0;
     }
 }
+
+// The 1D part of the block preconditioner in the upper order (z1 and the
+// lift with the input scale) and in the lower order (z1 from the network's
+// z0), for every instance that runs the network.
+static md_status launch_upper_1d(const Tables& T, const InstDesc* d, const long long* off, int ninst, int max_n1,
+                                 const float* v, float* z, KState* st, double* part, cudaStream_t s) {
+    k_tree_1d<<<ninst, TREE_TB, tree_smem_bytes(max_n1), s>>>(d, off, v, z, st);
+    MD_CHECK_LAUNCH();
+    if (T.touch.nblocks > 0) {
+        k_lift<<<T.touch.nblocks, MD_TB, 0, s>>>(T.touch.seg, T.touch.range, off, d, v, z, st, part);
+        MD_CHECK_LAUNCH();
+    }
+    return MD_OK;
+}
+
+static md_status launch_lower_1d(md_batch* B, const float* v, float* z, cudaStream_t s);
 
 // ---- Jacobi pre- and post-smoothing around the 3D solve (Section 5, 'Effect of
 // pre- and post-smoothing') --------------------------------------------------------
@@ -1174,19 +1347,26 @@ __global__ void __launch_bounds__(MD_TB) k_cg_final(const Seg* __restrict__ seg,
 
 // ---------------------------------------------------------------------------
 // host side
+static md_status launch_lower_1d(md_batch* B, const float* v, float* z, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    k_gather_z0<<<T.apply_a.nblocks, MD_TB, 0, s>>>(B->d, T.apply_a.seg, B->off, z, B->st);
+    MD_CHECK_LAUNCH();
+    k_lower_1d<<<B->ninst, TREE_TB, tree_smem_bytes(B->max_n1), s>>>(B->d, B->off, v, z, B->st);
+    MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
 // The network preconditioner with smoothing (B->smooth_nu > 0):
 //   x = S_J(C, b0, 0, nu);  x += N(b0 - C x);  z0 = S_J(C, b0, x, nu)
 // tmp: a whole-length scratch vector (the apply output and the network's
 // input and output).
 static md_status launch_precond_smoothed(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, float* tmp,
-                                         cudaStream_t s, cudaEvent_t e_conv0, cudaEvent_t e_conv1) {
+                                         cudaStream_t s, unsigned long long* e_conv0, unsigned long long* e_conv1) {
     const Tables& T = B->tabs;
-    const size_t smem = (size_t)B->max_n1 * 20;
     const bool lower = B->prec_order == 1;
     const float omega = B->smooth_omega;
     if (!lower) {
-        k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
-        MD_CHECK_LAUNCH();
+        MD_TRY(launch_upper_1d(T, B->d, B->off, B->ninst, B->max_n1, vin, zout, B->st, B->part, s));
     }
     k_smooth_first<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, omega, !lower);
     MD_CHECK_LAUNCH();
@@ -1208,8 +1388,7 @@ static md_status launch_precond_smoothed(md_batch* B, const md_cnn* cnn, const f
     MD_CHECK_LAUNCH();
     for (int i = 0; i < B->smooth_nu; ++i) MD_TRY(sweep());
     if (lower) {
-        k_lower_1d<<<B->ninst, TREE_TB, smem + (size_t)B->max_nq * 4, s>>>(B->d, B->off, vin, zout, B->st);
-        MD_CHECK_LAUNCH();
+        MD_TRY(launch_lower_1d(B, vin, zout, s));
     }
     return MD_OK;
 }
@@ -1218,16 +1397,15 @@ static md_status launch_precond_smoothed(md_batch* B, const md_cnn* cnn, const f
 // steps on C (kernels above).  The conv events bracket the first network
 // application only.
 static md_status launch_precond_inner(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, cudaStream_t s,
-                                      cudaEvent_t e_conv0, cudaEvent_t e_conv1) {
+                                      unsigned long long* e_conv0, unsigned long long* e_conv1) {
     const Tables& T = B->tabs;
-    const size_t smem = (size_t)B->max_n1 * 20;
     const bool lower = B->prec_order == 1;
     const long long tot = B->total;
     const int m = B->inner_m;
     if (lower) {
         k_lower_setup<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
     } else {
-        k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
+        MD_TRY(launch_upper_1d(T, B->d, B->off, B->ninst, B->max_n1, vin, zout, B->st, B->part, s));
     }
     MD_CHECK_LAUNCH();
     MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, B->iZ, s, !lower));
@@ -1258,20 +1436,20 @@ static md_status launch_precond_inner(md_batch* B, const md_cnn* cnn, const floa
     k_inner_combine<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->off, B->iZ, tot, zout, B->st, m);
     MD_CHECK_LAUNCH();
     if (lower) {
-        k_lower_1d<<<B->ninst, TREE_TB, smem + (size_t)B->max_nq * 4, s>>>(B->d, B->off, vin, zout, B->st);
-        MD_CHECK_LAUNCH();
+        MD_TRY(launch_lower_1d(B, vin, zout, s));
     }
     return MD_OK;
 }
 
 static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, float* tmp,
-                                cudaStream_t s, cudaEvent_t e_conv0 = nullptr, cudaEvent_t e_conv1 = nullptr) {
+                                cudaStream_t s, unsigned long long* e_conv0 = nullptr,
+                                unsigned long long* e_conv1 = nullptr) {
     const Tables& T = B->tabs;
     if (!cnn) {
         k_jacobi<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->d, vin, zout, B->st, 0);
         MD_CHECK_LAUNCH();
-        rec(e_conv0, s);
-        rec(e_conv1, s);
+        stamp(e_conv0, s);
+        stamp(e_conv1, s);
         return MD_OK;
     }
     // instances whose network application broke down continue with Jacobi
@@ -1279,57 +1457,41 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
     MD_CHECK_LAUNCH();
     if (B->inner_m > 0) return launch_precond_inner(B, cnn, vin, zout, s, e_conv0, e_conv1);
     if (B->smooth_nu > 0) return launch_precond_smoothed(B, cnn, vin, zout, tmp, s, e_conv0, e_conv1);
-    const size_t smem = (size_t)B->max_n1 * 20;
     const bool lower = B->prec_order == 1;
     if (lower) {
         k_lower_setup<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
     } else {
-        k_tree_lift<<<B->ninst, TREE_TB, smem, s>>>(B->d, B->off, vin, zout, B->st);
+        MD_TRY(launch_upper_1d(T, B->d, B->off, B->ninst, B->max_n1, vin, zout, B->st, B->part, s));
     }
     MD_CHECK_LAUNCH();
     MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, zout, s, !lower));
     OutIO io{zout, B->off, vin, B->off, B->st, B->d};
     MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
     if (lower) {
-        k_lower_1d<<<B->ninst, TREE_TB, smem + (size_t)B->max_nq * 4, s>>>(B->d, B->off, vin, zout, B->st);
-        MD_CHECK_LAUNCH();
+        MD_TRY(launch_lower_1d(B, vin, zout, s));
     }
     return MD_OK;
 }
 
-// 1 if some instance still iterates in the current restart cycle
-__global__ void k_any_active(const KState* st, int ninst, int* any) {
-    int a = 0;
-    for (int i = threadIdx.x; i < ninst; i += blockDim.x) a |= st[i].active;
-    a = __syncthreads_or(a);
-    if (threadIdx.x == 0) *any = a;
-}
-
-// Iteration slots j in [j0, j1) of a restart cycle.
-static md_status launch_slots(md_batch* B, int j0, int j1, cudaStream_t s) {
+// Iteration slot j of a restart cycle.
+static md_status launch_slot(md_batch* B, int j, cudaStream_t s) {
     const Tables& T = B->tabs;
     const long long tot = B->total;
     const int gb = (B->ninst + 31) / 32;
-    for (int j = j0; j < j1; ++j) {
-        const float* Vj = B->V + (long long)j * tot;
-        float* Zj = B->Z + (long long)j * tot;
-        float* W = B->V + (long long)(j + 1) * tot;
-        rec(ev_at(B, j, EV_PRE0), s);
-        // W (the next basis vector) is the preconditioner's scratch until the apply below fills it
-        MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, W, s,
-                              ev_at(B, j, EV_CONV0), ev_at(B, j, EV_CONV1)));
-        rec(ev_at(B, j, EV_APPLY0), s);
-        MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
-        rec(ev_at(B, j, EV_APPLY1), s);
-        for (int pass = 0; pass < 2; ++pass) {
-            launch_gs(B, j, pass, s);
-        }
-        k_givens<<<gb, 32, 0, s>>>(B->st, B->ninst, j, B->k);
-        MD_CHECK_LAUNCH();
-        rec(ev_at(B, j, EV_ARN1), s);
-    }
-    k_any_active<<<1, 1024, 0, s>>>(B->st, B->ninst, B->d_any);
+    const float* Vj = B->V + (long long)j * tot;
+    float* Zj = B->Z + (long long)j * tot;
+    float* W = B->V + (long long)(j + 1) * tot;
+    stamp(stamp_at(B, ST_PRE0), s);
+    // W (the next basis vector) is the preconditioner's scratch until the apply below fills it
+    MD_TRY(launch_precond(B, B->solver == MD_SOLVER_FGMRES_CNN ? B->cnn : nullptr, Vj, Zj, W, s,
+                          stamp_at(B, ST_CONV0), stamp_at(B, ST_CONV1)));
+    stamp(stamp_at(B, ST_APPLY0), s);
+    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP32, Zj, B->off, W, s, B->st, 1));
+    stamp(stamp_at(B, ST_APPLY1), s);
+    launch_gs(B, j, s);
+    k_givens<<<gb, 32, 0, s>>>(B->st, B->ninst, j, B->k);
     MD_CHECK_LAUNCH();
+    stamp(stamp_at(B, ST_ARN1), s);
     return MD_OK;
 }
 
@@ -1338,7 +1500,7 @@ static md_status launch_restart(md_batch* B, cudaStream_t s) {
     const Tables& T = B->tabs;
     const long long tot = B->total;
     const int gb = (B->ninst + 31) / 32;
-    rec(ev_restart(B, 0), s);
+    stamp(stamp_at(B, ST_REST0), s);
     k_lsq<<<gb, 32, 0, s>>>(B->st, B->ninst);
     k_xupd<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, B->off, B->Z, tot, B->x, B->st);
     MD_CHECK_LAUNCH();
@@ -1346,7 +1508,7 @@ static md_status launch_restart(md_batch* B, cudaStream_t s) {
     k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st, B->part,
                                              B->ndone, B->res, B->k);
     MD_CHECK_LAUNCH();
-    rec(ev_restart(B, 1), s);
+    stamp(stamp_at(B, ST_REST1), s);
     return MD_OK;
 }
 
@@ -1368,73 +1530,162 @@ static md_status launch_cycle_cg(md_batch* B, cudaStream_t s) {
     return MD_OK;
 }
 
-// Capture what `launch` issues on the capture stream into an executable graph.
-template <class F>
-static md_status capture_graph(md_batch* B, F&& launch, cudaGraphExec_t* out, long long* kernels) {
-    cudaGraph_t g;
-    MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
-    md_status st = launch(B->cap);
-    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
-    if (st != MD_OK) { if (e == cudaSuccess) cudaGraphDestroy(g); return st; }
-    MD_CUDA(e);
+// ---- the solve as one graph -------------------------------------------------
+// Kernel nodes of a captured graph (the nodes of its conditional bodies are
+// counted by the device when those bodies run).
+static long long kernel_nodes(cudaGraph_t g) {
     size_t nn = 0;
     cudaGraphGetNodes(g, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
     if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
-    *kernels = 0;
+    long long k = 0;
     for (auto nd : nodes) {
         cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++*kernels;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
     }
-    e = cudaGraphInstantiate(out, g, 0);
-    cudaGraphDestroy(g);
+    return k;
+}
+
+// Append a conditional node (IF or WHILE on handle h) to the graph being
+// captured on stream cs, after everything captured so far; *body receives
+// its body graph, to be filled by a capture of its own.
+static md_status add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                 cudaGraph_t* body) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    MD_CUDA(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, &deps, &edges, &nd));
+    if (status != cudaStreamCaptureStatusActive) { md_set_error("solve graph: capture not active"); return MD_ERR_CUDA; }
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = h;
+    prm.conditional.type = type;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    MD_CUDA(cudaGraphAddNode(&node, g, deps, edges, nd, &prm));
+    *body = prm.conditional.phGraph_out[0];
+    MD_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return MD_OK;
+}
+
+// The handle of a conditional node in the graph being captured on cs, reset
+// to 0 at every launch of the graph.
+static md_status capture_handle(cudaStream_t cs, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t g = nullptr;
+    MD_CUDA(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
+    MD_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault));
+    return MD_OK;
+}
+
+// Fill `body` by capturing what `launch` issues on stream cs.
+template <class F>
+static md_status capture_into(cudaStream_t cs, cudaGraph_t body, F&& launch) {
+    MD_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    md_status st = launch(cs);
+    cudaGraph_t out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &out);
+    if (st != MD_OK) return st;
     MD_CUDA(e);
     return MD_OK;
 }
 
+// The solve graph.  Set-up: state from the control block, ||b||, r = b - A x
+// (FP64), the first cycle's basis (CG: its first direction); then
+//   WHILE (an instance is unfinished and cycles < limit) {
+//     FGMRES: slot condition; for j < k: IF (an instance iterates) { slot j;
+//             slot condition }; restart (x += Z y, FP64 residual)
+//     CG:     a chunk of CG_CHUNK iterations and the true residual of the
+//             instances that stopped
+//     loop condition
+//   }
+// so a solve is one graph launch and the host waits once, at the end.
+static md_status capture_solve(md_batch* B, cudaStream_t s) {
+    const Tables& T = B->tabs;
+    const int gb = (B->ninst + 31) / 32;
+    const int prof = B->profiling ? 1 : 0;
+    k_init_state<<<gb, 32, 0, s>>>(B->st, B->ninst, B->ctl, B->ndone);
+    k_norm_b<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->b, B->st, B->part);
+    MD_CHECK_LAUNCH();
+    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
+    if (B->solver == MD_SOLVER_CG_JACOBI) {
+        k_cg_init<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->r64, B->p64,
+                                                   B->st, B->part, B->ndone, B->res);
+    } else {
+        k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st,
+                                                 B->part, B->ndone, B->res, B->k);
+    }
+    MD_CHECK_LAUNCH();
+    cudaGraphConditionalHandle hw;
+    MD_TRY(capture_handle(s, &hw));
+    k_loop_cond<<<1, 1, 0, s>>>(B->ctl, B->ndone, B->ninst, hw, 0ULL, 0, 0);
+    MD_CHECK_LAUNCH();
+    cudaGraph_t loop = nullptr;
+    MD_TRY(add_conditional(s, hw, cudaGraphCondTypeWhile, &loop));
+    return capture_into(B->cap_body, loop, [&](cudaStream_t sb) -> md_status {
+        if (B->solver == MD_SOLVER_CG_JACOBI) {
+            MD_TRY(launch_cycle_cg(B, sb));
+        } else {
+            cudaGraphConditionalHandle hi;
+            MD_TRY(capture_handle(sb, &hi));
+            k_slot_cond<<<1, 1024, 0, sb>>>(B->st, B->ninst, hi, B->ctl, 0ULL, 0);
+            MD_CHECK_LAUNCH();
+            for (int j = 0; j < B->k; ++j) {
+                cudaGraph_t slot = nullptr;
+                MD_TRY(add_conditional(sb, hi, cudaGraphCondTypeIf, &slot));
+                MD_TRY(capture_into(B->cap_slot, slot, [&](cudaStream_t ss) -> md_status {
+                    MD_TRY(launch_slot(B, j, ss));
+                    // the node count of this body, itself included, is known
+                    // only after capture: its kernels are the ones captured so
+                    // far plus this one
+                    cudaStreamCaptureStatus status;
+                    cudaGraph_t g = nullptr;
+                    MD_CUDA(cudaStreamGetCaptureInfo(ss, &status, nullptr, &g, nullptr, nullptr, nullptr));
+                    const unsigned long long nk = (unsigned long long)kernel_nodes(g) + 1;
+                    k_slot_cond<<<1, 1024, 0, ss>>>(B->st, B->ninst, hi, B->ctl, nk, prof);
+                    MD_CHECK_LAUNCH();
+                    return MD_OK;
+                }));
+            }
+            MD_TRY(launch_restart(B, sb));
+        }
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        MD_CUDA(cudaStreamGetCaptureInfo(sb, &status, nullptr, &g, nullptr, nullptr, nullptr));
+        const unsigned long long nk = (unsigned long long)kernel_nodes(g) + 1;
+        k_loop_cond<<<1, 1, 0, sb>>>(B->ctl, B->ndone, B->ninst, hw, nk, 1, prof);
+        MD_CHECK_LAUNCH();
+        return MD_OK;
+    });
+}
+
 static void destroy_graphs(md_batch* B) {
-    if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
-    for (auto g : B->parts) cudaGraphExecDestroy(g);
-    B->parts.clear();
-    B->part_end.clear();
-    B->part_kernels.clear();
-    if (B->restart_graph) { cudaGraphExecDestroy(B->restart_graph); B->restart_graph = nullptr; }
+    if (B->solve_graph) { cudaGraphExecDestroy(B->solve_graph); B->solve_graph = nullptr; }
 }
 
 static md_status build_graph(md_batch* B) {
     const int engine = B->cnn ? B->cnn->engine : 0;
     const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
-    const bool have = B->solver == MD_SOLVER_CG_JACOBI ? B->graph != nullptr : B->restart_graph != nullptr;
-    if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
+    if (B->solve_graph && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
         B->graph_prec_order == B->prec_order && B->graph_smooth_nu == B->smooth_nu &&
         B->graph_smooth_omega == B->smooth_omega && B->graph_inner_m == B->inner_m)
         return MD_OK;
     destroy_graphs(B);
-    if (B->profiling && B->ev.empty()) {
-        B->ev.resize((size_t)B->k * EV_PER_J + 2);
-        for (auto& e : B->ev) MD_CUDA(cudaEventCreate(&e));
+    cudaGraph_t g = nullptr;
+    MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+    md_status st = capture_solve(B, B->cap);
+    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+    if (st != MD_OK) {
+        if (e == cudaSuccess && g) cudaGraphDestroy(g);
+        return st;
     }
-    if (B->solver == MD_SOLVER_CG_JACOBI) {
-        MD_TRY(capture_graph(B, [&](cudaStream_t s) { return launch_cycle_cg(B, s); }, &B->graph, &B->graph_kernels));
-    } else {
-        // slot parts [0, 8), [8, 16), [16, k): a batch that converges early in a
-        // cycle skips the empty slots of the later parts
-        const int bounds[] = {8, 16, B->k};
-        int j0 = 0;
-        for (int b : bounds) {
-            const int j1 = std::min(b, B->k);
-            if (j1 <= j0) continue;
-            cudaGraphExec_t gx = nullptr;
-            long long nk = 0;
-            MD_TRY(capture_graph(B, [&](cudaStream_t s) { return launch_slots(B, j0, j1, s); }, &gx, &nk));
-            B->parts.push_back(gx);
-            B->part_end.push_back(j1);
-            B->part_kernels.push_back(nk);
-            j0 = j1;
-        }
-        MD_TRY(capture_graph(B, [&](cudaStream_t s) { return launch_restart(B, s); }, &B->restart_graph,
-                             &B->restart_kernels));
-    }
+    MD_CUDA(e);
+    B->init_kernels = kernel_nodes(g);
+    e = cudaGraphInstantiate(&B->solve_graph, g, 0);
+    cudaGraphDestroy(g);
+    MD_CUDA(e);
     B->graph_cnn_uid = uid;
     B->graph_prec_order = B->prec_order;
     B->graph_smooth_nu = B->smooth_nu;
@@ -1443,26 +1694,6 @@ static md_status build_graph(md_batch* B) {
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
     return MD_OK;
-}
-
-static void accumulate_events(md_batch* B) {
-    if (!B->profiling || B->solver == MD_SOLVER_CG_JACOBI) return;
-    auto el = [](cudaEvent_t a, cudaEvent_t b) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-            (void)cudaGetLastError();  // a failed read must not surface as a later launch error
-            return 0.0;
-        }
-        return (double)ms;
-    };
-    for (int j = 0; j < B->executed_slots; ++j) {
-        B->stats.prec_ms += el(ev_at(B, j, EV_PRE0), ev_at(B, j, EV_APPLY0));
-        B->stats.conv_hidden_ms += el(ev_at(B, j, EV_CONV0), ev_at(B, j, EV_CONV1));
-        B->stats.apply_ms += el(ev_at(B, j, EV_APPLY0), ev_at(B, j, EV_APPLY1));
-        B->stats.arnoldi_ms += el(ev_at(B, j, EV_APPLY1), ev_at(B, j, EV_ARN1));
-        if (B->solver == MD_SOLVER_FGMRES_CNN) B->stats.conv_hidden_launches += 4;
-    }
-    B->stats.restart_ms += el(ev_restart(B, 0), ev_restart(B, 1));
 }
 
 extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const md_cnn* cnn, md_solver solver,
@@ -1512,29 +1743,35 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
         chk(dev_alloc(&B->allocs, &B->Z, (size_t)B->k * tot));
     }
     chk(dev_alloc(&B->allocs, &B->st, (size_t)n_ops));
-    chk(dev_alloc(&B->allocs, &B->part, (size_t)std::max(B->tabs.vec.nblocks, 1) * MD_MAXR));
+    // partial sums of one block of a reduction kernel (its table: whole vectors, grid
+    // nodes or touched nodes)
+    chk(dev_alloc(&B->allocs, &B->part,
+                  (size_t)std::max({B->tabs.vec.nblocks, B->tabs.n3.nblocks, B->tabs.touch.nblocks, 1}) * MD_MAXR));
     chk(dev_alloc(&B->allocs, &B->ndone, 1));
-    chk(dev_alloc(&B->allocs, &B->d_any, 1));
-    if (st == MD_OK && cudaMallocHost(&B->h_any, sizeof(int)) != cudaSuccess) chk(MD_ERR_OOM);
+    chk(dev_alloc(&B->allocs, &B->ctl, 1));
+    if (st == MD_OK && cudaMallocHost(&B->h_ctl, sizeof(SolveCtl)) != cudaSuccess) chk(MD_ERR_OOM);
     chk(dev_alloc(&B->allocs, &B->res.iters, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->res.net_iters, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->res.relres, (size_t)n_ops));
     chk(dev_alloc(&B->allocs, &B->res.time, (size_t)n_ops));
     if (st == MD_OK && solver == MD_SOLVER_FGMRES_CNN) {
         chk(cnn_work_create(Ns, &B->cw));
-        const size_t smem = (size_t)B->max_n1 * 20;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) chk(md_cuda_status(e, "tree smem", __FILE__, __LINE__));
+        const size_t smem = tree_smem_bytes(B->max_n1);
+        if (smem > 227 * 1024) {
+            md_set_error("md_batch_create: a 1D mesh of %d nodes exceeds the shared memory of the tree solve", B->max_n1);
+            chk(MD_ERR_ARG);
         }
-        if (smem + (size_t)B->max_nq * 4 > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_lower_1d, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(smem + (size_t)B->max_nq * 4));
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_tree_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_lower_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) chk(md_cuda_status(e, "tree smem", __FILE__, __LINE__));
         }
     }
     if (st == MD_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_body, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_slot, cudaStreamNonBlocking);
         if (e != cudaSuccess) chk(md_cuda_status(e, "cudaStreamCreate", __FILE__, __LINE__));
     }
     if (st == MD_OK) {
@@ -1548,10 +1785,11 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
 
 extern "C" void md_batch_destroy(md_batch* B) {
     if (!B) return;
-    for (auto e : B->ev) cudaEventDestroy(e);
     destroy_graphs(B);
-    if (B->h_any) cudaFreeHost(B->h_any);
+    if (B->h_ctl) cudaFreeHost(B->h_ctl);
     if (B->cap) cudaStreamDestroy(B->cap);
+    if (B->cap_body) cudaStreamDestroy(B->cap_body);
+    if (B->cap_slot) cudaStreamDestroy(B->cap_slot);
     cnn_work_destroy(B->cw);
     dev_free_all(&B->allocs);
     delete B;
@@ -1564,48 +1802,29 @@ extern "C" md_status md_batch_offsets(const md_batch* B, long long* offsets) {
 }
 
 static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
-    const Tables& T = B->tabs;
-    const int gb = (B->ninst + 31) / 32;
-    k_init_state<<<gb, 32, 0, s>>>(B->st, B->ninst, tol, maxit, B->ndone);
-    k_norm_b<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->b, B->st, B->part);
-    MD_CHECK_LAUNCH();
-    MD_TRY(launch_apply(T, B->d, B->ninst, MD_FP64, B->x, B->off, B->y64, s, B->st, 2));
-    if (B->solver == MD_SOLVER_CG_JACOBI) {
-        k_cg_init<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->r64, B->p64,
-                                                   B->st, B->part, B->ndone, B->res);
-    } else {
-        k_resid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->b, B->y64, B->V, B->st,
-                                                 B->part, B->ndone, B->res, B->k);
-    }
-    MD_CHECK_LAUNCH();
     MD_TRY(build_graph(B));
     const int per_cycle = B->solver == MD_SOLVER_CG_JACOBI ? CG_CHUNK : B->k;
-    const long long max_cycles = (long long)maxit / per_cycle + 3;
+    SolveCtl& c = *B->h_ctl;
+    memset(&c, 0, sizeof(SolveCtl));
+    c.tol = tol;
+    c.maxit = maxit;
+    c.max_cycles = maxit / per_cycle + 3;
+    MD_CUDA(cudaMemcpyAsync(B->ctl, &c, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
+    MD_CUDA(cudaGraphLaunch(B->solve_graph, s));
     int ndone = 0;
-    B->stats.kernel_launches += 5;
-    for (long long c = 0; c <= max_cycles; ++c) {
-        MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
-        MD_CUDA(cudaStreamSynchronize(s));
-        if (c > 0) accumulate_events(B);
-        if (ndone >= B->ninst) break;
-        if (B->solver == MD_SOLVER_CG_JACOBI) {
-            MD_CUDA(cudaGraphLaunch(B->graph, s));
-            B->stats.kernel_launches += B->graph_kernels;
-        } else {
-            for (size_t p = 0; p < B->parts.size(); ++p) {
-                MD_CUDA(cudaGraphLaunch(B->parts[p], s));
-                B->stats.kernel_launches += B->part_kernels[p];
-                B->executed_slots = B->part_end[p];
-                if (p + 1 < B->parts.size()) {
-                    MD_CUDA(cudaMemcpyAsync(B->h_any, B->d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
-                    MD_CUDA(cudaStreamSynchronize(s));
-                    if (!*B->h_any) break;
-                }
-            }
-            MD_CUDA(cudaGraphLaunch(B->restart_graph, s));
-            B->stats.kernel_launches += B->restart_kernels;
-        }
-        B->stats.cycles += 1;
+    MD_CUDA(cudaMemcpyAsync(&c, B->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaStreamSynchronize(s));
+    B->stats.kernel_launches += B->init_kernels + (long long)c.kernels;
+    B->stats.graph_launches += 1;
+    B->stats.cycles += c.cycles;
+    if (B->profiling && B->solver != MD_SOLVER_CG_JACOBI) {
+        B->stats.prec_ms += c.t_prec * 1e-6;
+        B->stats.conv_hidden_ms += c.t_conv * 1e-6;
+        B->stats.apply_ms += c.t_apply * 1e-6;
+        B->stats.arnoldi_ms += c.t_arn * 1e-6;
+        B->stats.restart_ms += c.t_restart * 1e-6;
+        if (B->solver == MD_SOLVER_FGMRES_CNN) B->stats.conv_hidden_launches += 4 * (long long)c.slots;
     }
     if (B->cw) {
         int err = 0;
@@ -1742,11 +1961,10 @@ md_status launch_prec_input(const Tables& T, const InstDesc* d, const long long*
                             KState* st, int ninst, int max_n1, double* part, cudaStream_t s) {
     k_norm3<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, T.n3.range, off, v, st, part);
     MD_CHECK_LAUNCH();
-    const size_t smem = (size_t)max_n1 * 20;
-    if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_tree_lift<<<ninst, TREE_TB, smem, s>>>(d, off, v, z, st);
-    MD_CHECK_LAUNCH();
-    return MD_OK;
+    const size_t smem = tree_smem_bytes(max_n1);
+    if (smem > 227 * 1024) { md_set_error("training: 1D mesh of %d nodes too large for the tree solve", max_n1); return MD_ERR_ARG; }
+    if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    return launch_upper_1d(T, d, off, ninst, max_n1, v, z, st, part, s);
 }
 
 // Standalone preconditioner application (one instance).
@@ -1767,14 +1985,14 @@ extern "C" md_status md_lift(const md_op* op, const float* r, float* z1, float* 
     cudaStream_t s = (cudaStream_t)stream;
     md_batch* B = nullptr;
     MD_TRY(op_batch(op, MD_SOLVER_FGMRES_JACOBI, 1, nullptr, &B));
-    const size_t smem = (size_t)B->max_n1 * 20;
-    if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_lift, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const size_t smem = tree_smem_bytes(B->max_n1);
+    if (smem > 227 * 1024) { md_set_error("md_lift: 1D mesh of %d nodes too large for the tree solve", B->max_n1); return MD_ERR_ARG; }
+    if (smem > 48 * 1024) MD_CUDA(cudaFuncSetAttribute(k_tree_1d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_lift_setup<<<1, 1, 0, s>>>(B->st);
     // z1 = B11^{-1} r1 into the 1D part of the batch's first Z vector (scratch);
     // l = beta Pi^T W Psi z1 into the operator's lift buffer (zero off the
     // nodes the averaging reaches)
-    k_tree_lift<<<1, TREE_TB, smem, s>>>(B->d, B->off, r, B->Z, B->st);
-    MD_CHECK_LAUNCH();
+    MD_TRY(launch_upper_1d(B->tabs, B->d, B->off, 1, B->max_n1, r, B->Z, B->st, B->part, s));
     const InstDesc& d = B->hdesc[0];
     MD_CUDA(cudaMemcpyAsync(l, d.lift32, sizeof(float) * d.n3, cudaMemcpyDeviceToDevice, s));
     if (z1) MD_CUDA(cudaMemcpyAsync(z1, B->Z + d.n3, sizeof(float) * d.n1, cudaMemcpyDeviceToDevice, s));

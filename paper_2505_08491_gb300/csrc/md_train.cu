@@ -400,7 +400,8 @@ static md_status train_work_create(int B, int N, int max_n1, int max_nq, int max
         chk(dev_alloc(&t->allocs, &t->d, (size_t)B));
         chk(dev_alloc(&t->allocs, &t->st, (size_t)B));
         chk(dev_alloc(&t->allocs, &t->loss, (size_t)B));
-        chk(dev_alloc(&t->allocs, &t->part3, (size_t)B * (n3 / 2048 + 2) * MD_MAXR));
+        // per block of the n3 table (||r0||^2) or of the touched-node table (the lift)
+        chk(dev_alloc(&t->allocs, &t->part3, (size_t)B * (n3 / 256 + 2) * MD_MAXR));
         t->max_n1 = max_n1;
         for (int i = 0; i < B && st == MD_OK; ++i) {
             float *a = nullptr, *b = nullptr, *c = nullptr;

@@ -79,3 +79,39 @@ def test_solve_with_initial_guess_already_converged():
     xd = solvers.direct_solve(p.A, b)
     x, it, rel, ok = op.solve(torch.from_numpy(b).cuda(), x0=torch.from_numpy(xd).cuda(), tol=1e-8)
     assert ok and it == 0
+
+
+def test_batched_solve_is_one_graph_launch():
+    """A batched solve is one launch of its captured graph whatever the number
+    of restart cycles (they run under a conditional WHILE node on the device),
+    and the device-side counts and section times come back with it."""
+    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300.weights import default_network_params
+    insts = [mdgen.workload_instance("tree15_32", i) for i in range(3)]
+    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    b = torch.cat([op.rhs(torch.from_numpy(mdgen.interior_source(w["N"], w["f_seed"])).cuda(), w["g"])
+                   for w, op in zip(insts, ops)])
+    net = Network(default_network_params())
+    for solver, restart in (("fgmres_cnn", 8), ("cg_jacobi", 1)):
+        B = Batch(ops, solver, net if solver == "fgmres_cnn" else None, restart=restart)
+        B.set_profiling(True)
+        x = torch.zeros_like(b)
+        its, rels, ok = B.solve(b, x, tol=1e-8, maxit=20000)
+        assert ok
+        x.zero_()
+        B.reset_stats()
+        its, rels, ok = B.solve(b, x, tol=1e-8, maxit=20000)
+        st = B.stats()
+        assert ok and st["graph_launches"] == 1, st
+        assert st["cycles"] >= (max(its) + restart - 1) // restart if solver == "fgmres_cnn" else st["cycles"] >= 1
+        assert st["kernel_launches"] > 0
+        if solver == "fgmres_cnn":
+            # restart 8 and ~17 iterations: several cycles, every section timed
+            assert st["cycles"] >= 3
+            # four hidden convolutions per iteration slot that ran; at least one
+            # slot per iteration of the slowest instance
+            assert st["conv_hidden_launches"] % 4 == 0 and st["conv_hidden_launches"] >= 4 * max(its)
+            for k in ("prec_ms", "conv_hidden_ms", "apply_ms", "arnoldi_ms", "restart_ms"):
+                assert st[k] > 0, (k, st)
+            assert st["conv_hidden_ms"] < st["prec_ms"]
+        B.close()
