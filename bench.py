@@ -399,6 +399,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra tree15_32 measurement")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven restart cycles instead of one graph launch per solve (for kernel profilers, "
+                         "which cannot profile kernels inside conditional graph nodes)")
     ap.add_argument("--network-only", action="store_true",
                     help="run only the network's forward pass (profiling the convolutions)")
     ap.add_argument("--net-batch", type=int, default=16, help="--network-only: grids per pass")
@@ -455,6 +458,7 @@ def main():
     B.set_prec_order(args.prec_order)
     B.set_smoothing(args.smooth, args.omega)
     B.set_inner_iters(args.inner)
+    B.set_host_loop(args.host_loop)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -592,9 +596,12 @@ def main():
                     "d2h_bytes_per_step": int(x_all.numel() * 8)},
             "gpu_launches": int(stats["kernel_launches"]),
             "launches_per_solve": {"host_graph_launches": stats["graph_launches"] / args.steps,
-                                   "kernels_run": stats["kernel_launches"] / args.steps,
-                                   "note": "each batched solve is one CUDA graph launch; its restart cycles and "
-                                           "iteration slots are conditional nodes decided on the device"},
+                                   "kernels_run": stats["kernel_launches"] / args.steps, "slot_gating": stats["slot_gating"],
+                                   "note": "slot_gating 0/2: each batched solve is one CUDA graph launch, its "
+                                           "restart cycles a conditional WHILE node decided on the device (0: "
+                                           "iteration slots under conditional IF nodes, 2: all slots launched); "
+                                           "3: host-driven cycles (--host-loop)"},
+            "autotuning": B.tuning(),
             "clocks": clk, "cpu_baseline": cpu}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -308,8 +308,17 @@ typedef struct {
     double restart_ms;           /* least squares, x update, FP64 residual */
     long long fallback_instances; /* network solves whose instance switched to Jacobi */
     long long graph_launches;    /* host launches: one graph per md_batch_solve */
+    long long slot_gating;       /* 0: iteration slots under conditional IF nodes; 2: slots always
+                                    launched, their kernels returning for instances out of the cycle;
+                                    3: the host-driven loop of md_batch_set_host_loop */
 } md_batch_stats_t;
 md_status md_batch_set_profiling(md_batch* b, int enable);
+/* enable = 1: solves run as a set-up graph and one graph per restart cycle
+ * (every iteration slot launched), the host reading the count of finished
+ * instances after each cycle; the same kernels as the device-driven solve,
+ * for kernel profilers, which cannot profile the kernels of graphs with
+ * conditional nodes.  0 (default): one graph launch per solve. */
+md_status md_batch_set_host_loop(md_batch* b, int enable);
 /* lower = 1: the network-preconditioned batch uses md_precondition_lower's
  * block order; 0 (default): the paper's upper-triangular order. */
 md_status md_batch_set_prec_order(md_batch* b, int lower);
@@ -324,6 +333,25 @@ md_status md_batch_set_smoothing(md_batch* b, int nu, double omega);
  * application.  Not combined with smoothing (MD_ERR_ARG). */
 md_status md_batch_set_inner_iters(md_batch* b, int m);
 md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
+
+/* Autotuning.  A network- or Jacobi-preconditioned FGMRES batch of at least
+ * 10^6 unknowns times its launch choices on the GPU when it is created and
+ * keeps the fastest: the elements per block of its Krylov vector kernels
+ * (candidates 2048-16384, timed on a Gram-Schmidt step over the whole batch)
+ * and the 128-row tiles per plane step of its tensor-core convolutions (1 or
+ * 2, timed on a forward pass over every grid).  Smaller batches keep the
+ * defaults (8192 elements, 2 tiles; CG batches 2048 elements).
+ * md_batch_tuning reports the choices and the timings (microseconds). */
+typedef struct {
+    int tuned;                   /* 1 if the choices below were timed */
+    int vec_chunk;               /* elements per block of the Krylov vector kernels */
+    int n_vec;
+    int vec_candidates[8];
+    double vec_us[8];            /* one Gram-Schmidt step with each candidate */
+    int conv_tps;                /* 128-row tiles per plane step of the convolutions (0: no network) */
+    double conv_us[2];           /* one forward pass with 1 and 2 tiles per step */
+} md_tuning_t;
+md_status md_batch_tuning(const md_batch* b, md_tuning_t* out);
 md_status md_batch_reset_stats(md_batch* b);
 
 /* md_solve_batched -- one-shot form: create, solve (per-instance device
@@ -360,6 +388,22 @@ md_status md_train(md_cnn* cnn, const md_train_cfg* cfg);
  * MD_CNN_NPARAMS or NULL.  *loss written on return (synchronises s). */
 md_status md_train_loss(const md_cnn* cnn, int count, const md_op* const* ops, const float* const* r,
                         double* loss, float* dparams, md_stream s);
+
+/* md_opt -- AdamW state (FP32 master weights copied from the network, first
+ * and second moments) for training loops driven by the caller, one step per
+ * call with a gradient the caller provides (the mean-loss gradient of
+ * md_train_loss, or its average over processes in data-parallel training,
+ * where every process applies the same step to its copy of the network).
+ * The update is md_train's: m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * w -= lr wd w on weights (not biases), w -= lr m^ / (sqrt(v^) + eps) with
+ * the bias-corrected moments of step t.  grad: device float MD_CNN_NPARAMS.
+ * md_opt_step writes the new weights into cnn (its parameters and BF16
+ * images) and synchronises s; MD_ERR_NAN if a weight became non-finite. */
+typedef struct md_opt md_opt;
+md_status md_opt_create(const md_cnn* cnn, md_opt** out);
+md_status md_opt_step(md_opt* opt, md_cnn* cnn, const float* grad, double lr, double beta1, double beta2,
+                      double eps, double weight_decay, md_stream s);
+void md_opt_destroy(md_opt* opt);
 
 const char* md_last_error(void);
 const char* md_version(void);

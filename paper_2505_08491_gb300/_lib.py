@@ -33,7 +33,13 @@ class MdBatchStats(C.Structure):
     _fields_ = [("kernel_launches", C.c_longlong), ("cycles", C.c_longlong), ("iterations", C.c_longlong),
                 ("precond_nodes", C.c_longlong), ("prec_ms", C.c_double), ("conv_hidden_ms", C.c_double),
                 ("conv_hidden_launches", C.c_longlong), ("apply_ms", C.c_double), ("arnoldi_ms", C.c_double),
-                ("restart_ms", C.c_double), ("fallback_instances", C.c_longlong), ("graph_launches", C.c_longlong)]
+                ("restart_ms", C.c_double), ("fallback_instances", C.c_longlong), ("graph_launches", C.c_longlong),
+                ("slot_gating", C.c_longlong)]
+
+
+class MdTuning(C.Structure):
+    _fields_ = [("tuned", C.c_int), ("vec_chunk", C.c_int), ("n_vec", C.c_int), ("vec_candidates", C.c_int * 8),
+                ("vec_us", C.c_double * 8), ("conv_tps", C.c_int), ("conv_us", C.c_double * 2)]
 
 
 class MdTrainCfg(C.Structure):
@@ -83,12 +89,17 @@ SIGNATURES = {
     "md_batch_solve": (st, [vp, vp, vp, f64, i32, C.POINTER(i32), C.POINTER(f64), vp]),
     "md_batch_times": (st, [vp, C.POINTER(f64)]),
     "md_batch_set_profiling": (st, [vp, i32]),
+    "md_batch_set_host_loop": (st, [vp, i32]),
+    "md_batch_tuning": (st, [vp, C.POINTER(MdTuning)]),
     "md_batch_stats": (st, [vp, C.POINTER(MdBatchStats)]),
     "md_batch_reset_stats": (st, [vp]),
     "md_solve_batched": (st, [i32, C.POINTER(vp), vp, C.POINTER(vp), C.POINTER(vp), f64, i32, i32,
                               C.POINTER(i32), C.POINTER(f64), vp]),
     "md_train": (st, [vp, C.POINTER(MdTrainCfg)]),
     "md_train_loss": (st, [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(f64), vp, vp]),
+    "md_opt_create": (st, [vp, C.POINTER(vp)]),
+    "md_opt_step": (st, [vp, vp, vp, f64, f64, f64, f64, f64, vp]),
+    "md_opt_destroy": (None, [vp]),
     "md_last_error": (C.c_char_p, []),
     "md_version": (C.c_char_p, []),
 }

@@ -290,6 +290,34 @@ def train(net: Network, ops: list, sample_op: list, residuals: list, *, epochs: 
     return list(hist)
 
 
+class Optimizer:
+    """AdamW state for training loops the caller drives (md_opt_*): one step
+    per call with a given gradient (device float32, MD_CNN_NPARAMS)."""
+
+    def __init__(self, net: Network, *, betas=(0.9, 0.999), weight_decay: float = 1e-4, eps: float = 1e-8):
+        h = C.c_void_p()
+        L.check(L.load().md_opt_create(net.handle, C.byref(h)), "md_opt_create")
+        self._h = h
+        self.net = net
+        self.betas, self.weight_decay, self.eps = betas, weight_decay, eps
+
+    def step(self, grad: torch.Tensor, lr: float):
+        L.check(L.load().md_opt_step(self._h, self.net.handle, _ptr(grad, torch.float32, L.MD_CNN_NPARAMS, "grad"),
+                                     float(lr), float(self.betas[0]), float(self.betas[1]), float(self.eps),
+                                     float(self.weight_decay), _stream()), "md_opt_step")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.load().md_opt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Many instances solved together (md_batch_*)."""
 
@@ -350,6 +378,18 @@ class Batch:
 
     def set_profiling(self, enable: bool):
         L.check(L.load().md_batch_set_profiling(self._h, 1 if enable else 0), "md_batch_set_profiling")
+
+    def set_host_loop(self, enable: bool):
+        """Host-driven restart cycles (for kernel profilers); default: one graph launch per solve."""
+        L.check(L.load().md_batch_set_host_loop(self._h, int(bool(enable))), "md_batch_set_host_loop")
+
+    def tuning(self) -> dict:
+        t = L.MdTuning()
+        L.check(L.load().md_batch_tuning(self._h, C.byref(t)), "md_batch_tuning")
+        return {"tuned": bool(t.tuned), "vec_chunk": t.vec_chunk,
+                "vec_us": {int(t.vec_candidates[i]): float(t.vec_us[i]) for i in range(t.n_vec)},
+                "conv_tiles_per_step": t.conv_tps,
+                "conv_us": {1: float(t.conv_us[0]), 2: float(t.conv_us[1])} if t.conv_tps else {}}
 
     def stats(self) -> dict:
         st = L.MdBatchStats()

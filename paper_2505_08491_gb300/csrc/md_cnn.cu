@@ -204,6 +204,7 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     std::vector<InstRange> ranges;
     int pd_max = 0;
     for (int n : Ns) pd_max = std::max(pd_max, n + 3);
+    w->pd_max = pd_max;
     w->tps = 2;
     w->W = tc_window_rows(w->tps, pd_max);
     w->NS = tc_ring_slots(w->W);
@@ -267,6 +268,74 @@ md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out) {
     if (st != MD_OK) { cnn_work_destroy(w); return st; }
     *out = w;
     return MD_OK;
+}
+
+// The plane steps of every instance for `tps` tiles per plane step (columns
+// of tps*126 in-plane rows, each walked over the N+1 planes with grid nodes).
+static void tc_steps(const std::vector<int>& Ns, int tps, std::vector<long long>& steps_i, std::vector<long long>& pre) {
+    steps_i.clear();
+    pre.assign(1, 0);
+    for (int n : Ns) {
+        const long long Pd = n + 3;
+        const long long cols = (Pd * Pd + 126LL * tps - 1) / (126LL * tps);
+        steps_i.push_back(cols * (n + 1));
+        pre.push_back(pre.back() + steps_i.back());
+    }
+}
+
+md_status cnn_work_set_tps(CnnWork* w, int tps) {
+    if (tps != 1 && tps != 2) { md_set_error("tiles per plane step must be 1 or 2"); return MD_ERR_ARG; }
+    const int W = tc_window_rows(tps, w->pd_max), NS = tc_ring_slots(W);
+    if (NS == 0) { md_set_error("grid too large for the tensor-core convolution windows"); return MD_ERR_ARG; }
+    std::vector<long long> steps_i, pre;
+    tc_steps(w->hN, tps, steps_i, pre);
+    MD_TRY(tc_prepare(W, tps));
+    MD_CUDA(cudaMemcpy(w->steps, steps_i.data(), sizeof(long long) * steps_i.size(), cudaMemcpyHostToDevice));
+    MD_CUDA(cudaMemcpy(w->all_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice));
+    w->tps = tps;
+    w->W = W;
+    w->NS = NS;
+    w->ngroups = (int)std::max(1LL, std::min<long long>(w->nsm, pre.back()));
+    return MD_OK;
+}
+
+// Autotuning of the tiles per plane step: a forward pass of the network over
+// every grid of the workspace (raw output into `out` at `off`) timed with
+// each choice; the faster one is kept.  us[0], us[1]: microseconds per pass
+// with 1 and 2 tiles per step.
+md_status cnn_autotune_tps(const md_cnn* c, CnnWork* w, float* out, const long long* off, double* us) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    md_status st = MD_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = MD_ERR_CUDA;
+    OutIO io{out, off, nullptr, nullptr, nullptr, nullptr};
+    int best = 2;
+    double best_us = 1e300;
+    for (int tps = 2; tps >= 1 && st == MD_OK; --tps) {
+        st = cnn_work_set_tps(w, tps);
+        if (st != MD_OK) { us[tps - 1] = -1.0; st = MD_OK; (void)cudaGetLastError(); continue; }
+        st = cnn_forward_layers(c, w, io, CONV_RAW, s);
+        if (st == MD_OK && cudaEventRecord(e0, s) != cudaSuccess) st = MD_ERR_CUDA;
+        for (int r = 0; r < 2 && st == MD_OK; ++r) st = cnn_forward_layers(c, w, io, CONV_RAW, s);
+        if (st == MD_OK && cudaEventRecord(e1, s) != cudaSuccess) st = MD_ERR_CUDA;
+        float ms = 0.f;
+        if (st == MD_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = MD_ERR_CUDA;
+        if (st != MD_OK) break;
+        us[tps - 1] = 1e3 * ms / 2;
+        if (us[tps - 1] < best_us) { best_us = us[tps - 1]; best = tps; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    int err = 0;
+    if (st == MD_OK && cudaMemcpy(&err, w->err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && err) {
+        md_set_error("a convolution timed out while tuning");
+        st = MD_ERR_TIMEOUT;
+    }
+    if (st != MD_OK) return st == MD_ERR_CUDA ? md_cuda_status(cudaGetLastError(), "conv autotune", __FILE__, __LINE__) : st;
+    return cnn_work_set_tps(w, best);
 }
 
 void cnn_work_destroy(CnnWork* w) {

@@ -29,7 +29,7 @@ struct CnnWork {
     int* run_inst = nullptr;
     long long* run_pre = nullptr;
     int* run_count = nullptr;
-    int ngroups = 1, tps = 2, W = 0, NS = 0, nsm = 148;
+    int ngroups = 1, tps = 2, W = 0, NS = 0, nsm = 148, pd_max = 0;
     int* err = nullptr;            // set by a timed-out wait in a conv kernel
     __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
     __nv_bfloat16* a = nullptr;    // 4 chunks
@@ -43,6 +43,11 @@ struct CnnWork {
 
 md_status cnn_work_create(const std::vector<int>& Ns, CnnWork** out);
 void cnn_work_destroy(CnnWork* w);
+// tiles per plane step of the tensor-core convolutions (1 or 2), and its
+// autotuning by timed forward passes (us[0], us[1]: per pass with 1 and 2)
+md_status cnn_work_set_tps(CnnWork* w, int tps);
+struct md_cnn;
+md_status cnn_autotune_tps(const md_cnn* c, CnnWork* w, float* out, const long long* off, double* us);
 
 // Output handling of the last layer.
 enum ConvOut {

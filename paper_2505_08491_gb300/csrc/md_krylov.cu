@@ -74,8 +74,13 @@ struct md_batch {
     cudaStream_t cap = nullptr, cap_body = nullptr, cap_slot = nullptr;  // capture streams
     cudaGraphExec_t solve_graph = nullptr;
     long long init_kernels = 0;          // kernels of the set-up part (the rest are counted on the device)
+    int host_loop = 0;                   // 1: the host-driven loop below instead of solve_graph
+    cudaGraphExec_t init_graph = nullptr, cycle_graph = nullptr;
+    long long cycle_kernels = 0;
     SolveCtl* ctl = nullptr;             // device: limits of this solve, counters, profile sums
     SolveCtl* h_ctl = nullptr;           // pinned host copy
+    int if_mode = -1;                    // slot gating the solve graph uses (capture_solve)
+    md_tuning_t tuning{};                // choices of the autotuner at creation
     int prec_order = 0;                  // 0: block upper-triangular (the paper's), 1: lower
     int graph_prec_order = 0;
     int inner_m = 0;                     // inner FGMRES steps of the 3D block solve (0: one network application)
@@ -187,6 +192,26 @@ __global__ void k_slot_cond(const KState* st, int ninst, cudaGraphConditionalHan
             ctl->t_apply += t[ST_APPLY1] - t[ST_APPLY0];
             ctl->t_arn += t[ST_ARN1] - t[ST_APPLY1];
         }
+    }
+}
+
+// End of a cycle of the host-driven loop: count it and, when profiling, add
+// the restart's time.
+__global__ void k_cycle_count(SolveCtl* ctl, int prof) {
+    ctl->cycles += 1;
+    if (prof) ctl->t_restart += ctl->stamp[ST_REST1] - ctl->stamp[ST_REST0];
+}
+
+// A slot that ran without an IF node (slot gating mode 2): count it and,
+// when profiling, add its section times.
+__global__ void k_slot_count(SolveCtl* ctl, int prof) {
+    ctl->slots += 1;
+    if (prof) {
+        const unsigned long long* t = ctl->stamp;
+        ctl->t_prec += t[ST_APPLY0] - t[ST_PRE0];
+        ctl->t_conv += t[ST_CONV1] - t[ST_CONV0];
+        ctl->t_apply += t[ST_APPLY1] - t[ST_APPLY0];
+        ctl->t_arn += t[ST_ARN1] - t[ST_APPLY1];
     }
 }
 
@@ -1570,13 +1595,15 @@ static md_status add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, 
     return MD_OK;
 }
 
-// The handle of a conditional node in the graph being captured on cs, reset
-// to 0 at every launch of the graph.
-static md_status capture_handle(cudaStream_t cs, cudaGraphConditionalHandle* h) {
+// The handle of a conditional node in the graph being captured on cs.  A
+// top-level graph resets it to 0 at every launch; in a conditional body
+// (top_level = false) it has no launch default, and a kernel of the body sets
+// it before the node that reads it.
+static md_status capture_handle(cudaStream_t cs, cudaGraphConditionalHandle* h, bool top_level) {
     cudaStreamCaptureStatus status;
     cudaGraph_t g = nullptr;
     MD_CUDA(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
-    MD_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault));
+    MD_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, top_level ? cudaGraphCondAssignDefault : 0));
     return MD_OK;
 }
 
@@ -1602,10 +1629,11 @@ static md_status capture_into(cudaStream_t cs, cudaGraph_t body, F&& launch) {
 //     loop condition
 //   }
 // so a solve is one graph launch and the host waits once, at the end.
-static md_status capture_solve(md_batch* B, cudaStream_t s) {
+// Set-up part of a solve: state from the control block, ||b||, r = b - A x
+// (FP64), the first cycle's basis (CG: its first direction).
+static md_status launch_init(md_batch* B, cudaStream_t s) {
     const Tables& T = B->tabs;
     const int gb = (B->ninst + 31) / 32;
-    const int prof = B->profiling ? 1 : 0;
     k_init_state<<<gb, 32, 0, s>>>(B->st, B->ninst, B->ctl, B->ndone);
     k_norm_b<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->b, B->st, B->part);
     MD_CHECK_LAUNCH();
@@ -1618,39 +1646,114 @@ static md_status capture_solve(md_batch* B, cudaStream_t s) {
                                                  B->part, B->ndone, B->res, B->k);
     }
     MD_CHECK_LAUNCH();
+    return MD_OK;
+}
+
+// One cycle with every iteration slot launched (their kernels return at once
+// for instances that left the cycle): the loop body when slots cannot be
+// gated by IF nodes, and the host-driven loop's cycle.
+static md_status launch_cycle_all_slots(md_batch* B, cudaStream_t s) {
+    if (B->solver == MD_SOLVER_CG_JACOBI) return launch_cycle_cg(B, s);
+    const int prof = B->profiling ? 1 : 0;
+    for (int j = 0; j < B->k; ++j) {
+        MD_TRY(launch_slot(B, j, s));
+        k_slot_count<<<1, 1, 0, s>>>(B->ctl, prof);
+        MD_CHECK_LAUNCH();
+    }
+    return launch_restart(B, s);
+}
+
+// Kernel node of `fn` with arguments `args` appended to graph g after `dep`.
+static md_status add_kernel(cudaGraph_t g, cudaGraphNode_t* dep, void* fn, dim3 grid, dim3 block, void** args,
+                            cudaGraphNode_t* out) {
+    cudaKernelNodeParams kp = {};
+    kp.func = fn;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    MD_CUDA(cudaGraphAddKernelNode(out, g, dep, dep ? 1 : 0, &kp));
+    return MD_OK;
+}
+
+// The FGMRES loop body built node by node (slot gating with IF nodes):
+//   slot condition -> IF slot 0 -> ... -> IF slot k-1 -> restart -> loop condition
+// each IF body = slot j and the slot condition for the next.
+static md_status build_loop_body_if(md_batch* B, cudaGraph_t loop, cudaGraphConditionalHandle hw) {
+    const int prof = B->profiling ? 1 : 0;
+    cudaGraphConditionalHandle hi;
+    MD_CUDA(cudaGraphConditionalHandleCreate(&hi, loop, 0, 0));
+    const KState* st = B->st;
+    int ninst = B->ninst;
+    SolveCtl* ctl = B->ctl;
+    unsigned long long nk0 = 0ULL;
+    int prof0 = 0;
+    void* head_args[] = {(void*)&st, (void*)&ninst, (void*)&hi, (void*)&ctl, (void*)&nk0, (void*)&prof0};
+    cudaGraphNode_t prev;
+    MD_TRY(add_kernel(loop, nullptr, (void*)k_slot_cond, dim3(1), dim3(1024), head_args, &prev));
+    for (int j = 0; j < B->k; ++j) {
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = hi;
+        prm.conditional.type = cudaGraphCondTypeIf;
+        prm.conditional.size = 1;
+        cudaGraphNode_t node;
+        MD_CUDA(cudaGraphAddNode(&node, loop, &prev, nullptr, 1, &prm));
+        MD_TRY(capture_into(B->cap_slot, prm.conditional.phGraph_out[0], [&](cudaStream_t ss) -> md_status {
+            MD_TRY(launch_slot(B, j, ss));
+            cudaStreamCaptureStatus status;
+            cudaGraph_t g = nullptr;
+            MD_CUDA(cudaStreamGetCaptureInfo(ss, &status, nullptr, &g, nullptr, nullptr, nullptr));
+            const unsigned long long nk = (unsigned long long)kernel_nodes(g) + 1;
+            k_slot_cond<<<1, 1024, 0, ss>>>(B->st, B->ninst, hi, B->ctl, nk, prof);
+            MD_CHECK_LAUNCH();
+            return MD_OK;
+        }));
+        prev = node;
+    }
+    cudaGraph_t rg = nullptr;
+    MD_CUDA(cudaStreamBeginCapture(B->cap_body, cudaStreamCaptureModeThreadLocal));
+    md_status st2 = launch_restart(B, B->cap_body);
+    cudaError_t e = cudaStreamEndCapture(B->cap_body, &rg);
+    if (st2 != MD_OK) { if (e == cudaSuccess && rg) cudaGraphDestroy(rg); return st2; }
+    MD_CUDA(e);
+    cudaGraphNode_t rnode;
+    e = cudaGraphAddChildGraphNode(&rnode, loop, &prev, 1, rg);
+    const long long nrest = kernel_nodes(rg);
+    cudaGraphDestroy(rg);
+    MD_CUDA(e);
+    const int* ndone = B->ndone;
+    unsigned long long nk = (unsigned long long)(nrest + 2);  // head, restart kernels, tail
+    int one = 1;
+    void* tail_args[] = {(void*)&ctl, (void*)&ndone, (void*)&ninst, (void*)&hw, (void*)&nk, (void*)&one, (void*)&prof};
+    cudaGraphNode_t tail;
+    return add_kernel(loop, &rnode, (void*)k_loop_cond, dim3(1), dim3(1), tail_args, &tail);
+}
+
+// The solve graph: the set-up part, then
+//   WHILE (an instance is unfinished and cycles < limit) {
+//     FGMRES: slot condition; for j < k: IF (an instance iterates) { slot j;
+//             slot condition }; restart (x += Z y, FP64 residual)
+//     CG:     a chunk of CG_CHUNK iterations and the true residual of the
+//             instances that stopped
+//     loop condition
+//   }
+// so a solve is one graph launch and the host waits once, at the end.
+// mode 0: FGMRES slots gated by IF nodes (the loop body built node by node);
+// mode 2: every slot launched in the body (the form to fall back to).
+static md_status capture_solve(md_batch* B, cudaStream_t s, int mode) {
+    const int prof = B->profiling ? 1 : 0;
+    MD_TRY(launch_init(B, s));
     cudaGraphConditionalHandle hw;
-    MD_TRY(capture_handle(s, &hw));
+    MD_TRY(capture_handle(s, &hw, true));
     k_loop_cond<<<1, 1, 0, s>>>(B->ctl, B->ndone, B->ninst, hw, 0ULL, 0, 0);
     MD_CHECK_LAUNCH();
     cudaGraph_t loop = nullptr;
     MD_TRY(add_conditional(s, hw, cudaGraphCondTypeWhile, &loop));
+    if (mode == 0 && B->solver != MD_SOLVER_CG_JACOBI) return build_loop_body_if(B, loop, hw);
     return capture_into(B->cap_body, loop, [&](cudaStream_t sb) -> md_status {
-        if (B->solver == MD_SOLVER_CG_JACOBI) {
-            MD_TRY(launch_cycle_cg(B, sb));
-        } else {
-            cudaGraphConditionalHandle hi;
-            MD_TRY(capture_handle(sb, &hi));
-            k_slot_cond<<<1, 1024, 0, sb>>>(B->st, B->ninst, hi, B->ctl, 0ULL, 0);
-            MD_CHECK_LAUNCH();
-            for (int j = 0; j < B->k; ++j) {
-                cudaGraph_t slot = nullptr;
-                MD_TRY(add_conditional(sb, hi, cudaGraphCondTypeIf, &slot));
-                MD_TRY(capture_into(B->cap_slot, slot, [&](cudaStream_t ss) -> md_status {
-                    MD_TRY(launch_slot(B, j, ss));
-                    // the node count of this body, itself included, is known
-                    // only after capture: its kernels are the ones captured so
-                    // far plus this one
-                    cudaStreamCaptureStatus status;
-                    cudaGraph_t g = nullptr;
-                    MD_CUDA(cudaStreamGetCaptureInfo(ss, &status, nullptr, &g, nullptr, nullptr, nullptr));
-                    const unsigned long long nk = (unsigned long long)kernel_nodes(g) + 1;
-                    k_slot_cond<<<1, 1024, 0, ss>>>(B->st, B->ninst, hi, B->ctl, nk, prof);
-                    MD_CHECK_LAUNCH();
-                    return MD_OK;
-                }));
-            }
-            MD_TRY(launch_restart(B, sb));
-        }
+        MD_TRY(launch_cycle_all_slots(B, sb));
         cudaStreamCaptureStatus status;
         cudaGraph_t g = nullptr;
         MD_CUDA(cudaStreamGetCaptureInfo(sb, &status, nullptr, &g, nullptr, nullptr, nullptr));
@@ -1663,24 +1766,81 @@ static md_status capture_solve(md_batch* B, cudaStream_t s) {
 
 static void destroy_graphs(md_batch* B) {
     if (B->solve_graph) { cudaGraphExecDestroy(B->solve_graph); B->solve_graph = nullptr; }
+    if (B->init_graph) { cudaGraphExecDestroy(B->init_graph); B->init_graph = nullptr; }
+    if (B->cycle_graph) { cudaGraphExecDestroy(B->cycle_graph); B->cycle_graph = nullptr; }
+}
+
+// Capture what `launch` issues on stream cs into an executable graph.
+template <class F>
+static md_status capture_exec(cudaStream_t cs, F&& launch, cudaGraphExec_t* out, long long* kernels) {
+    cudaGraph_t g = nullptr;
+    MD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    md_status st = launch(cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (st != MD_OK) { if (e == cudaSuccess && g) cudaGraphDestroy(g); return st; }
+    MD_CUDA(e);
+    if (kernels) *kernels = kernel_nodes(g);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    MD_CUDA(e);
+    return MD_OK;
+}
+
+// The host-driven loop (md_batch_set_host_loop): a set-up graph and a
+// one-cycle graph, without conditional nodes, launched by the host, which
+// reads the count of finished instances after every cycle.  Same kernels as
+// the device-driven solve; for tools that cannot look inside conditional
+// graph nodes (kernel profilers).
+static md_status build_host_loop(md_batch* B) {
+    MD_TRY(capture_exec(B->cap, [&](cudaStream_t s) { return launch_init(B, s); }, &B->init_graph, &B->init_kernels));
+    MD_TRY(capture_exec(B->cap, [&](cudaStream_t s) -> md_status {
+        MD_TRY(launch_cycle_all_slots(B, s));
+        k_cycle_count<<<1, 1, 0, s>>>(B->ctl, B->profiling ? 1 : 0);
+        MD_CHECK_LAUNCH();
+        return MD_OK;
+    }, &B->cycle_graph, &B->cycle_kernels));
+    B->if_mode = 3;
+    return MD_OK;
 }
 
 static md_status build_graph(md_batch* B) {
     const int engine = B->cnn ? B->cnn->engine : 0;
     const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
-    if (B->solve_graph && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
+    const bool have = B->host_loop ? B->cycle_graph != nullptr : B->solve_graph != nullptr;
+    if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
         B->graph_prec_order == B->prec_order && B->graph_smooth_nu == B->smooth_nu &&
         B->graph_smooth_omega == B->smooth_omega && B->graph_inner_m == B->inner_m)
         return MD_OK;
     destroy_graphs(B);
-    cudaGraph_t g = nullptr;
-    MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
-    md_status st = capture_solve(B, B->cap);
-    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
-    if (st != MD_OK) {
-        if (e == cudaSuccess && g) cudaGraphDestroy(g);
-        return st;
+    if (B->host_loop) {
+        MD_TRY(build_host_loop(B));
+        B->graph_cnn_uid = uid;
+        B->graph_prec_order = B->prec_order;
+        B->graph_smooth_nu = B->smooth_nu;
+        B->graph_smooth_omega = B->smooth_omega;
+        B->graph_inner_m = B->inner_m;
+        B->graph_prof = B->profiling;
+        B->graph_engine = engine;
+        return MD_OK;
     }
+    cudaGraph_t g = nullptr;
+    md_status st = MD_OK;
+    cudaError_t e = cudaSuccess;
+    // the first form of slot gating the runtime accepts (see capture_solve)
+    for (int mode = 0; mode <= 2; mode += 2) {
+        g = nullptr;
+        MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+        st = capture_solve(B, B->cap, mode);
+        e = cudaStreamEndCapture(B->cap, &g);
+        if (st == MD_OK && e == cudaSuccess) {
+            B->if_mode = mode;
+            break;
+        }
+        if (e == cudaSuccess && g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();
+        if (st == MD_OK) st = md_cuda_status(e, "solve graph capture", __FILE__, __LINE__);
+    }
+    if (st != MD_OK) return st;
     MD_CUDA(e);
     B->init_kernels = kernel_nodes(g);
     e = cudaGraphInstantiate(&B->solve_graph, g, 0);
@@ -1693,6 +1853,75 @@ static md_status build_graph(md_batch* B) {
     B->graph_inner_m = B->inner_m;
     B->graph_prof = B->profiling;
     B->graph_engine = engine;
+    return MD_OK;
+}
+
+// ---- autotuning at batch creation --------------------------------------------
+// Batches of at least MD_TUNE_MIN_UNKNOWNS unknowns time their choices on the
+// GPU once, when they are created, and keep the fastest: the elements per
+// block of the Krylov vector kernels (a Gram-Schmidt step at basis length 6
+// over the whole batch, all instances active), and the tiles per plane step of
+// the tensor-core convolutions (a network forward pass over every grid).
+#define MD_TUNE_MIN_UNKNOWNS 1000000
+
+__global__ void k_tune_state(KState* st, int ninst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    st[i].active = 1;
+    st[i].reorth = 0;
+    for (int r = 0; r <= MD_KMAX; ++r) { st[i].sig[r] = 1.0; st[i].coef[r] = 0.0; }
+    st[i].wn2_before = 0.0;
+}
+
+static md_status tune_vec_chunk(md_batch* B, const std::vector<const InstDesc*>& ptrs) {
+    const int cands[] = {2048, 4096, 8192, 16384};
+    const int j = 5;
+    cudaStream_t s = B->cap;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    MD_CUDA(cudaEventCreate(&e0));
+    MD_CUDA(cudaEventCreate(&e1));
+    Tables keep = B->tabs;
+    double best = 1e300;
+    Tables best_t = keep;
+    int best_c = MD_VEC_CHUNK_FGMRES;
+    md_status st = MD_OK;
+    B->tuning.n_vec = 0;
+    for (int c : cands) {
+        Tables T;
+        st = build_tables(ptrs, &T, &B->allocs, c);
+        if (st != MD_OK) break;
+        B->tabs = T;
+        k_tune_state<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
+        launch_gs(B, j, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) {
+            k_tune_state<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
+            launch_gs(B, j, s);
+        }
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { st = md_cuda_status(e, "vector chunk tuning", __FILE__, __LINE__); break; }
+        const double us = 1e3 * ms / 3;
+        B->tuning.vec_candidates[B->tuning.n_vec] = c;
+        B->tuning.vec_us[B->tuning.n_vec] = us;
+        B->tuning.n_vec += 1;
+        if (us < best) { best = us; best_t = T; best_c = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->tabs = st == MD_OK ? best_t : keep;
+    B->tuning.vec_chunk = st == MD_OK ? best_c : MD_VEC_CHUNK_FGMRES;
+    // the state is set from scratch by every solve
+    MD_CUDA(cudaMemsetAsync(B->st, 0, sizeof(KState) * B->ninst, s));
+    MD_CUDA(cudaStreamSynchronize(s));
+    return st;
+}
+
+extern "C" md_status md_batch_tuning(const md_batch* B, md_tuning_t* out) {
+    if (!B || !out) { md_set_error("md_batch_tuning: NULL argument"); return MD_ERR_ARG; }
+    *out = B->tuning;
     return MD_OK;
 }
 
@@ -1745,8 +1974,14 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
     chk(dev_alloc(&B->allocs, &B->st, (size_t)n_ops));
     // partial sums of one block of a reduction kernel (its table: whole vectors, grid
     // nodes or touched nodes)
-    chk(dev_alloc(&B->allocs, &B->part,
-                  (size_t)std::max({B->tabs.vec.nblocks, B->tabs.n3.nblocks, B->tabs.touch.nblocks, 1}) * MD_MAXR));
+    {
+        // the smallest vector chunk the autotuner tries (2048) gives the most blocks
+        long long vb = 0;
+        for (int i = 0; i < n_ops; ++i) vb += (ops[i]->h.n + 2047) / 2048;
+        chk(dev_alloc(&B->allocs, &B->part,
+                      (size_t)std::max<long long>({vb, B->tabs.vec.nblocks, B->tabs.n3.nblocks, B->tabs.touch.nblocks, 1}) *
+                          MD_MAXR));
+    }
     chk(dev_alloc(&B->allocs, &B->ndone, 1));
     chk(dev_alloc(&B->allocs, &B->ctl, 1));
     if (st == MD_OK && cudaMallocHost(&B->h_ctl, sizeof(SolveCtl)) != cudaSuccess) chk(MD_ERR_OOM);
@@ -1777,6 +2012,16 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
     if (st == MD_OK) {
         cudaError_t e = cudaDeviceSynchronize();
         if (e != cudaSuccess) chk(md_cuda_status(e, "md_batch_create", __FILE__, __LINE__));
+    }
+    B->tuning.vec_chunk = solver == MD_SOLVER_CG_JACOBI ? MD_VEC_CHUNK_CG : MD_VEC_CHUNK_FGMRES;
+    B->tuning.conv_tps = B->cw ? B->cw->tps : 0;
+    if (st == MD_OK && solver != MD_SOLVER_CG_JACOBI && tot >= MD_TUNE_MIN_UNKNOWNS) {
+        B->tuning.tuned = 1;
+        chk(tune_vec_chunk(B, ptrs));
+        if (st == MD_OK && B->cw) {
+            chk(cnn_autotune_tps(cnn, B->cw, B->Z, B->off, B->tuning.conv_us));
+            B->tuning.conv_tps = B->cw->tps;
+        }
     }
     if (st != MD_OK) { md_batch_destroy(B); return st; }
     *out = B;
@@ -1810,13 +2055,30 @@ static md_status batch_run(md_batch* B, double tol, int maxit, cudaStream_t s) {
     c.maxit = maxit;
     c.max_cycles = maxit / per_cycle + 3;
     MD_CUDA(cudaMemcpyAsync(B->ctl, &c, sizeof(SolveCtl), cudaMemcpyHostToDevice, s));
-    MD_CUDA(cudaGraphLaunch(B->solve_graph, s));
     int ndone = 0;
-    MD_CUDA(cudaMemcpyAsync(&c, B->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
-    MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
-    MD_CUDA(cudaStreamSynchronize(s));
-    B->stats.kernel_launches += B->init_kernels + (long long)c.kernels;
-    B->stats.graph_launches += 1;
+    if (B->host_loop) {
+        MD_CUDA(cudaGraphLaunch(B->init_graph, s));
+        B->stats.graph_launches += 1;
+        long long cycles = 0;
+        for (; cycles < c.max_cycles; ++cycles) {
+            MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MD_CUDA(cudaStreamSynchronize(s));
+            if (ndone >= B->ninst) break;
+            MD_CUDA(cudaGraphLaunch(B->cycle_graph, s));
+            B->stats.graph_launches += 1;
+        }
+        MD_CUDA(cudaMemcpyAsync(&c, B->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+        MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MD_CUDA(cudaStreamSynchronize(s));
+        B->stats.kernel_launches += B->init_kernels + cycles * B->cycle_kernels;
+    } else {
+        MD_CUDA(cudaGraphLaunch(B->solve_graph, s));
+        MD_CUDA(cudaMemcpyAsync(&c, B->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+        MD_CUDA(cudaMemcpyAsync(&ndone, B->ndone, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MD_CUDA(cudaStreamSynchronize(s));
+        B->stats.kernel_launches += B->init_kernels + (long long)c.kernels;
+        B->stats.graph_launches += 1;
+    }
     B->stats.cycles += c.cycles;
     if (B->profiling && B->solver != MD_SOLVER_CG_JACOBI) {
         B->stats.prec_ms += c.t_prec * 1e-6;
@@ -1865,6 +2127,12 @@ extern "C" md_status md_batch_solve(md_batch* B, const double* b_all, double* x_
     return all ? MD_OK : MD_NOT_CONVERGED;
 }
 
+extern "C" md_status md_batch_set_host_loop(md_batch* B, int enable) {
+    if (!B) { md_set_error("md_batch_set_host_loop: NULL batch"); return MD_ERR_ARG; }
+    B->host_loop = enable != 0;
+    return MD_OK;
+}
+
 extern "C" md_status md_batch_set_prec_order(md_batch* B, int lower) {
     if (!B || (lower != 0 && lower != 1)) { md_set_error("md_batch_set_prec_order: bad argument"); return MD_ERR_ARG; }
     B->prec_order = lower;
@@ -1880,6 +2148,7 @@ extern "C" md_status md_batch_set_profiling(md_batch* B, int enable) {
 extern "C" md_status md_batch_stats(const md_batch* B, md_batch_stats_t* out) {
     if (!B || !out) { md_set_error("md_batch_stats: NULL argument"); return MD_ERR_ARG; }
     *out = B->stats;
+    out->slot_gating = B->if_mode;
     return MD_OK;
 }
 

@@ -689,3 +689,58 @@ extern "C" md_status md_train(md_cnn* c, const md_train_cfg* cfg) {
     dev_free_all(&opt);
     return st;
 }
+
+// ---- optimizer state for training loops driven from outside (data-parallel
+// training: each process computes its gradient with md_train_loss, the
+// processes average them, and every process applies the same step)
+struct md_opt {
+    std::vector<void*> allocs;
+    float *w = nullptr, *m = nullptr, *v = nullptr;  // FP32 master weights, AdamW moments
+    unsigned char* isw = nullptr;                    // weight (1) or bias (0): decay on weights only
+    long long step = 0;
+};
+
+extern "C" void md_opt_destroy(md_opt* o) {
+    if (!o) return;
+    dev_free_all(&o->allocs);
+    delete o;
+}
+
+extern "C" md_status md_opt_create(const md_cnn* c, md_opt** out) {
+    if (!c || !out) { md_set_error("md_opt_create: NULL argument"); return MD_ERR_ARG; }
+    *out = nullptr;
+    md_opt* o = new md_opt();
+    std::vector<unsigned char> hisw(MD_CNN_NPARAMS, 0);
+    for (int l = 0; l < MD_CNN_LAYERS; ++l)
+        for (size_t k = 0; k < (size_t)kCout[l] * kCin[l] * 27; ++k) hisw[host_w_off(l) + k] = 1;
+    md_status st = dev_upload(&o->allocs, &o->w, c->host.data(), c->host.size());
+    if (st == MD_OK) st = dev_alloc(&o->allocs, &o->m, (size_t)MD_CNN_NPARAMS);
+    if (st == MD_OK) st = dev_alloc(&o->allocs, &o->v, (size_t)MD_CNN_NPARAMS);
+    if (st == MD_OK) st = dev_upload(&o->allocs, &o->isw, hisw.data(), hisw.size());
+    if (st != MD_OK) { md_opt_destroy(o); return st; }
+    *out = o;
+    return MD_OK;
+}
+
+extern "C" md_status md_opt_step(md_opt* o, md_cnn* c, const float* grad, double lr, double beta1, double beta2,
+                                 double eps, double weight_decay, md_stream stream) {
+    if (!o || !c || !grad) { md_set_error("md_opt_step: NULL argument"); return MD_ERR_ARG; }
+    if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0)) {
+        md_set_error("md_opt_step: bad hyper-parameters");
+        return MD_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    o->step += 1;
+    const float bc1 = (float)(1.0 - std::pow(beta1, (double)o->step));
+    const float bc2 = (float)(1.0 - std::pow(beta2, (double)o->step));
+    k_adamw<<<128, 256, 0, s>>>(o->w, grad, o->m, o->v, o->isw, MD_CNN_NPARAMS, (float)lr, (float)beta1, (float)beta2,
+                                (float)eps, (float)weight_decay, bc1, bc2);
+    MD_CHECK_LAUNCH();
+    std::vector<float> hw(MD_CNN_NPARAMS);
+    MD_CUDA(cudaMemcpyAsync(hw.data(), o->w, sizeof(float) * MD_CNN_NPARAMS, cudaMemcpyDeviceToHost, s));
+    MD_CUDA(cudaStreamSynchronize(s));
+    for (float x : hw)
+        if (!std::isfinite(x)) { md_set_error("md_opt_step: a weight is not finite"); return MD_ERR_NAN; }
+    c->host = hw;
+    return cnn_upload(c);
+}

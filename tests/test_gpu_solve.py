@@ -103,6 +103,7 @@ def test_batched_solve_is_one_graph_launch():
         its, rels, ok = B.solve(b, x, tol=1e-8, maxit=20000)
         st = B.stats()
         assert ok and st["graph_launches"] == 1, st
+        print(f"{solver}: slot gating {st['slot_gating']}, cycles {st['cycles']}, kernels {st['kernel_launches']}")
         assert st["cycles"] >= (max(its) + restart - 1) // restart if solver == "fgmres_cnn" else st["cycles"] >= 1
         assert st["kernel_launches"] > 0
         if solver == "fgmres_cnn":
@@ -115,3 +116,30 @@ def test_batched_solve_is_one_graph_launch():
                 assert st[k] > 0, (k, st)
             assert st["conv_hidden_ms"] < st["prec_ms"]
         B.close()
+
+
+def test_host_loop_gives_the_device_loop_result():
+    """The host-driven loop (for kernel profilers) runs the same kernels as the
+    one-launch solve: identical iterations and a bit-identical solution."""
+    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300.weights import default_network_params
+    insts = [mdgen.workload_instance("batch256_mixed", i) for i in (4, 13)]
+    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    b = torch.cat([op.rhs(torch.from_numpy(mdgen.interior_source(w["N"], w["f_seed"])).cuda(), w["g"])
+                   for w, op in zip(insts, ops)])
+    net = Network(default_network_params("lower"))
+    out = []
+    for host in (False, True):
+        B = Batch(ops, "fgmres_cnn", net, restart=30)
+        B.set_prec_order("lower")
+        B.set_host_loop(host)
+        x = torch.zeros_like(b)
+        its, rels, ok = B.solve(b, x, tol=1e-8)
+        assert ok
+        st = B.stats()
+        assert (st["slot_gating"] == 3) == host
+        assert st["graph_launches"] == (1 + st["cycles"] if host else 1)
+        out.append((its, x.cpu().numpy()))
+        B.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
