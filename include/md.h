@@ -73,13 +73,26 @@ typedef struct {
     int elems_per_edge;         /* >= 1 */
 } md_graph;
 
-/* Coefficients of eq. (problem).  NULL selects k_omega = 1, sigma_omega = 0,
- * k_lambda = 1.  The 1D diffusion coefficient used is k_lambda * pi R^2 (the
- * |D| weight of a_Lambda, eq. (alambda)). */
+/* Coefficients and boundary conditions of eq. (problem).  NULL selects
+ * k_omega = 1, sigma_omega = 0, k_lambda = 1, homogeneous Dirichlet
+ * conditions on the cube faces and natural conditions at every graph end.
+ * The 1D diffusion coefficient used is k_lambda * pi R^2 (the |D| weight of
+ * a_Lambda, eq. (alambda)).
+ *   natural_boundary = 1: the natural (Neumann) condition of eq. (problem)
+ *     on the cube faces: every grid node is an unknown (sigma_omega > 0 or a
+ *     1D Dirichlet node keeps A positive definite);
+ *   dirichlet_1d: graph node ids on the part dLambda_D of the graph boundary
+ *     where u_Lambda = u_d (eq. (problem)); those unknowns are eliminated
+ *     symmetrically -- identity rows and columns of the 1D block, no
+ *     coupling columns -- and their value enters the load vector (md_rhs). */
 typedef struct {
     double k_omega;
     double sigma_omega;
     double k_lambda;
+    int natural_boundary;
+    int n_dirichlet_1d;
+    const int* dirichlet_1d;     /* host, n_dirichlet_1d graph node ids */
+    double u_d;
 } md_params;
 
 /* Sizes of an assembled instance. */
@@ -116,7 +129,9 @@ md_status md_op_distance(const md_op* op, float* d, md_stream s);
 
 /* md_rhs -- the load vector of eq. (problem_weak): b0 = M_Omega f (Q1 mass
  * times nodal values f, device FP64, n3 entries, NULL for f = 0) with b0 = 0
- * on Dirichlet nodes, b1_i = g * int_Lambda psi_i ds.  b: device FP64, n. */
+ * on Dirichlet nodes, b1_i = g * int_Lambda psi_i ds; with 1D Dirichlet nodes
+ * (md_params) b1 = u_d on them, and their value's columns moved to the right
+ * (b0 += beta Pi^T W Psi_D u_d, b1 -= B11[:, D] u_d).  b: device FP64, n. */
 md_status md_rhs(const md_op* op, const double* f, double g, double* b, md_stream s);
 
 /* md_apply -- y = A u, eq. (mainsys), matrix-free.  prec selects FP32 (u, y
@@ -350,6 +365,7 @@ typedef struct {
     double vec_us[8];            /* one Gram-Schmidt step with each candidate */
     int conv_tps;                /* 128-row tiles per plane step of the convolutions (0: no network) */
     double conv_us[2];           /* one forward pass with 1 and 2 tiles per step */
+    char gating_note[200];       /* why a form of slot gating was refused by the runtime (empty if none) */
 } md_tuning_t;
 md_status md_batch_tuning(const md_batch* b, md_tuning_t* out);
 md_status md_batch_reset_stats(md_batch* b);
@@ -388,6 +404,15 @@ md_status md_train(md_cnn* cnn, const md_train_cfg* cfg);
  * MD_CNN_NPARAMS or NULL.  *loss written on return (synchronises s). */
 md_status md_train_loss(const md_cnn* cnn, int count, const md_op* const* ops, const float* const* r,
                         double* loss, float* dparams, md_stream s);
+
+/* md_krylov_basis -- the Krylov augmentation of the training set (Section
+ * 4.1.1): an orthonormal basis q_0 = b/||b||, q_1, ..., q_m of the Krylov space
+ * K_{m+1}(C, b) of the 3D block C = K00 + beta Pi^T W Pi (C q is the 3D part of
+ * A [q; 0]), each new vector orthogonalised by two passes of modified
+ * Gram-Schmidt, in FP64.  b: device float n3 (nonzero); Q: device float,
+ * (m+1) x n3, row j = q_j.  m in [1, 16], else MD_ERR_ARG.  Allocates its FP64
+ * work vectors; synchronises s. */
+md_status md_krylov_basis(const md_op* op, const float* b, int m, float* Q, md_stream s);
 
 /* md_opt -- AdamW state (FP32 master weights copied from the network, first
  * and second moments) for training loops driven by the caller, one step per

@@ -21,7 +21,9 @@ class MdGraph(C.Structure):
 
 
 class MdParams(C.Structure):
-    _fields_ = [("k_omega", C.c_double), ("sigma_omega", C.c_double), ("k_lambda", C.c_double)]
+    _fields_ = [("k_omega", C.c_double), ("sigma_omega", C.c_double), ("k_lambda", C.c_double),
+                ("natural_boundary", C.c_int), ("n_dirichlet_1d", C.c_int), ("dirichlet_1d", C.POINTER(C.c_int)),
+                ("u_d", C.c_double)]
 
 
 class MdOpInfo(C.Structure):
@@ -39,7 +41,8 @@ class MdBatchStats(C.Structure):
 
 class MdTuning(C.Structure):
     _fields_ = [("tuned", C.c_int), ("vec_chunk", C.c_int), ("n_vec", C.c_int), ("vec_candidates", C.c_int * 8),
-                ("vec_us", C.c_double * 8), ("conv_tps", C.c_int), ("conv_us", C.c_double * 2)]
+                ("vec_us", C.c_double * 8), ("conv_tps", C.c_int), ("conv_us", C.c_double * 2),
+                ("gating_note", C.c_char * 200)]
 
 
 class MdTrainCfg(C.Structure):
@@ -97,6 +100,7 @@ SIGNATURES = {
                               C.POINTER(i32), C.POINTER(f64), vp]),
     "md_train": (st, [vp, C.POINTER(MdTrainCfg)]),
     "md_train_loss": (st, [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(f64), vp, vp]),
+    "md_krylov_basis": (st, [vp, vp, i32, vp, vp]),
     "md_opt_create": (st, [vp, C.POINTER(vp)]),
     "md_opt_step": (st, [vp, vp, vp, f64, f64, f64, f64, f64, vp]),
     "md_opt_destroy": (None, [vp]),

@@ -47,13 +47,16 @@ def _ptr(t: torch.Tensor | None, dtype=None, numel=None, name="tensor"):
 class Operator:
     """One assembled instance: grid N, graph, radius, coupling beta (md_assemble)."""
 
-    def __init__(self, N: int, graph: dict, beta: float, *, k_omega=1.0, sigma_omega=0.0, k_lambda=1.0):
+    def __init__(self, N: int, graph: dict, beta: float, *, k_omega=1.0, sigma_omega=0.0, k_lambda=1.0,
+                 dirichlet: bool = True, dirichlet_1d=None, u_d: float = 1.0):
         lib = L.load()
         xyz = np.ascontiguousarray(graph["xyz"], dtype=np.float64)
         edges = np.ascontiguousarray(graph["edges"], dtype=np.int32)
         g = L.MdGraph(len(xyz), xyz.ctypes.data_as(C.POINTER(C.c_double)), len(edges),
                       edges.ctypes.data_as(C.POINTER(C.c_int)), int(graph["elems"]))
-        prm = L.MdParams(k_omega, sigma_omega, k_lambda)
+        d1 = np.ascontiguousarray(dirichlet_1d if dirichlet_1d is not None else [], dtype=np.int32)
+        prm = L.MdParams(k_omega, sigma_omega, k_lambda, 0 if dirichlet else 1, len(d1),
+                         d1.ctypes.data_as(C.POINTER(C.c_int)) if len(d1) else None, float(u_d))
         h = C.c_void_p()
         torch.cuda.init()
         L.check(lib.md_assemble(int(N), C.byref(g), float(graph["radius"]), float(beta), C.byref(prm), C.byref(h)),
@@ -146,6 +149,14 @@ class Operator:
                                          _ptr(r, torch.float32, self.n, "r"), _ptr(z, torch.float32, self.n, "z"),
                                          _stream()), "md_precondition")
         return z
+
+    def krylov_basis(self, b: torch.Tensor, m: int) -> torch.Tensor:
+        """Orthonormal basis q_0 = b/||b||, ..., q_m of K_{m+1}(C, b), C the 3D
+        block (md_krylov_basis); b float32 of length n3; returns (m+1, n3) float32."""
+        Q = torch.empty((m + 1, self.n3), dtype=torch.float32, device="cuda")
+        L.check(L.load().md_krylov_basis(self._h, _ptr(b, torch.float32, self.n3, "b"), int(m), _ptr(Q), _stream()),
+                "md_krylov_basis")
+        return Q
 
     def lift(self, r: torch.Tensor):
         """(l, z1): z1 = B11^{-1} r1 and its 3D forcing l = beta Pi^T W Psi z1
@@ -389,7 +400,8 @@ class Batch:
         return {"tuned": bool(t.tuned), "vec_chunk": t.vec_chunk,
                 "vec_us": {int(t.vec_candidates[i]): float(t.vec_us[i]) for i in range(t.n_vec)},
                 "conv_tiles_per_step": t.conv_tps,
-                "conv_us": {1: float(t.conv_us[0]), 2: float(t.conv_us[1])} if t.conv_tps else {}}
+                "conv_us": {1: float(t.conv_us[0]), 2: float(t.conv_us[1])} if t.conv_tps else {},
+                "gating_note": t.gating_note.decode(errors="replace")}
 
     def stats(self) -> dict:
         st = L.MdBatchStats()

@@ -183,8 +183,9 @@ __host__ __device__ inline bool cnn_runs(const KState* st, int inst) {
 }
 
 // Stencil tile shape of the operator apply for grid N: ty rows of all N+1
-// columns (at most 256 columns, one per thread) and tz planes, such that the
-// FP64 input tile with its halo and the output tile fit 64 KB of shared memory.
+// columns (at most 512 columns, about two per thread) and tz planes, such that
+// the FP64 input tile with its halo and the output tile fit 100 KB of shared
+// memory.
 void apply_tile_shape(int N, int* ty, int* tz);
 int apply_tile_smem(int N, int ty, int tz, int elem_bytes);
 md_status apply_prepare(int smem32, int smem64);

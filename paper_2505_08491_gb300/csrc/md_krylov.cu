@@ -18,6 +18,7 @@
 // recursive residual, then reports the true one.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "md_cnn.h"
@@ -1839,6 +1840,9 @@ static md_status build_graph(md_batch* B) {
         if (e == cudaSuccess && g) cudaGraphDestroy(g);
         (void)cudaGetLastError();
         if (st == MD_OK) st = md_cuda_status(e, "solve graph capture", __FILE__, __LINE__);
+        // why this form was refused (md_tuning_t.gating_note)
+        snprintf(B->tuning.gating_note, sizeof(B->tuning.gating_note), "slot gating %d refused: %s", mode,
+                 md_last_error());
     }
     if (st != MD_OK) return st;
     MD_CUDA(e);

