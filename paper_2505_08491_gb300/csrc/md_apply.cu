@@ -27,6 +27,35 @@ __device__ inline bool gate_skip(const KState* st, int gate, int inst) {
     return gate == 1 ? !st[inst].active : st[inst].t_done != 0ULL;
 }
 
+// Row (i, j, k) of a Q1 operator on the cube with natural conditions on its
+// faces: the element-by-element sum gives neighbour (i, j, k) + d the
+// coefficient c[|dx|+|dy|+|dz|] of the interior stencil times 1/2 for every
+// axis a with d_a = 0 on which the node lies on a face (half of the elements
+// around that axis are missing).  u: grid vector; neighbours outside the
+// grid do not exist.
+template <typename T>
+__device__ inline T q1_row_natural(const T* __restrict__ u, int i, int j, int k, int N, const T* c) {
+    const int M = N + 1;
+    const T fx = (i == 0 || i == N) ? T(0.5) : T(1), fy = (j == 0 || j == N) ? T(0.5) : T(1),
+            fz = (k == 0 || k == N) ? T(0.5) : T(1);
+    T acc = T(0);
+    for (int dz = -1; dz <= 1; ++dz) {
+        if (k + dz < 0 || k + dz > N) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (j + dy < 0 || j + dy > N) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (i + dx < 0 || i + dx > N) continue;
+                T w = c[(dx != 0) + (dy != 0) + (dz != 0)];
+                if (dx == 0) w *= fx;
+                if (dy == 0) w *= fy;
+                if (dz == 0) w *= fz;
+                acc += w * u[(i + dx) + M * ((j + dy) + M * (k + dz))];
+            }
+        }
+    }
+    return acc;
+}
+
 // a / (N+1) for 0 <= a < 2^20 (InstDesc::mdiv)
 __device__ __forceinline__ int div_m(unsigned int a, unsigned int mdiv) { return (int)__umulhi(a, mdiv); }
 
@@ -67,6 +96,7 @@ __device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __rest
                                     T* s_in) {
     const int N = d.N, M = N + 1, TY = d.ty;
     const unsigned int mdiv = d.mdiv;
+    const bool natural = d.natural != 0;
     const int zt = tile / d.nyt, yt = tile - zt * d.nyt;
     const int z0 = zt * d.tz, y0 = yt * TY;
     const int nz = min(d.tz, M - z0), ny = min(TY, M - y0);
@@ -90,8 +120,11 @@ __device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __rest
                     const int pz = (int)__umulhi((unsigned int)e, sdiv), er = e - pz * slab_in;
                     const int r = div_m((unsigned int)er, mdiv), x = er - r * M;
                     const int z = z0 - 1 + pz, y = y0 - 1 + r;
-                    if (z >= 1 && z <= N - 1 && y >= 1 && y <= N - 1 && x >= 1 && x <= N - 1)
-                        v[k] = ui[((long long)z * M + y) * M + x];
+                    // Dirichlet nodes are eliminated columns (zero); with natural
+                    // conditions only nodes outside the grid are
+                    const bool keep = natural ? (z >= 0 && z <= N && y >= 0 && y <= N)
+                                              : (z >= 1 && z <= N - 1 && y >= 1 && y <= N - 1 && x >= 1 && x <= N - 1);
+                    if (keep) v[k] = ui[((long long)z * M + y) * M + x];
                 }
             }
 #pragma unroll
@@ -107,9 +140,36 @@ __device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __rest
     for (int c = threadIdx.x; c < ny * M; c += blockDim.x) {
         const int r = div_m((unsigned int)c, mdiv), x = c - r * M, y = y0 + r;
         T* so = s_out + c;
+        // a node on a cube face: with natural conditions its row of the
+        // element-by-element sum (the neighbour of offset d weighs the class
+        // coefficient times 1/2 per axis a with d_a = 0 on which the node lies
+        // on a face; the tile's out-of-grid rows and planes are zero), a
+        // Dirichlet row (u itself) otherwise
+        auto face_node = [&](int zz) -> T {
+            const int z = z0 + zz;
+            if (!natural) return ui[((long long)z * M + y) * M + x];
+            const T fx = (x == 0 || x == N) ? T(0.5) : T(1), fy = (y == 0 || y == N) ? T(0.5) : T(1),
+                    fz = (z == 0 || z == N) ? T(0.5) : T(1);
+            T acc = T(0);
+            for (int dz = -1; dz <= 1; ++dz) {
+                const T* pl = s_in + (size_t)(zz + 1 + dz) * slab_in + (size_t)(r + 1) * M;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const T* row = pl + dy * M;
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (x + dx < 0 || x + dx > N) continue;
+                        T w = Pr<T>::st(d, (dx != 0) + (dy != 0) + (dz != 0));
+                        if (dx == 0) w *= fx;
+                        if (dy == 0) w *= fy;
+                        if (dz == 0) w *= fz;
+                        acc += w * row[x + dx];
+                    }
+                }
+            }
+            return acc;
+        };
         const bool col_bd = x == 0 || x == N || y == 0 || y == N;
         if (col_bd) {
-            for (int zz = 0; zz < nz; ++zz) so[(size_t)zz * ny * M] = ui[((long long)(z0 + zz) * M + y) * M + x];
+            for (int zz = 0; zz < nz; ++zz) so[(size_t)zz * ny * M] = face_node(zz);
             continue;
         }
         // plane sums of input plane pz at this column
@@ -130,7 +190,7 @@ __device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __rest
             const int z = z0 + zz;
             T v;
             if (z == 0 || z == N) {
-                v = ui[((long long)z * M + y) * M + x];
+                v = face_node(zz);
             } else {
                 const T face = b1 + (a0 + f0);
                 const T edge = b2 + (a1 + f1);
@@ -221,16 +281,28 @@ __global__ void k_rhs(const InstDesc* __restrict__ D, const double* __restrict__
     const long long total = d.n;
     const int N = d.N, M = N + 1;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total; idx += (long long)gridDim.x * blockDim.x) {
-        if (idx >= d.n3) { b[idx] = g * d.load1[idx - d.n3]; continue; }
+        if (idx >= d.n3) {
+            const int i1 = (int)(idx - d.n3);
+            b[idx] = g * d.load1[i1] + (d.rhs1 ? d.rhs1[i1] : 0.0);
+            continue;
+        }
         const int n = (int)idx;
         const int i = n % M, r = n / M, j = r % M, k = r / M;
-        if (!f || i == 0 || i == N || j == 0 || j == N || k == 0 || k == N) { b[n] = 0.0; continue; }
+        const double lift = d.rhs0 ? d.rhs0[n] : 0.0;
+        if (d.natural) {
+            b[n] = (f ? q1_row_natural<double>(f, i, j, k, N, d.ms64) : 0.0) + lift;
+            continue;
+        }
+        if (!f || i == 0 || i == N || j == 0 || j == N || k == 0 || k == N) {
+            b[n] = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N) ? 0.0 : lift;
+            continue;
+        }
         double s[4] = {0.0, 0.0, 0.0, 0.0};
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx)
                     s[(dx != 0) + (dy != 0) + (dz != 0)] += f[n + dx + dy * M + dz * M * M];
-        b[n] = d.ms64[0] * s[0] + d.ms64[1] * s[1] + d.ms64[2] * s[2] + d.ms64[3] * s[3];
+        b[n] = d.ms64[0] * s[0] + d.ms64[1] * s[1] + d.ms64[2] * s[2] + d.ms64[3] * s[3] + lift;
     }
 }
 
@@ -292,13 +364,38 @@ md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_m, const 
     const double a0 = std::fabs(D.st64[0]), a1 = std::fabs(D.st64[1]), a2 = std::fabs(D.st64[2]),
                  a3 = std::fabs(D.st64[3]);
     auto nside = [&](int c) { return (double)((c - 1 >= 1) + (c + 1 <= N - 1)); };
+    // natural conditions: every node is a row; the stencil centre of a node on
+    // f faces is scaled by 1/2^f, and each neighbour's coefficient by 1/2 per
+    // boundary axis it does not move along (q1_row_natural)
+    auto fac = [&](int c) { return (c == 0 || c == N) ? 0.5 : 1.0; };
+    std::vector<double> cdiag((size_t)D.n3, 0.0);  // diagonal of K00 (0: Dirichlet row)
     for (int k = 0; k < M; ++k)
         for (int j = 0; j < M; ++j)
             for (int i = 0; i < M; ++i) {
-                const bool bd = i == 0 || i == N || j == 0 || j == N || k == 0 || k == N;
                 const int n = i + M * (j + M * k);
-                dv[n] = bd ? 1.0 : 1.0 / D.st64[0];
+                if (D.natural) {
+                    const double f[3] = {fac(i), fac(j), fac(k)};
+                    const int c[3] = {i, j, k};
+                    cdiag[n] = D.st64[0] * f[0] * f[1] * f[2];
+                    double sabs = 0.0;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const int dd[3] = {dx, dy, dz};
+                                bool in = true;
+                                double w = std::fabs(D.st64[(dx != 0) + (dy != 0) + (dz != 0)]);
+                                for (int a = 0; a < 3; ++a) {
+                                    if (c[a] + dd[a] < 0 || c[a] + dd[a] > N) in = false;
+                                    if (dd[a] == 0) w *= f[a];
+                                }
+                                if (in) sabs += w;
+                            }
+                    kabs[n] = sabs;
+                    continue;
+                }
+                const bool bd = i == 0 || i == N || j == 0 || j == N || k == 0 || k == N;
                 if (!bd) {
+                    cdiag[n] = D.st64[0];
                     const double x = nside(i), y = nside(j), z = nside(k);
                     kabs[n] = a0 + (x + y + z) * a1 + (x * y + x * z + y * z) * a2 + x * y * z * a3;
                 }
@@ -307,9 +404,10 @@ md_status launch_dinv_fill(md_op* op, const std::vector<double>& touch_m, const 
     if (D.ntouch) MD_CUDA(cudaMemcpy(tn.data(), D.tn_node, sizeof(int) * D.ntouch, cudaMemcpyDeviceToHost));
     std::vector<double> srow((size_t)D.n3, 0.0);  // beta (Pi^T W Pi) row sums
     for (int i = 0; i < D.ntouch; ++i) {
-        dv[tn[i]] = 1.0 / (D.st64[0] + D.beta * touch_m[i]);
+        cdiag[tn[i]] += D.beta * touch_m[i];
         srow[tn[i]] = D.beta * touch_rs[i];
     }
+    for (int n = 0; n < D.n3; ++n) dv[n] = cdiag[n] != 0.0 ? 1.0 / cdiag[n] : 1.0;
     std::vector<float> sv((size_t)D.n3);
     for (int n = 0; n < D.n3; ++n) {
         if (kabs[n] == 0.0) { sv[n] = 1.f; continue; }   // Dirichlet row

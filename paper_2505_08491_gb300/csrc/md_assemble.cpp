@@ -3,7 +3,9 @@
 //
 // Readings of points the paper leaves open, shared with the oracle by
 // specification only (no code is shared):
-//   - homogeneous Dirichlet rows/columns on the cube boundary;
+//   - homogeneous Dirichlet rows/columns on the cube boundary, or the natural
+//     condition of eq. (problem) (md_params.natural_boundary), with the 1D
+//     Dirichlet nodes of dLambda_D eliminated symmetrically;
 //   - beta multiplies the coupling form with unit line weight;
 //   - 1D diffusion kappa = k_lambda * pi R^2;
 //   - 2 Gauss points per 1D element; 8 circle points at theta_k = 2 pi k / 8
@@ -46,7 +48,22 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     const double k_omega = prm ? prm->k_omega : 1.0;
     const double sigma_omega = prm ? prm->sigma_omega : 0.0;
     const double k_lambda = prm ? prm->k_lambda : 1.0;
+    const bool natural = prm && prm->natural_boundary;
+    const double u_d = prm ? prm->u_d : 1.0;
     const int V = g->n_nodes, E = g->n_edges, m = g->elems_per_edge;
+    if (prm && prm->n_dirichlet_1d > 0) {
+        if (!prm->dirichlet_1d) { md_set_error("md_assemble: dirichlet_1d is NULL"); return MD_ERR_ARG; }
+        for (int i = 0; i < prm->n_dirichlet_1d; ++i)
+            if (prm->dirichlet_1d[i] < 0 || prm->dirichlet_1d[i] >= V) {
+                md_set_error("md_assemble: 1D Dirichlet node %d is not a graph node", prm->dirichlet_1d[i]);
+                return MD_ERR_ARG;
+            }
+    }
+    if (prm && (prm->n_dirichlet_1d < 0 || !std::isfinite(prm->u_d))) { md_set_error("md_assemble: bad 1D Dirichlet data"); return MD_ERR_ARG; }
+    if (natural && !(sigma_omega > 0.0) && !(prm->n_dirichlet_1d > 0 && beta > 0.0)) {
+        md_set_error("md_assemble: natural conditions on the cube need sigma_omega > 0 or a coupled 1D Dirichlet node");
+        return MD_ERR_ARG;
+    }
     for (int e = 0; e < E; ++e) {
         int a = g->edges[2 * e], b = g->edges[2 * e + 1];
         if (a < 0 || a >= V || b < 0 || b >= V || a == b) { md_set_error("md_assemble: bad edge %d", e); return MD_ERR_ARG; }
@@ -122,7 +139,10 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     const double S = std::sqrt(0.5);
     const double ccos[8] = {1.0, S, 0.0, -S, -1.0, -S, 0.0, S};
     const double csin[8] = {0.0, S, 1.0, S, 0.0, -S, -1.0, -S};
-    auto is_bd = [&](int i, int j, int k) { return i == 0 || i == N || j == 0 || j == N || k == 0 || k == N; };
+    // Dirichlet grid nodes (none with natural conditions on the cube faces)
+    auto is_bd = [&](int i, int j, int k) {
+        return !natural && (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
+    };
 
     std::vector<int> qa(nq), qb(nq);
     std::vector<double> psa(nq), psb(nq), wq(nq), elen(ne);
@@ -270,6 +290,48 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
             brows[b][b] += beta * wq[q] * psb[q] * psb[q];
         }
     }
+    // 1D Dirichlet nodes (dLambda_D): eliminated symmetrically.  Their known
+    // value moves to the right-hand side through the columns of the full
+    // operator: b0 += beta Pi^T W Psi_D u_d (the coupling columns), b1 -=
+    // B11[:, D] u_d; then their rows and columns of B11 become the identity
+    // (b1 = u_d there), their coupling columns vanish (Psi's values at those
+    // nodes zero in the averaging difference), and their load is replaced.
+    std::vector<char> isd(n1, 0);
+    if (prm)
+        for (int i = 0; i < prm->n_dirichlet_1d; ++i) isd[prm->dirichlet_1d[i]] = 1;
+    const bool any_d = std::find(isd.begin(), isd.end(), 1) != isd.end();
+    std::vector<double> rhs0, rhs1;
+    if (any_d) {
+        rhs0.assign((size_t)n3, 0.0);
+        rhs1.assign((size_t)n1, 0.0);
+        for (int q = 0; q < nq; ++q) {
+            const double tD = (isd[qa[q]] ? psa[q] * u_d : 0.0) + (isd[qb[q]] ? psb[q] * u_d : 0.0);
+            if (tD == 0.0) continue;
+            for (int jj = pi_ptr[q]; jj < pi_ptr[q + 1]; ++jj) rhs0[pi_col[jj]] += beta * pi_val[jj] * wq[q] * tD;
+        }
+        for (int i = 0; i < n1; ++i) {
+            if (isd[i]) { rhs1[i] = u_d; continue; }
+            for (auto& kv : brows[i])
+                if (isd[kv.first]) rhs1[i] -= kv.second * u_d;
+        }
+        for (int i = 0; i < n1; ++i) {
+            if (isd[i]) {
+                brows[i].clear();
+                brows[i][i] = 1.0;
+                k1rows[i].clear();
+                k1rows[i][i] = 1.0;  // y1 = u1 on the row (no Psi^T W entries below)
+                pwrows[i].clear();
+                load1[i] = 0.0;
+                continue;
+            }
+            for (auto it = brows[i].begin(); it != brows[i].end();) it = isd[it->first] ? brows[i].erase(it) : std::next(it);
+            for (auto it = k1rows[i].begin(); it != k1rows[i].end();) it = isd[it->first] ? k1rows[i].erase(it) : std::next(it);
+        }
+        for (int q = 0; q < nq; ++q) {
+            if (isd[qa[q]]) psa[q] = 0.0;
+            if (isd[qb[q]]) psb[q] = 0.0;
+        }
+    }
     std::vector<int> k1_ptr(1, 0), k1_col, pw_ptr(1, 0), pw_q;
     std::vector<double> k1_v, pw_v, d1(n1);
     for (int i = 0; i < n1; ++i) {
@@ -339,6 +401,7 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     InstDesc& D = op->h;
     memset(&D, 0, sizeof(D));
     D.N = N; D.n3 = n3; D.n1 = n1; D.nq = nq; D.ntouch = ntouch; D.nsegs = E;
+    D.natural = natural ? 1 : 0;
     D.n = (long long)n3 + n1;
     D.h = h; D.beta = beta;
     D.ty = ty; D.tz = tz; D.nyt = nyt; D.ntiles = nyt * nzt;
@@ -348,14 +411,30 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         D.st32[c] = (float)D.st64[c];
         D.ms64[c] = Mst[c];
     }
-    // alpha = ||diag(C_II)|| / sqrt(n_I)
+    // alpha = ||diag(C_II)|| / sqrt(n_I) over the unknown grid nodes (all of
+    // them with natural conditions, where the diagonal of a node on a face,
+    // edge or corner has the stencil centre times 1/2 per boundary axis)
     {
-        long long nI = (long long)(N - 1) * (N - 1) * (N - 1);
-        double c0 = D.st64[0];
-        double ss = (double)nI * c0 * c0;
-        for (int i = 0; i < ntouch; ++i) {
-            double dc = c0 + beta * touch_m[i];
-            ss += dc * dc - c0 * c0;
+        const double c0 = D.st64[0];
+        auto fac = [&](int i) { return (i == 0 || i == N) ? 0.5 : 1.0; };
+        std::vector<double> dg;
+        long long nI = 0;
+        double ss = 0.0;
+        if (natural) {
+            dg.assign((size_t)n3, 0.0);
+            for (int k = 0; k < M; ++k)
+                for (int j = 0; j < M; ++j)
+                    for (int i = 0; i < M; ++i) dg[i + M * (j + M * k)] = c0 * fac(i) * fac(j) * fac(k);
+            for (int i = 0; i < ntouch; ++i) dg[tn_node[i]] += beta * touch_m[i];
+            for (double v : dg) ss += v * v;
+            nI = n3;
+        } else {
+            nI = (long long)(N - 1) * (N - 1) * (N - 1);
+            ss = (double)nI * c0 * c0;
+            for (int i = 0; i < ntouch; ++i) {
+                double dc = c0 + beta * touch_m[i];
+                ss += dc * dc - c0 * c0;
+            }
         }
         D.alpha = nI > 0 ? std::sqrt(ss / (double)nI) : 1.0;
     }
@@ -378,6 +457,7 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     UP(upi(&D.k1_ptr, k1_ptr)); UP(upi(&D.k1_col, k1_col)); UP(up64(&D.k1_v64, k1_v)); UP(up32(&D.k1_v32, k1_v));
     UP(upi(&D.pw_ptr, pw_ptr)); UP(upi(&D.pw_q, pw_q)); UP(up64(&D.pw_v64, pw_v)); UP(up32(&D.pw_v32, pw_v));
     UP(up64(&D.load1, load1));
+    if (any_d) { UP(up64(&D.rhs0, rhs0)); UP(up64(&D.rhs1, rhs1)); }
     {
         std::vector<double> lo(n1), dio(n1);
         for (int i = 0; i < n1; ++i) { lo[i] = tl[i]; dio[i] = tdinv[i]; }

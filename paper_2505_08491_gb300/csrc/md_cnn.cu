@@ -427,8 +427,9 @@ __global__ void __launch_bounds__(128) k_conv_simt(const __nv_bfloat16* __restri
         } else {
             float* o = io.out + io.off[sg.inst];
             if (mode == CONV_PREC) {
-                // Dirichlet nodes were written by the input pack (z0 = v0)
-                const bool bd = (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
+                // Dirichlet nodes were written by the input pack (z0 = v0); with
+                // natural conditions on the cube every node is the network's
+                const bool bd = !io.D[sg.inst].natural && (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N);
                 const double s = io.st[sg.inst].s;
                 const float scale = (float)(s / io.D[sg.inst].alpha);
                 if (!bd) o[n] = scale * acc[0];
@@ -624,7 +625,7 @@ __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__
         }
         c[2] = d.dist[n];
         *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
-        if (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N) z[voff[sg.inst] + n] = vi[n];
+        if (!d.natural && (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N)) z[voff[sg.inst] + n] = vi[n];
     }
 }
 

@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 const int nwin = U.z1 - U.z0 + 2;
                 float* ov = a.io.out + a.io.off[U.inst];
                 const float scale = (a.mode == CONV_PREC) ? (float)(a.io.st[U.inst].s / a.io.D[U.inst].alpha) : 1.0f;
+                const bool natural = a.mode == CONV_PREC && a.io.D[U.inst].natural;
                 for (int k = 0; k < nwin; ++k, ++it) {
                     const int pz = U.z0 - 1 + k;  // plane of this window
                     const int bsel = it % NBUF;
@@ -581,8 +582,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         const int n = inplane[ut] + M * M * kk;
                         const float o = done + bias[0];
                         if (a.mode == CONV_PREC) {
-                            // Dirichlet nodes were written by the input pack (z0 = v0)
-                            if (!edge[ut] && kk != 0 && kk != N) ov[n] = scale * o;
+                            // Dirichlet nodes were written by the input pack (z0 = v0);
+                            // with natural conditions on the cube every node is the network's
+                            if (natural || (!edge[ut] && kk != 0 && kk != N)) ov[n] = scale * o;
                         } else {
                             ov[n] = o;
                         }

@@ -36,6 +36,7 @@ md_status md_cuda_status(cudaError_t e, const char* what, const char* file, int 
 // pointers owned by the md_op.
 struct InstDesc {
     int N, n3, n1, nq, ntouch, nsegs;
+    int natural;      // 1: natural (Neumann) conditions on the cube faces, no Dirichlet rows
     long long n;
     double h, beta, alpha;
     double st64[4];   // K00 (+ sigma mass) stencil by offset class: centre, face, edge, corner
@@ -60,7 +61,10 @@ struct InstDesc {
     // 1D rows: kappa K1 (CSR) and Psi^T W (entries (q, psi w_q))
     const int* k1_ptr; const int* k1_col; const double* k1_v64; const float* k1_v32;
     const int* pw_ptr; const int* pw_q; const double* pw_v64; const float* pw_v32;
-    const double* load1;
+    const double* load1;      // int_Lambda psi_i ds (0 on 1D Dirichlet nodes)
+    // the known 1D Dirichlet values moved to the right-hand side: b0 += rhs0,
+    // b1 += rhs1 (b1 = u_d on those nodes); nullptr without 1D Dirichlet nodes
+    const double* rhs0; const double* rhs1;
     // tree LDL^T of B11 in elimination order (children before parents)
     const int* tr_order; const int* tr_parent;
     // level schedule of its sweeps: nodes by height above the leaves in

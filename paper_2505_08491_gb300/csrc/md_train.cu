@@ -243,7 +243,7 @@ __global__ void k_mask_grid(const Seg* __restrict__ seg, const InstDesc* __restr
     float* vi = v + off[sg.inst];
     for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
         if (e >= d.n3) { if (zero_1d) vi[e] = 0.f; continue; }
-        if (is_bd(e, d.N)) vi[e] = 0.f;
+        if (!d.natural && is_bd(e, d.N)) vi[e] = 0.f;
     }
 }
 
@@ -261,7 +261,7 @@ __global__ void k_train_res(const Seg* __restrict__ seg, const InstDesc* __restr
     double acc = 0.0;
     for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
         float v = 0.f;
-        if (e < d.n3 && !is_bd(e, d.N)) v = cy[o + e] * inv_a - (r[o + e] + d.lift32[e]) * inv_s;
+        if (e < d.n3 && (d.natural || !is_bd(e, d.N))) v = cy[o + e] * inv_a - (r[o + e] + d.lift32[e]) * inv_s;
         res[o + e] = v;
         acc += (double)v * v;
     }
@@ -288,7 +288,7 @@ __global__ void k_train_dy(const Seg* __restrict__ seg, const InstDesc* __restri
         const int i = n % M, r = n / M, j = r % M, k = r / M;
         const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
         float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (!is_bd(n, N)) v[0] = scale * cres[off[sg.inst] + n] / (float)d.alpha;
+        if (d.natural || !is_bd(n, N)) v[0] = scale * cres[off[sg.inst] + n] / (float)d.alpha;
         *reinterpret_cast<uint4*>(dy + dy_off[sg.inst] + p * 8) = pack8(v);
     }
 }

@@ -5,11 +5,12 @@ differing sums move a fraction of the hidden activations across a BF16
 rounding boundary (one unit, 2^-8 relative), and a randomly initialised
 six-layer network spreads those flips to every output: a few 1e-3 relative
 L2 (the FP64-vs-BF16 oracle gap itself is ~5e-3).  Tolerance: 1e-2 relative
-L2 for whole networks; single-random-layer networks must agree to 3e-3: the
-GPU's GELU is the tanh form (within 4.8e-4 of x Phi(x), tanh from
-tanh.approx.f32), the oracle's the exact x Phi(x), and the five GELUs the
-other layers pass a channel through add up to ~1.8e-3 relative L2 on N(0,1)
-inputs.  A wrong tap, channel or bias moves outputs by O(1) and fails both."""
+L2 for whole networks; single-random-layer networks must agree to 5e-3: the
+GPU's GELU is the tanh form (within 4.8e-4 of x Phi(x), ~3.6e-4 relative L2
+on N(0,1) inputs) with tanh from tanh.approx.f32 (error about 2^-11, 4.9e-4
+relative), the oracle's the exact x Phi(x), and a channel passes through
+five GELUs: up to 5 x 8.5e-4 = 4.3e-3 (measured 3.3e-3).  A wrong tap,
+channel or bias moves outputs by O(1) and fails both."""
 import numpy as np
 import pytest
 import torch
@@ -110,4 +111,4 @@ def test_single_random_layer(layer):
     Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
     for s in range(2):
         ref = cnn.forward(X[s].astype(np.float64), lay, bf16=True)
-        assert rel_l2(Y[s], ref) <= 3e-3
+        assert rel_l2(Y[s], ref) <= 5e-3
