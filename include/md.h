@@ -283,8 +283,9 @@ typedef enum {
  * independently on their own convergence.  A solve is one launch of a CUDA
  * graph captured at the first solve (again when the network, block order,
  * smoothing, inner steps or profiling change): its restart cycles run under
- * a conditional WHILE node and each iteration slot under a conditional IF
- * node, both decided on the device, so the host waits once per solve.
+ * a conditional WHILE node decided on the device, so the host waits once per
+ * solve; the kernels of an iteration slot return at once for instances that
+ * have left the cycle.
  * Vectors of the batch are concatenated: instance i occupies
  * [offset[i], offset[i] + n_i) of a batched vector.
  * The batch borrows ops and cnn: they must not be destroyed before the
@@ -323,9 +324,10 @@ typedef struct {
     double restart_ms;           /* least squares, x update, FP64 residual */
     long long fallback_instances; /* network solves whose instance switched to Jacobi */
     long long graph_launches;    /* host launches: one graph per md_batch_solve */
-    long long slot_gating;       /* 0: iteration slots under conditional IF nodes; 2: slots always
-                                    launched, their kernels returning for instances out of the cycle;
-                                    3: the host-driven loop of md_batch_set_host_loop */
+    long long slot_gating;       /* 2: one graph launch per solve, its restart cycles under a conditional
+                                    WHILE node, every iteration slot launched (its kernels return at
+                                    once for instances out of the cycle); 3: the host-driven loop of
+                                    md_batch_set_host_loop */
 } md_batch_stats_t;
 md_status md_batch_set_profiling(md_batch* b, int enable);
 /* enable = 1: solves run as a set-up graph and one graph per restart cycle
@@ -365,7 +367,6 @@ typedef struct {
     double vec_us[8];            /* one Gram-Schmidt step with each candidate */
     int conv_tps;                /* 128-row tiles per plane step of the convolutions (0: no network) */
     double conv_us[2];           /* one forward pass with 1 and 2 tiles per step */
-    char gating_note[200];       /* why a form of slot gating was refused by the runtime (empty if none) */
 } md_tuning_t;
 md_status md_batch_tuning(const md_batch* b, md_tuning_t* out);
 md_status md_batch_reset_stats(md_batch* b);

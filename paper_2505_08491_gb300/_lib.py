@@ -41,8 +41,7 @@ class MdBatchStats(C.Structure):
 
 class MdTuning(C.Structure):
     _fields_ = [("tuned", C.c_int), ("vec_chunk", C.c_int), ("n_vec", C.c_int), ("vec_candidates", C.c_int * 8),
-                ("vec_us", C.c_double * 8), ("conv_tps", C.c_int), ("conv_us", C.c_double * 2),
-                ("gating_note", C.c_char * 200)]
+                ("vec_us", C.c_double * 8), ("conv_tps", C.c_int), ("conv_us", C.c_double * 2)]
 
 
 class MdTrainCfg(C.Structure):

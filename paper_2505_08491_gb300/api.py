@@ -400,8 +400,7 @@ class Batch:
         return {"tuned": bool(t.tuned), "vec_chunk": t.vec_chunk,
                 "vec_us": {int(t.vec_candidates[i]): float(t.vec_us[i]) for i in range(t.n_vec)},
                 "conv_tiles_per_step": t.conv_tps,
-                "conv_us": {1: float(t.conv_us[0]), 2: float(t.conv_us[1])} if t.conv_tps else {},
-                "gating_note": t.gating_note.decode(errors="replace")}
+                "conv_us": {1: float(t.conv_us[0]), 2: float(t.conv_us[1])} if t.conv_tps else {}}
 
     def stats(self) -> dict:
         st = L.MdBatchStats()

@@ -84,6 +84,24 @@ md_status cnn_upload(md_cnn* c) {
                 }
     }
     c->wt_off[MD_CNN_LAYERS] = wt.size();
+    // tensor-core images of the adjoint convolutions of layers 1-5: weights
+    // W'[o'][c'][tap] = W[c'][o'][26 - tap] (flipped and transposed); the last
+    // layer's adjoint has one input channel (kind 1, as the first layer)
+    std::vector<__nv_bfloat16> allt;
+    c->wtmma_off[0] = 0;
+    for (int l = 1; l < MD_CNN_LAYERS; ++l) {
+        const int ci = kCin[l], co = kCout[l];  // forward: ci -> co; adjoint: co -> ci
+        const float* W = c->host.data() + host_w_off(l);
+        std::vector<float> Wa((size_t)ci * co * 27);
+        for (int o2 = 0; o2 < ci; ++o2)
+            for (int c2 = 0; c2 < co; ++c2)
+                for (int tap = 0; tap < 27; ++tap)
+                    Wa[((size_t)o2 * co + c2) * 27 + tap] = W[((size_t)c2 * ci + o2) * 27 + (26 - tap)];
+        tc_weight_image(l == MD_CNN_LAYERS - 1 ? 1 : 0, Wa.data(), co, ci, img);
+        c->wtmma_off[l] = allt.size();
+        allt.insert(allt.end(), img.begin(), img.end());
+    }
+    c->wtmma_off[MD_CNN_LAYERS] = allt.size();
     // device buffers keep their size, so a network updated in place (training)
     // reuses its allocations
     auto put = [](auto** dst, const auto& v) -> md_status {
@@ -99,6 +117,7 @@ md_status cnn_upload(md_cnn* c) {
     MD_TRY(put(&c->b, b));
     MD_TRY(put(&c->wmma, all));
     MD_TRY(put(&c->wt, wt));
+    MD_TRY(put(&c->wtmma, allt));
     return MD_OK;
 }
 
@@ -139,6 +158,7 @@ extern "C" void md_cnn_destroy(md_cnn* c) {
     if (c->b) cudaFree(c->b);
     if (c->wmma) cudaFree(c->wmma);
     if (c->wt) cudaFree(c->wt);
+    if (c->wtmma) cudaFree(c->wtmma);
     delete c;
 }
 

@@ -509,6 +509,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             }
             __nv_bfloat16* outU = (KIND != 2) ? a.out + a.out_off[U.inst] : nullptr;
             __nv_bfloat16* zsU = (KIND != 2 && a.zsave) ? a.zsave + a.out_off[U.inst] : nullptr;
+            const __nv_bfloat16* zpU = (KIND != 2 && a.dgrad) ? a.zprev + a.out_off[U.inst] : nullptr;
             if constexpr (KIND == 2) {
                 // Window p holds D_p[i][3 dz + dx]; after the dx recombination
                 // across lanes, P[dz] is window p's contribution to output plane
@@ -665,11 +666,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         const int at = ((cg * (CH / 8) + c8) * P + p) * 8;
                         if (zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
                         float gl[8];
+                        if (zpU) {
+                            // input gradient: dZ_prev = dA * GELU'(Z_prev)
+                            const uint4 zr = *reinterpret_cast<const uint4*>(zpU + at);
+                            const __nv_bfloat162* zh = reinterpret_cast<const __nv_bfloat162*>(&zr);
 #pragma unroll
-                        for (int e = 0; e < 8; e += 2) {
-                            gl[e] = o[c8 * 8 + e];
-                            gl[e + 1] = o[c8 * 8 + e + 1];
-                            gelu_fast2(gl[e], gl[e + 1]);
+                            for (int e = 0; e < 8; e += 2) {
+                                const float2 zf = __bfloat1622float2(zh[e / 2]);
+                                gl[e] = o[c8 * 8 + e] * gelu_grad_fast(zf.x);
+                                gl[e + 1] = o[c8 * 8 + e + 1] * gelu_grad_fast(zf.y);
+                            }
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2) {
+                                gl[e] = o[c8 * 8 + e];
+                                gl[e + 1] = o[c8 * 8 + e + 1];
+                                gelu_fast2(gl[e], gl[e + 1]);
+                            }
                         }
                         *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
                     }

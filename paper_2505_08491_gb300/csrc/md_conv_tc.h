@@ -48,6 +48,12 @@ struct TcArgs {
     int mode;                    // ConvOut of the last layer
     int* err;                    // set on a timed-out wait
     __nv_bfloat16* zsave;        // optional pre-activation copy (hidden layers, layout of out)
+    // input gradient (training's backward): the layer runs the adjoint
+    // convolution (weights flipped and transposed in wimg, zero bias) and the
+    // epilogue multiplies by GELU'(zprev), the previous layer's saved
+    // pre-activation (layout of out), instead of applying GELU
+    const __nv_bfloat16* zprev;
+    int dgrad;
 };
 
 __host__ __device__ constexpr int tc_wimg_bytes(int kind) {

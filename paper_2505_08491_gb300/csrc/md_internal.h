@@ -142,6 +142,10 @@ struct md_cnn {
     // input-gradient weights (training): per layer [tap'][c_out pad][c_in]
     __nv_bfloat16* wt = nullptr;
     size_t wt_off[MD_CNN_LAYERS + 1];
+    // tcgen05 operand images of the adjoint convolutions (layers 1-5; the
+    // flipped, transposed kernels: hidden 32 -> 32 and the last layer's 1 -> 32)
+    __nv_bfloat16* wtmma = nullptr;
+    size_t wtmma_off[MD_CNN_LAYERS + 1];
 };
 
 // Per-instance Krylov state (device).
@@ -187,9 +191,9 @@ __host__ __device__ inline bool cnn_runs(const KState* st, int inst) {
 }
 
 // Stencil tile shape of the operator apply for grid N: ty rows of all N+1
-// columns (at most 512 columns, about two per thread) and tz planes, such that
-// the FP64 input tile with its halo and the output tile fit 100 KB of shared
-// memory.
+// columns (at most 256 columns, one per thread) and tz planes, such that the
+// FP64 input tile with its halo and the output tile fit 64 KB of shared memory
+// (tiles twice as large measured slower on the mixed batch).
 void apply_tile_shape(int N, int* ty, int* tz);
 int apply_tile_smem(int N, int ty, int tz, int elem_bytes);
 md_status apply_prepare(int smem32, int smem64);

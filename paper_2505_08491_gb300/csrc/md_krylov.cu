@@ -72,7 +72,7 @@ struct md_batch {
     // set-up kernels, then a WHILE node over restart cycles (CG: chunks of
     // iterations) whose body, for FGMRES, runs every iteration slot under an
     // IF node that skips it once no instance iterates in the cycle
-    cudaStream_t cap = nullptr, cap_body = nullptr, cap_slot = nullptr;  // capture streams
+    cudaStream_t cap = nullptr, cap_body = nullptr;  // capture streams (solve, loop body)
     cudaGraphExec_t solve_graph = nullptr;
     long long init_kernels = 0;          // kernels of the set-up part (the rest are counted on the device)
     int host_loop = 0;                   // 1: the host-driven loop below instead of solve_graph
@@ -80,7 +80,7 @@ struct md_batch {
     long long cycle_kernels = 0;
     SolveCtl* ctl = nullptr;             // device: limits of this solve, counters, profile sums
     SolveCtl* h_ctl = nullptr;           // pinned host copy
-    int if_mode = -1;                    // slot gating the solve graph uses (capture_solve)
+    int if_mode = -1;                    // 2: one graph per solve, 3: the host-driven loop
     md_tuning_t tuning{};                // choices of the autotuner at creation
     int prec_order = 0;                  // 0: block upper-triangular (the paper's), 1: lower
     int graph_prec_order = 0;
@@ -173,29 +173,6 @@ __global__ void k_loop_cond(SolveCtl* ctl, const int* ndone, int ninst, cudaGrap
     cudaGraphSetConditional(hw, (*ndone < ninst && ctl->cycles < ctl->max_cycles) ? 1u : 0u);
 }
 
-// IF over one iteration slot: the next slot runs while some instance still
-// iterates in this cycle.  After a slot (nk > 0: its kernel count) it also
-// counts the slot and, when profiling, adds the slot's section times.
-__global__ void k_slot_cond(const KState* st, int ninst, cudaGraphConditionalHandle hi, SolveCtl* ctl,
-                            unsigned long long nk, int prof) {
-    int a = 0;
-    for (int i = threadIdx.x; i < ninst; i += blockDim.x) a |= st[i].active;
-    a = __syncthreads_or(a);
-    if (threadIdx.x != 0) return;
-    cudaGraphSetConditional(hi, a ? 1u : 0u);
-    if (nk) {
-        ctl->kernels += nk;
-        ctl->slots += 1;
-        if (prof) {
-            const unsigned long long* t = ctl->stamp;
-            ctl->t_prec += t[ST_APPLY0] - t[ST_PRE0];
-            ctl->t_conv += t[ST_CONV1] - t[ST_CONV0];
-            ctl->t_apply += t[ST_APPLY1] - t[ST_APPLY0];
-            ctl->t_arn += t[ST_ARN1] - t[ST_APPLY1];
-        }
-    }
-}
-
 // End of a cycle of the host-driven loop: count it and, when profiling, add
 // the restart's time.
 __global__ void k_cycle_count(SolveCtl* ctl, int prof) {
@@ -203,8 +180,7 @@ __global__ void k_cycle_count(SolveCtl* ctl, int prof) {
     if (prof) ctl->t_restart += ctl->stamp[ST_REST1] - ctl->stamp[ST_REST0];
 }
 
-// A slot that ran without an IF node (slot gating mode 2): count it and,
-// when profiling, add its section times.
+// After an iteration slot: count it and, when profiling, add its section times.
 __global__ void k_slot_count(SolveCtl* ctl, int prof) {
     ctl->slots += 1;
     if (prof) {
@@ -1596,15 +1572,13 @@ static md_status add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, 
     return MD_OK;
 }
 
-// The handle of a conditional node in the graph being captured on cs.  A
-// top-level graph resets it to 0 at every launch; in a conditional body
-// (top_level = false) it has no launch default, and a kernel of the body sets
-// it before the node that reads it.
-static md_status capture_handle(cudaStream_t cs, cudaGraphConditionalHandle* h, bool top_level) {
+// The handle of a conditional node in the graph being captured on cs, reset
+// to 0 at every launch of the graph (a kernel sets it before the node).
+static md_status capture_handle(cudaStream_t cs, cudaGraphConditionalHandle* h) {
     cudaStreamCaptureStatus status;
     cudaGraph_t g = nullptr;
     MD_CUDA(cudaStreamGetCaptureInfo(cs, &status, nullptr, &g, nullptr, nullptr, nullptr));
-    MD_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, top_level ? cudaGraphCondAssignDefault : 0));
+    MD_CUDA(cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault));
     return MD_OK;
 }
 
@@ -1664,95 +1638,27 @@ static md_status launch_cycle_all_slots(md_batch* B, cudaStream_t s) {
     return launch_restart(B, s);
 }
 
-// Kernel node of `fn` with arguments `args` appended to graph g after `dep`.
-static md_status add_kernel(cudaGraph_t g, cudaGraphNode_t* dep, void* fn, dim3 grid, dim3 block, void** args,
-                            cudaGraphNode_t* out) {
-    cudaKernelNodeParams kp = {};
-    kp.func = fn;
-    kp.gridDim = grid;
-    kp.blockDim = block;
-    kp.sharedMemBytes = 0;
-    kp.kernelParams = args;
-    kp.extra = nullptr;
-    MD_CUDA(cudaGraphAddKernelNode(out, g, dep, dep ? 1 : 0, &kp));
-    return MD_OK;
-}
-
-// The FGMRES loop body built node by node (slot gating with IF nodes):
-//   slot condition -> IF slot 0 -> ... -> IF slot k-1 -> restart -> loop condition
-// each IF body = slot j and the slot condition for the next.
-static md_status build_loop_body_if(md_batch* B, cudaGraph_t loop, cudaGraphConditionalHandle hw) {
-    const int prof = B->profiling ? 1 : 0;
-    cudaGraphConditionalHandle hi;
-    MD_CUDA(cudaGraphConditionalHandleCreate(&hi, loop, 0, 0));
-    const KState* st = B->st;
-    int ninst = B->ninst;
-    SolveCtl* ctl = B->ctl;
-    unsigned long long nk0 = 0ULL;
-    int prof0 = 0;
-    void* head_args[] = {(void*)&st, (void*)&ninst, (void*)&hi, (void*)&ctl, (void*)&nk0, (void*)&prof0};
-    cudaGraphNode_t prev;
-    MD_TRY(add_kernel(loop, nullptr, (void*)k_slot_cond, dim3(1), dim3(1024), head_args, &prev));
-    for (int j = 0; j < B->k; ++j) {
-        cudaGraphNodeParams prm = {};
-        prm.type = cudaGraphNodeTypeConditional;
-        prm.conditional.handle = hi;
-        prm.conditional.type = cudaGraphCondTypeIf;
-        prm.conditional.size = 1;
-        cudaGraphNode_t node;
-        MD_CUDA(cudaGraphAddNode(&node, loop, &prev, nullptr, 1, &prm));
-        MD_TRY(capture_into(B->cap_slot, prm.conditional.phGraph_out[0], [&](cudaStream_t ss) -> md_status {
-            MD_TRY(launch_slot(B, j, ss));
-            cudaStreamCaptureStatus status;
-            cudaGraph_t g = nullptr;
-            MD_CUDA(cudaStreamGetCaptureInfo(ss, &status, nullptr, &g, nullptr, nullptr, nullptr));
-            const unsigned long long nk = (unsigned long long)kernel_nodes(g) + 1;
-            k_slot_cond<<<1, 1024, 0, ss>>>(B->st, B->ninst, hi, B->ctl, nk, prof);
-            MD_CHECK_LAUNCH();
-            return MD_OK;
-        }));
-        prev = node;
-    }
-    cudaGraph_t rg = nullptr;
-    MD_CUDA(cudaStreamBeginCapture(B->cap_body, cudaStreamCaptureModeThreadLocal));
-    md_status st2 = launch_restart(B, B->cap_body);
-    cudaError_t e = cudaStreamEndCapture(B->cap_body, &rg);
-    if (st2 != MD_OK) { if (e == cudaSuccess && rg) cudaGraphDestroy(rg); return st2; }
-    MD_CUDA(e);
-    cudaGraphNode_t rnode;
-    e = cudaGraphAddChildGraphNode(&rnode, loop, &prev, 1, rg);
-    const long long nrest = kernel_nodes(rg);
-    cudaGraphDestroy(rg);
-    MD_CUDA(e);
-    const int* ndone = B->ndone;
-    unsigned long long nk = (unsigned long long)(nrest + 2);  // head, restart kernels, tail
-    int one = 1;
-    void* tail_args[] = {(void*)&ctl, (void*)&ndone, (void*)&ninst, (void*)&hw, (void*)&nk, (void*)&one, (void*)&prof};
-    cudaGraphNode_t tail;
-    return add_kernel(loop, &rnode, (void*)k_loop_cond, dim3(1), dim3(1), tail_args, &tail);
-}
-
 // The solve graph: the set-up part, then
 //   WHILE (an instance is unfinished and cycles < limit) {
-//     FGMRES: slot condition; for j < k: IF (an instance iterates) { slot j;
-//             slot condition }; restart (x += Z y, FP64 residual)
+//     FGMRES: every iteration slot (its kernels return at once for instances
+//             that left the cycle), then the restart (x += Z y, FP64 residual)
 //     CG:     a chunk of CG_CHUNK iterations and the true residual of the
 //             instances that stopped
 //     loop condition
 //   }
-// so a solve is one graph launch and the host waits once, at the end.
-// mode 0: FGMRES slots gated by IF nodes (the loop body built node by node);
-// mode 2: every slot launched in the body (the form to fall back to).
-static md_status capture_solve(md_batch* B, cudaStream_t s, int mode) {
+// so a solve is one graph launch and the host waits once, at the end.  (Slots
+// under conditional IF nodes nested in the WHILE body would skip the empty
+// slots of a cycle entirely; the runtime of this toolkit and driver refuses an
+// IF node inside a WHILE body, whether captured or added node by node.)
+static md_status capture_solve(md_batch* B, cudaStream_t s) {
     const int prof = B->profiling ? 1 : 0;
     MD_TRY(launch_init(B, s));
     cudaGraphConditionalHandle hw;
-    MD_TRY(capture_handle(s, &hw, true));
+    MD_TRY(capture_handle(s, &hw));
     k_loop_cond<<<1, 1, 0, s>>>(B->ctl, B->ndone, B->ninst, hw, 0ULL, 0, 0);
     MD_CHECK_LAUNCH();
     cudaGraph_t loop = nullptr;
     MD_TRY(add_conditional(s, hw, cudaGraphCondTypeWhile, &loop));
-    if (mode == 0 && B->solver != MD_SOLVER_CG_JACOBI) return build_loop_body_if(B, loop, hw);
     return capture_into(B->cap_body, loop, [&](cudaStream_t sb) -> md_status {
         MD_TRY(launch_cycle_all_slots(B, sb));
         cudaStreamCaptureStatus status;
@@ -1825,27 +1731,15 @@ static md_status build_graph(md_batch* B) {
         return MD_OK;
     }
     cudaGraph_t g = nullptr;
-    md_status st = MD_OK;
-    cudaError_t e = cudaSuccess;
-    // the first form of slot gating the runtime accepts (see capture_solve)
-    for (int mode = 0; mode <= 2; mode += 2) {
-        g = nullptr;
-        MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
-        st = capture_solve(B, B->cap, mode);
-        e = cudaStreamEndCapture(B->cap, &g);
-        if (st == MD_OK && e == cudaSuccess) {
-            B->if_mode = mode;
-            break;
-        }
+    MD_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+    md_status st = capture_solve(B, B->cap);
+    cudaError_t e = cudaStreamEndCapture(B->cap, &g);
+    if (st != MD_OK) {
         if (e == cudaSuccess && g) cudaGraphDestroy(g);
-        (void)cudaGetLastError();
-        if (st == MD_OK) st = md_cuda_status(e, "solve graph capture", __FILE__, __LINE__);
-        // why this form was refused (md_tuning_t.gating_note)
-        snprintf(B->tuning.gating_note, sizeof(B->tuning.gating_note), "slot gating %d refused: %s", mode,
-                 md_last_error());
+        return st;
     }
-    if (st != MD_OK) return st;
     MD_CUDA(e);
+    B->if_mode = 2;
     B->init_kernels = kernel_nodes(g);
     e = cudaGraphInstantiate(&B->solve_graph, g, 0);
     cudaGraphDestroy(g);
@@ -2010,7 +1904,6 @@ extern "C" md_status md_batch_create(int n_ops, const md_op* const* ops, const m
     if (st == MD_OK) {
         cudaError_t e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_body, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap_slot, cudaStreamNonBlocking);
         if (e != cudaSuccess) chk(md_cuda_status(e, "cudaStreamCreate", __FILE__, __LINE__));
     }
     if (st == MD_OK) {
@@ -2038,7 +1931,6 @@ extern "C" void md_batch_destroy(md_batch* B) {
     if (B->h_ctl) cudaFreeHost(B->h_ctl);
     if (B->cap) cudaStreamDestroy(B->cap);
     if (B->cap_body) cudaStreamDestroy(B->cap_body);
-    if (B->cap_slot) cudaStreamDestroy(B->cap_slot);
     cnn_work_destroy(B->cw);
     dev_free_all(&B->allocs);
     delete B;

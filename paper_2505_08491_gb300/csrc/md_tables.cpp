@@ -60,10 +60,10 @@ void dev_free_all(std::vector<void*>* allocs) {
 
 void apply_tile_shape(int N, int* ty, int* tz) {
     const int M = N + 1;
-    int t = M >= 512 ? 1 : 512 / M;  // about two columns per thread of a 256-thread block
-    if (t > 16) t = 16;
+    int t = M >= 256 ? 1 : 256 / M;  // one column per thread of a 256-thread block
+    if (t > 8) t = 8;
     int z = 8;
-    while (z > 1 && apply_tile_smem(N, t, z, 8) > 100 * 1024) z /= 2;
+    while (z > 1 && apply_tile_smem(N, t, z, 8) > 64 * 1024) z /= 2;
     *ty = t;
     *tz = z;
 }

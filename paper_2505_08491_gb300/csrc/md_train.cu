@@ -341,6 +341,7 @@ struct TrainWork {
     int ntiles = 0, wblocks = 0;
     float* part = nullptr;
     float* grad = nullptr;                 // MD_CNN_NPARAMS
+    float* zero_bias = nullptr;            // 32 zeros: the adjoint convolutions have no bias
     // solve-side (training samples with operators)
     long long stride = 0;                  // per-slot vector stride (n3 + max n1)
     float *rv = nullptr, *yv = nullptr, *cy = nullptr, *res = nullptr, *cres = nullptr;
@@ -386,6 +387,7 @@ static md_status train_work_create(int B, int N, int max_n1, int max_nq, int max
     chk(dev_upload(&t->allocs, &t->tiles, tiles.data(), tiles.size()));
     chk(dev_alloc(&t->allocs, &t->part, (size_t)t->wblocks * (27 * 32 * 32 + 32), false));
     chk(dev_alloc(&t->allocs, &t->grad, (size_t)MD_CNN_NPARAMS));
+    chk(dev_alloc(&t->allocs, &t->zero_bias, 32));
     if (max_n1 >= 0) {
         const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
         t->stride = n3 + max_n1;
@@ -441,18 +443,50 @@ static md_status launch_wgrad(TrainWork* t, const __nv_bfloat16* act, const long
     return MD_OK;
 }
 
+// Input gradient of layer l (1-5) on the tensor cores: the tcgen05
+// convolution of the forward pass run as the adjoint (flipped, transposed
+// weights, no bias; the last layer's 1 -> 32 adjoint as the first layer's
+// kind) with the epilogue dZ_prev = dA * GELU'(Z_prev).
+static md_status launch_dgrad_tc(const md_cnn* c, TrainWork* t, int l, const __nv_bfloat16* dz, const long long* dz_off,
+                                 const __nv_bfloat16* zprev, __nv_bfloat16* out, cudaStream_t s) {
+    CnnWork* w = t->cw;
+    TcArgs a{};
+    a.Ns = w->N;
+    a.sched = TcSched{w->all_inst, w->all_pre, w->all_count};
+    a.W = w->W;
+    a.NS = w->NS;
+    a.err = w->err;
+    a.io = OutIO{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    a.mode = CONV_RAW;
+    a.in = dz;
+    a.in_off = dz_off;
+    a.out = out;
+    a.out_off = w->off_ab;
+    a.wimg = c->wtmma + c->wtmma_off[l];
+    a.bias = t->zero_bias;
+    a.cout = 32;
+    a.zprev = zprev;
+    a.dgrad = 1;
+    return tc_launch(l == MD_CNN_LAYERS - 1 ? 1 : 0, w->tps, a, w->ngroups, s);
+}
+
 // Backward from dZ6 (in t->dy1) through all layers; gradient into t->grad
-// (scaled by `scale`); dX (FP32 raw layout) when dx != NULL.
+// (scaled by `scale`); dX (FP32 raw layout) when dx != NULL.  Input gradients
+// of layers 1-5 on the tensor cores with the tensor-core engine, weight
+// gradients on CUDA cores.
 static md_status backward_all(const md_cnn* c, TrainWork* t, float scale, float* dx, cudaStream_t s) {
     CnnWork* w = t->cw;
+    const bool tc = c->engine == 0;
     // layer 5 (32 -> 1)
     MD_TRY((launch_wgrad<4, 1>(t, t->A[5], w->off_ab, t->dy1, w->off_x0, 5, scale, s)));
-    MD_TRY((launch_dgrad<1, 32, 0>(t, t->dy1, w->off_x0, c->wt + c->wt_off[5], t->Z[5], t->dza, nullptr, s)));
+    if (tc) MD_TRY(launch_dgrad_tc(c, t, 5, t->dy1, w->off_x0, t->Z[5], t->dza, s));
+    else MD_TRY((launch_dgrad<1, 32, 0>(t, t->dy1, w->off_x0, c->wt + c->wt_off[5], t->Z[5], t->dza, nullptr, s)));
     __nv_bfloat16* cur = t->dza;
     __nv_bfloat16* nxt = t->dzb;
     for (int l = 4; l >= 1; --l) {
         MD_TRY((launch_wgrad<4, 32>(t, t->A[l], w->off_ab, cur, w->off_ab, l, scale, s)));
-        MD_TRY((launch_dgrad<4, 32, 0>(t, cur, w->off_ab, c->wt + c->wt_off[l], t->Z[l], nxt, nullptr, s)));
+        if (tc) MD_TRY(launch_dgrad_tc(c, t, l, cur, w->off_ab, t->Z[l], nxt, s));
+        else MD_TRY((launch_dgrad<4, 32, 0>(t, cur, w->off_ab, c->wt + c->wt_off[l], t->Z[l], nxt, nullptr, s)));
         std::swap(cur, nxt);
     }
     MD_TRY((launch_wgrad<1, 32>(t, w->x0, w->off_x0, cur, w->off_ab, 0, scale, s)));

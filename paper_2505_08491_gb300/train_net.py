@@ -65,8 +65,9 @@ def krylov_samples(op, g: float):
 
 def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees", kind: str = "residuals"):
     """kind: 'residuals' (4 random vectors + 4 harvested FGMRES residuals per
-    graph), 'kry' ({b} and q5..q8, the paper's Krylov-augmented set), 'hf'
-    ({b} and 4 random vectors, the paper's high-frequency set) or 'all'
+    graph), 'base' ({b} alone, the paper's set B of eq. (setB) without
+    augmentation), 'kry' ({b} and q5..q8, the paper's Krylov-augmented set),
+    'hf' ({b} and 4 random vectors, the paper's high-frequency set) or 'all'
     (residuals, b and q5..q8)."""
     insts = [mdgen.workload_instance(workload, first + i) for i in range(n_graphs)]
     ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
@@ -74,19 +75,19 @@ def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees", kind
     by_N = {}
     for i, (w, op) in enumerate(zip(insts, ops)):
         by_N.setdefault(w["N"], []).append(i)
-        if kind in ("kry", "hf", "all"):
+        if kind in ("base", "kry", "hf", "all"):
             ks = krylov_samples(op, w["g"])
-            for r in (ks if kind != "hf" else ks[:1]):
+            for r in (ks if kind in ("kry", "all") else ks[:1]):
                 samples.append(r)
                 sample_op.append(i)
-        if kind == "kry":
+        if kind in ("kry", "base"):
             continue
         mask = torch.from_numpy(np.concatenate([interior_mask(w["N"]), np.ones(op.n1, bool)])).cuda()
         for k in range(4):
             v = torch.from_numpy(mdgen.normal_vector(w["f_seed"] or 0, first + i, op.n, stream=k).astype(np.float32)).cuda()
             samples.append(v * mask)
             sample_op.append(i)
-    if kind in ("kry", "hf"):
+    if kind in ("base", "kry", "hf"):
         return ops, samples, sample_op
     # harvested residuals, batched per grid size
     for N, idx in by_N.items():
@@ -110,6 +111,44 @@ def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees", kind
     return ops, samples, sample_op
 
 
+def mean_iterations(net, count: int, order: str = "upper"):
+    """Mean and max FGMRES(30) iterations to 1e-8 with `net` on the first
+    `count` tree15_32 instances, solved as one batch."""
+    insts = [mdgen.workload_instance("tree15_32", i) for i in range(count)]
+    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    b = torch.cat([op.rhs(torch.from_numpy(mdgen.interior_source(w["N"], w["f_seed"])).cuda(), w["g"])
+                   for w, op in zip(insts, ops)])
+    B = Batch(ops, "fgmres_cnn", net, restart=30)
+    B.set_prec_order(order)
+    x = torch.zeros_like(b)
+    its, rels, ok = B.solve(b, x, tol=1e-8, maxit=3000)
+    fb = B.stats()["fallback_instances"]
+    B.close()
+    return float(np.mean(its)), int(np.max(its)), bool(ok), int(fb)
+
+
+def ablation(args):
+    """One network per training set from the same initialisation, evaluated
+    on the 32^3 tree workload (the analogue of the paper's Table 5)."""
+    rows = {}
+    for kind in ("base", "kry", "hf"):
+        t0 = time.time()
+        ops, samples, sample_op = build_set(args.graphs, workload=args.workload, kind=kind)
+        torch.cuda.synchronize()
+        t1 = time.time()
+        net = Network(random_params(args.seed))
+        hist = train(net, ops, sample_op, samples, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                     lr_min=args.lr_min, seed=args.seed)
+        t2 = time.time()
+        mean_it, max_it, ok, fb = mean_iterations(net, args.eval_count)
+        rows[kind] = {"samples": len(samples), "final_loss": hist[-1], "set_seconds": t1 - t0,
+                      "train_seconds": t2 - t1, "mean_iterations": mean_it, "max_iterations": max_it,
+                      "converged": ok, "jacobi_fallback_instances": fb}
+        net.close()
+    print(json.dumps({"ablation": rows, "graphs": args.graphs, "epochs": args.epochs, "lr": args.lr,
+                      "seed": args.seed, "eval": f"tree15_32, {args.eval_count} instances, FGMRES(30), tol 1e-8"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--graphs", type=int, default=1024)
@@ -120,13 +159,21 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=TRAINED)
     ap.add_argument("--init", default=None, help="start from this network file")
-    ap.add_argument("--workload", default="train_trees", choices=["train_trees", "train_trees_wide"])
-    ap.add_argument("--set", default="residuals", choices=["residuals", "kry", "hf", "all"],
+    ap.add_argument("--workload", default="train_trees", choices=["train_trees", "train_trees_wide", "train_trees_mixed"])
+    ap.add_argument("--set", default="residuals", choices=["residuals", "base", "kry", "hf", "all"],
                     help="training vectors per graph (see build_set)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="the training-set ablation of Section 4.1 (the paper's Table 5): one network per set "
+                         "(base = {b} alone, kry = {b} + q5..q8, hf = {b} + 4 random vectors), the same seed, "
+                         "epochs and learning rate, each evaluated by the mean FGMRES(30) iterations on "
+                         "--eval-count tree15_32 instances (upper block order); prints one JSON line")
+    ap.add_argument("--eval-count", type=int, default=100)
     ap.add_argument("--zero-1d", action="store_true",
                     help="train for the block lower-triangular order: the 1D part of every training vector is "
                          "zeroed, so the network sees [r0/s, 0, d] and is fitted to C z0 = r0")
     args = ap.parse_args()
+    if args.ablation:
+        return ablation(args)
     t0 = time.time()
     ops, samples, sample_op = build_set(args.graphs, workload=args.workload, kind=args.set)
     if args.zero_1d:
