@@ -16,9 +16,7 @@
 
 template <typename T>
 __device__ inline T gather_q(const InstDesc& d, const T* __restrict__ u0, const T* __restrict__ u1, int q) {
-    const T* pv = Pr<T>::pi(d);
-    T acc = T(0);
-    for (int jj = d.pi_ptr[q]; jj < d.pi_ptr[q + 1]; ++jj) acc += pv[jj] * u0[d.pi_col[jj]];
+    const T acc = csr_row<T, T>(d.pi_col, Pr<T>::pi(d), d.pi_ptr[q], d.pi_ptr[q + 1], u0);
     return acc - (Pr<T>::psa(d)[q] * u1[d.qa[q]] + Pr<T>::psb(d)[q] * u1[d.qb[q]]);
 }
 
@@ -208,8 +206,7 @@ __device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __rest
     const T* tq = Pr<T>::t(d);
     const T beta = (T)d.beta;
     for (int idx = d.tile_tptr[tile] + threadIdx.x; idx < d.tile_tptr[tile + 1]; idx += blockDim.x) {
-        T acc = T(0);
-        for (int jj = d.tn_ptr[idx]; jj < d.tn_ptr[idx + 1]; ++jj) acc += tv[jj] * tq[d.tn_q[jj]];
+        const T acc = csr_row<T, T>(d.tn_q, tv, d.tn_ptr[idx], d.tn_ptr[idx + 1], tq);
         const int n = d.tn_node[idx];
         const int zy = n / M, x = n - zy * M, z = zy / M, y = zy - z * M;
         s_out[((size_t)(z - z0) * ny + (y - y0)) * M + x] += beta * acc;
@@ -224,7 +221,7 @@ __device__ inline void stencil_tile(const InstDesc& d, int tile, const T* __rest
 }
 
 template <typename T>
-__global__ void __launch_bounds__(MD_TB) k_apply_b(const InstDesc* __restrict__ D, const Seg* __restrict__ seg,
+__global__ void __launch_bounds__(MD_TB, 5) k_apply_b(const InstDesc* __restrict__ D, const Seg* __restrict__ seg,
                                                    const long long* __restrict__ off, const T* __restrict__ u,
                                                    T* __restrict__ y, const KState* __restrict__ st, int gate) {
     extern __shared__ __align__(16) unsigned char apply_smem[];
@@ -244,9 +241,8 @@ __global__ void __launch_bounds__(MD_TB) k_apply_b(const InstDesc* __restrict__ 
     const T* kv = Pr<T>::k1(d);
     const T* pv = Pr<T>::pw(d);
     for (int i = sg.begin + threadIdx.x; i < sg.end; i += blockDim.x) {
-        T a1 = T(0), a2 = T(0);
-        for (int jj = d.k1_ptr[i]; jj < d.k1_ptr[i + 1]; ++jj) a1 += kv[jj] * u1[d.k1_col[jj]];
-        for (int jj = d.pw_ptr[i]; jj < d.pw_ptr[i + 1]; ++jj) a2 += pv[jj] * t[d.pw_q[jj]];
+        const T a1 = csr_row<T, T>(d.k1_col, kv, d.k1_ptr[i], d.k1_ptr[i + 1], u1);
+        const T a2 = csr_row<T, T>(d.pw_q, pv, d.pw_ptr[i], d.pw_ptr[i + 1], t);
         y1[i] = a1 - beta * a2;
     }
 }

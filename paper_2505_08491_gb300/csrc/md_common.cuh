@@ -27,6 +27,33 @@ template <> struct Pr<double> {
     __device__ static const double* dinv(const InstDesc& d) { return d.dinv64; }
 };
 
+// One row of a CSR product, sum over jj in [j0, j1) of vals[jj] x[cols[jj]],
+// added in row order.  The column indices of eight entries are loaded before
+// any value they point to, so a row costs about two memory round trips per
+// eight entries instead of two per entry (the gathers from x depend on the
+// index loads).
+template <typename T, typename V>
+__device__ __forceinline__ T csr_row(const int* __restrict__ cols, const V* __restrict__ vals, int j0, int j1,
+                                     const T* __restrict__ x) {
+    T acc = T(0);
+    for (int jb = j0; jb < j1; jb += 8) {
+        int c[8];
+        T v[8], xv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const bool in = jb + k < j1;
+            c[k] = in ? cols[jb + k] : 0;
+            v[k] = in ? (T)vals[jb + k] : T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) xv[k] = (jb + k < j1) ? x[c[k]] : T(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (jb + k < j1) acc += v[k] * xv[k];
+    }
+    return acc;
+}
+
 // Block-wide sum of R values per thread (FP64), result valid in thread 0.
 // `sh` must hold R * 32 doubles.
 template <int R>

@@ -727,22 +727,22 @@ static md_status launch_one(const TcArgs& a, int grid, cudaStream_t s) {
 int tc_window_rows(int tps, int pd_max) { return (tc_window_load_rows(tps, pd_max) + 7) & ~7; }
 
 // Kernel attributes are set once per window size, outside stream capture.
+// The kernels' dynamic shared memory limit only grows: workspaces of several
+// grid sizes (training groups them by N) need different window rows W and ring
+// slots, and a larger W can take less shared memory than a smaller one (fewer
+// slots fit), so the limit set is the largest any workspace needed.
 md_status tc_prepare(int W, int tps) {
-    static int done[3] = {-1, -1, -1};
-    if (done[tps] == W) return MD_OK;
+    static int set[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // [tps][kind]
     const int ns = tc_ring_slots(W);
     if (ns == 0) { md_set_error("conv tile window too large for shared memory"); return MD_ERR_ARG; }
-    const int s0 = tc_smem_bytes(0, W, ns), s1 = tc_smem_bytes(1, W, ns), s2 = tc_smem_bytes(2, W, ns);
-    if (tps == 2) {
-        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
-        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
-        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
-    } else {
-        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s0));
-        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1));
-        MD_CUDA(cudaFuncSetAttribute(k_conv_tc<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2));
+    const int need[3] = {tc_smem_bytes(0, W, ns), tc_smem_bytes(1, W, ns), tc_smem_bytes(2, W, ns)};
+    const void* fn[2][3] = {{(const void*)k_conv_tc<0, 1>, (const void*)k_conv_tc<1, 1>, (const void*)k_conv_tc<2, 1>},
+                            {(const void*)k_conv_tc<0, 2>, (const void*)k_conv_tc<1, 2>, (const void*)k_conv_tc<2, 2>}};
+    for (int k = 0; k < 3; ++k) {
+        if (need[k] <= set[tps][k]) continue;
+        MD_CUDA(cudaFuncSetAttribute(fn[tps - 1][k], cudaFuncAttributeMaxDynamicSharedMemorySize, need[k]));
+        set[tps][k] = need[k];
     }
-    done[tps] = W;
     return MD_OK;
 }
 

@@ -666,11 +666,8 @@ __global__ void __launch_bounds__(MD_TB) k_gather_z0(const InstDesc* __restrict_
     if (!cnn_runs(st, sg.inst)) return;
     const InstDesc& d = D[sg.inst];
     const float* z0 = z + off[sg.inst];
-    for (int q = sg.begin + threadIdx.x; q < sg.end; q += blockDim.x) {
-        float a = 0.f;
-        for (int jj = d.pi_ptr[q]; jj < d.pi_ptr[q + 1]; ++jj) a += d.pi_v32[jj] * z0[d.pi_col[jj]];
-        d.t32[q] = a;
-    }
+    for (int q = sg.begin + threadIdx.x; q < sg.end; q += blockDim.x)
+        d.t32[q] = csr_row<float, float>(d.pi_col, d.pi_v32, d.pi_ptr[q], d.pi_ptr[q + 1], z0);
 }
 
 // Lower block order, 1D part after the network: z1 = B11^{-1} (v1 + beta Psi^T W Pi z0),
@@ -690,11 +687,8 @@ __global__ void __launch_bounds__(TREE_TB) k_lower_1d(const InstDesc* __restrict
     const long long o = off[inst];
     const float beta = (float)d.beta;
     const float* v1 = v + o + d.n3;
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
-        float a = 0.f;
-        for (int jj = d.pw_ptr[i]; jj < d.pw_ptr[i + 1]; ++jj) a += d.pw_v32[jj] * t[d.pw_q[jj]];
-        y[i] = v1[i] + beta * a;
-    }
+    for (int i = threadIdx.x; i < n1; i += blockDim.x)
+        y[i] = v1[i] + beta * csr_row<float, float>(d.pw_q, d.pw_v32, d.pw_ptr[i], d.pw_ptr[i + 1], t);
     __syncthreads();
     tree_solve_levels(d, tr);
     float* z1 = z + o + d.n3;
