@@ -82,10 +82,20 @@ DEFAULT_ORDER = {"tree15_32": "upper", "batch256_mixed": "lower", "transfer_64":
 # paper's setting, whose tolerance of 1e-15 lies at the FP64 rounding floor
 # of the true residual of those systems
 WORKLOAD_TOL = {"paper_21": 1e-12}
+# the paper's setting: its network and its 3D block solve (three inner
+# P-FGMRES steps, Section 6)
+PAPER_SETTING = {"paper_21"}
+DEFAULT_INNER = {"paper_21": 3}
 
 
 def tol_of(workload: str) -> float:
     return WORKLOAD_TOL.get(workload, TOL)
+
+
+def network_params(workload: str, order: str):
+    """The shipped network for the workload's setting and block order."""
+    from paper_2505_08491_gb300.weights import default_network_params, paper_network_params
+    return paper_network_params() if workload in PAPER_SETTING else default_network_params(order)
 
 
 def make_operator(w):
@@ -280,8 +290,7 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_2505_08491_gb300.weights import default_network_params
-    params = default_network_params(args.prec_order)
+    params = network_params(args.workload, args.prec_order)
     sample = _reference_sample(args.workload, args.count)
     rs = restart_of(args.workload)
     tol = tol_of(args.workload)
@@ -362,8 +371,8 @@ def extra_workload(name: str, steps: int, flush):
     import torch
 
     from paper_2505_08491_gb300 import Batch, Network, Operator
-    from paper_2505_08491_gb300.weights import default_network_params
     order = DEFAULT_ORDER[name]
+    inner = DEFAULT_INNER.get(name, 0)
     tol = tol_of(name)
     insts = instances(name, 0, DEFAULT_COUNT[name])
     ops = [make_operator(w) for w in insts]
@@ -372,12 +381,15 @@ def extra_workload(name: str, steps: int, flush):
                                         for w, op in zip(insts, ops))]).contiguous()
     x_all = torch.zeros_like(b_all)
     stream = torch.cuda.current_stream()
-    out = {"workload": f"{name}: {len(insts)} {WORKLOAD_TEXT[name]}", "prec_order": order, "tol": tol}
+    out = {"workload": f"{name}: {len(insts)} {WORKLOAD_TEXT[name]}", "prec_order": order, "tol": tol,
+           "inner_fgmres_steps": inner}
     for solver in ("fgmres_cnn", "cg_jacobi"):
         if solver == "fgmres_cnn":
-            net = Network(default_network_params(order))
+            net = Network(network_params(name, order))
             B = Batch(ops, solver, net, restart=restart_of(name))
             B.set_prec_order(order)
+            if inner:
+                B.set_inner_iters(inner)
         else:
             B = Batch(ops, solver)
         for _ in range(3):
@@ -414,8 +426,9 @@ def main():
     ap.add_argument("--smooth", type=int, default=0,
                     help="damped Jacobi sweeps before and after the network in the 3D solve (0: none)")
     ap.add_argument("--omega", type=float, default=None, help="damping of those sweeps (default: the package's SMOOTH_OMEGA, 2/3)")
-    ap.add_argument("--inner", type=int, default=0,
-                    help="the 3D block solve as this many inner FGMRES steps with the network (0: one application)")
+    ap.add_argument("--inner", type=int, default=None,
+                    help="the 3D block solve as this many inner FGMRES steps with the network (0: one application; "
+                         "default: 3 for the paper's setting, as in its Section 6, else 0)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workload measurements")
@@ -437,6 +450,8 @@ def main():
         args.count = DEFAULT_COUNT[args.workload]
     if args.prec_order is None:
         args.prec_order = DEFAULT_ORDER[args.workload]
+    if args.inner is None:
+        args.inner = DEFAULT_INNER.get(args.workload, 0)
     if args.omega is None:
         from paper_2505_08491_gb300 import SMOOTH_OMEGA
         args.omega = SMOOTH_OMEGA
@@ -447,7 +462,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2505_08491_gb300 import Batch, Network
-    from paper_2505_08491_gb300.weights import default_network_params, read_network_file
+    from paper_2505_08491_gb300.weights import read_network_file
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -467,7 +482,7 @@ def main():
     ops = [make_operator(w) for w in insts]
     torch.cuda.synchronize()
     assembly_s = (time.perf_counter() - t_asm) / len(ops)
-    params = default_network_params(args.prec_order) if not args.weights else read_network_file(args.weights)
+    params = network_params(args.workload, args.prec_order) if not args.weights else read_network_file(args.weights)
     net = Network(params)
     bs = []
     for w, op in zip(insts, ops):

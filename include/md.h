@@ -354,7 +354,7 @@ md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
 /* Autotuning.  A network- or Jacobi-preconditioned FGMRES batch of at least
  * 10^6 unknowns times its launch choices on the GPU when it is created and
  * keeps the fastest: the elements per block of its Krylov vector kernels
- * (candidates 2048-16384, timed on a Gram-Schmidt step over the whole batch)
+ * (candidates 4096-32768, timed on Gram-Schmidt steps over the whole batch)
  * and the 128-row tiles per plane step of its tensor-core convolutions (1 or
  * 2, timed on a forward pass over every grid).  Smaller batches keep the
  * defaults (8192 elements, 2 tiles; CG batches 2048 elements).
@@ -364,7 +364,8 @@ typedef struct {
     int vec_chunk;               /* elements per block of the Krylov vector kernels */
     int n_vec;
     int vec_candidates[8];
-    double vec_us[8];            /* one Gram-Schmidt step with each candidate */
+    double vec_us[8];            /* Gram-Schmidt steps at basis lengths 6, 14, 22, 30 (those below
+                                    the restart length), summed, with each candidate */
     int conv_tps;                /* 128-row tiles per plane step of the convolutions (0: no network) */
     double conv_us[2];           /* one forward pass with 1 and 2 tiles per step */
 } md_tuning_t;

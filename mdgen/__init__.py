@@ -170,6 +170,10 @@ WORKLOADS = {
     "paper_21": dict(N=20, beta=2.0 * np.pi * 1e-3, kind="tree", depth=(1, 7), elems=8, radius=(1e-3, 1e-3),
                      f="zero", g=0.0, tol=1e-15, restart=20, seed=5_000_000,
                      physics=dict(k_omega=1e-3, sigma_omega=1e-3, dirichlet=False, dirichlet_1d=(0,), u_d=1.0)),
+    # training graphs of the paper's setting: the same physics and sizes as paper_21, seeds disjoint
+    "train_paper_21": dict(N=20, beta=2.0 * np.pi * 1e-3, kind="tree", depth=(1, 7), elems=8, radius=(1e-3, 1e-3),
+                           f="zero", g=0.0, seed=8_000_000,
+                           physics=dict(k_omega=1e-3, sigma_omega=1e-3, dirichlet=False, dirichlet_1d=(0,), u_d=1.0)),
 }
 
 

@@ -237,7 +237,10 @@ __device__ __forceinline__ bool walk_next(const TcSched& sc, const int* Ns, TcWa
 // [w Pd^2 + s0 - 1 - Pd, + TPS*126 + 2 Pd + 10) of every input chunk; plane z
 // reads windows z-1, z, z+1, so each copied window serves three planes.
 // Windows go round a ring of NS shared-memory slots.
-template <int KIND, int TPS>
+//
+// GEN = 0: the plain forward epilogue (no pre-activation saved, no input
+// gradient), compiled without those branches; GEN = 1 reads a.zsave / a.dgrad.
+template <int KIND, int TPS, int GEN>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     constexpr int CIN8 = (KIND == 1) ? 1 : 4;
     constexpr int NCOL = (KIND == 2) ? 16 : 96;   // MMA N (accumulator columns per tile)
@@ -508,8 +511,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                 val[ut] = writer && i >= 1 && i <= 126 && r < P2 && xp >= 1 && xp <= M && yp >= 1 && yp <= M;
             }
             __nv_bfloat16* outU = (KIND != 2) ? a.out + a.out_off[U.inst] : nullptr;
-            __nv_bfloat16* zsU = (KIND != 2 && a.zsave) ? a.zsave + a.out_off[U.inst] : nullptr;
-            const __nv_bfloat16* zpU = (KIND != 2 && a.dgrad) ? a.zprev + a.out_off[U.inst] : nullptr;
+            __nv_bfloat16* zsU = (KIND != 2 && GEN && a.zsave) ? a.zsave + a.out_off[U.inst] : nullptr;
+            const __nv_bfloat16* zpU = (KIND != 2 && GEN && a.dgrad) ? a.zprev + a.out_off[U.inst] : nullptr;
             if constexpr (KIND == 2) {
                 // Window p holds D_p[i][3 dz + dx]; after the dx recombination
                 // across lanes, P[dz] is window p's contribution to output plane
@@ -718,7 +721,12 @@ int tc_ring_slots(int W) {
 template <int KIND, int TPS>
 static md_status launch_one(const TcArgs& a, int grid, cudaStream_t s) {
     const int smem = tc_smem_bytes(KIND, a.W, a.NS);
-    k_conv_tc<KIND, TPS><<<grid, TC_THREADS, smem, s>>>(a);
+    if constexpr (KIND != 2) {
+        if (a.zsave || a.dgrad) k_conv_tc<KIND, TPS, 1><<<grid, TC_THREADS, smem, s>>>(a);
+        else k_conv_tc<KIND, TPS, 0><<<grid, TC_THREADS, smem, s>>>(a);
+    } else {
+        k_conv_tc<KIND, TPS, 0><<<grid, TC_THREADS, smem, s>>>(a);
+    }
     MD_CHECK_LAUNCH();
     return MD_OK;
 }
@@ -736,11 +744,17 @@ md_status tc_prepare(int W, int tps) {
     const int ns = tc_ring_slots(W);
     if (ns == 0) { md_set_error("conv tile window too large for shared memory"); return MD_ERR_ARG; }
     const int need[3] = {tc_smem_bytes(0, W, ns), tc_smem_bytes(1, W, ns), tc_smem_bytes(2, W, ns)};
-    const void* fn[2][3] = {{(const void*)k_conv_tc<0, 1>, (const void*)k_conv_tc<1, 1>, (const void*)k_conv_tc<2, 1>},
-                            {(const void*)k_conv_tc<0, 2>, (const void*)k_conv_tc<1, 2>, (const void*)k_conv_tc<2, 2>}};
+    const void* fn[2][3][2] = {{{(const void*)k_conv_tc<0, 1, 0>, (const void*)k_conv_tc<0, 1, 1>},
+                                {(const void*)k_conv_tc<1, 1, 0>, (const void*)k_conv_tc<1, 1, 1>},
+                                {(const void*)k_conv_tc<2, 1, 0>, nullptr}},
+                               {{(const void*)k_conv_tc<0, 2, 0>, (const void*)k_conv_tc<0, 2, 1>},
+                                {(const void*)k_conv_tc<1, 2, 0>, (const void*)k_conv_tc<1, 2, 1>},
+                                {(const void*)k_conv_tc<2, 2, 0>, nullptr}}};
     for (int k = 0; k < 3; ++k) {
         if (need[k] <= set[tps][k]) continue;
-        MD_CUDA(cudaFuncSetAttribute(fn[tps - 1][k], cudaFuncAttributeMaxDynamicSharedMemorySize, need[k]));
+        for (int g = 0; g < 2; ++g)
+            if (fn[tps - 1][k][g])
+                MD_CUDA(cudaFuncSetAttribute(fn[tps - 1][k][g], cudaFuncAttributeMaxDynamicSharedMemorySize, need[k]));
         set[tps][k] = need[k];
     }
     return MD_OK;

@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(MD_TB) k_dots(const Seg* __restrict__ seg, con
     const float* V0 = V + o;
     // U elements per thread and loop trip, so U x (j + 1) independent loads are
     // in flight before the first FMA needs one
-    constexpr int U = JB <= 8 ? 4 : (JB <= 16 ? 2 : 1);
+    constexpr int U = JB <= 8 ? 4 : (JB <= 32 ? 2 : 1);
     float acc[JB + 1];
 #pragma unroll
     for (int i = 0; i <= JB; ++i) acc[i] = 0.f;
@@ -364,11 +364,12 @@ __global__ void __launch_bounds__(MD_TB) k_dots(const Seg* __restrict__ seg, con
 // adds them to column j of H and makes them the second pass's coefficients;
 // otherwise it ends the step (H[j+1][j], sig_{j+1}).  The second pass
 // (pass = 1, only where the condition fired) applies them and ends the step.
-template <int JB>
+template <int JB, int PASS>
 __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, const InstRange* __restrict__ rng,
                                                   const long long* __restrict__ off, const InstDesc* __restrict__ D,
-                                                  float* V, long long total, int j, int pass, KState* st, double* part) {
+                                                  float* V, long long total, int j, KState* st, double* part) {
     constexpr int NW = MD_TB / 32;
+    constexpr int pass = PASS;
     __shared__ double sh[(JB + 2) * NW];
     __shared__ float sc[JB];
     const Seg sg = seg[blockIdx.x];
@@ -381,7 +382,8 @@ __global__ void __launch_bounds__(MD_TB) k_update(const Seg* __restrict__ seg, c
     float* W = V + (long long)(j + 1) * total + o;
     const float* V0 = V + o;
     constexpr int U = JB <= 8 ? 4 : (JB <= 16 ? 2 : 1);
-    const bool dots2 = pass == 0;
+    // the second pass forms no dots (compiled without their registers)
+    constexpr bool dots2 = PASS == 0;
     float a = 0.f, a3 = 0.f;
     float acc[JB];
 #pragma unroll
@@ -483,13 +485,15 @@ template <int JB>
 static void launch_gs_step(md_batch* B, int j, cudaStream_t s) {
     const Tables& T = B->tabs;
     k_dots<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->V, B->total, j, 0, B->st, B->part);
-    for (int pass = 0; pass < 2; ++pass)
-        k_update<JB><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, B->total, j, pass,
-                                                     B->st, B->part);
+    k_update<JB, 0><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, B->total, j, B->st,
+                                                    B->part);
+    k_update<JB, 1><<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, T.vec.range, B->off, B->d, B->V, B->total, j, B->st,
+                                                    B->part);
 }
 static void launch_gs(md_batch* B, int j, cudaStream_t s) {
     if (j < 8) launch_gs_step<8>(B, j, s);
     else if (j < 16) launch_gs_step<16>(B, j, s);
+    else if (j < 24) launch_gs_step<24>(B, j, s);
     else if (j < 32) launch_gs_step<32>(B, j, s);
     else launch_gs_step<MD_KMAX>(B, j, s);
 }
@@ -1751,8 +1755,9 @@ static md_status build_graph(md_batch* B) {
 // ---- autotuning at batch creation --------------------------------------------
 // Batches of at least MD_TUNE_MIN_UNKNOWNS unknowns time their choices on the
 // GPU once, when they are created, and keep the fastest: the elements per
-// block of the Krylov vector kernels (a Gram-Schmidt step at basis length 6
-// over the whole batch, all instances active), and the tiles per plane step of
+// block of the Krylov vector kernels (Gram-Schmidt steps at basis lengths 6,
+// 14, 22 and 30, those below the restart length, over the whole batch, all
+// instances active), and the tiles per plane step of
 // the tensor-core convolutions (a network forward pass over every grid).
 #define MD_TUNE_MIN_UNKNOWNS 1000000
 
@@ -1766,8 +1771,9 @@ __global__ void k_tune_state(KState* st, int ninst) {
 }
 
 static md_status tune_vec_chunk(md_batch* B, const std::vector<const InstDesc*>& ptrs) {
-    const int cands[] = {2048, 4096, 8192, 16384};
-    const int j = 5;
+    const int cands[] = {4096, 8192, 16384, 32768};
+    // one step of each compiled basis bound (8, 16, 24, 32) below the restart length
+    const int js[4] = {std::min(5, B->k - 1), 13, 21, 29};
     cudaStream_t s = B->cap;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MD_CUDA(cudaEventCreate(&e0));
@@ -1784,11 +1790,14 @@ static md_status tune_vec_chunk(md_batch* B, const std::vector<const InstDesc*>&
         if (st != MD_OK) break;
         B->tabs = T;
         k_tune_state<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
-        launch_gs(B, j, s);
+        launch_gs(B, js[0], s);
         cudaEventRecord(e0, s);
         for (int r = 0; r < 3; ++r) {
-            k_tune_state<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
-            launch_gs(B, j, s);
+            for (int q = 0; q < 4; ++q) {
+                if (js[q] >= B->k) continue;
+                k_tune_state<<<(B->ninst + 31) / 32, 32, 0, s>>>(B->st, B->ninst);
+                launch_gs(B, js[q], s);
+            }
         }
         cudaEventRecord(e1, s);
         cudaError_t e = cudaEventSynchronize(e1);
@@ -1799,7 +1808,11 @@ static md_status tune_vec_chunk(md_batch* B, const std::vector<const InstDesc*>&
         B->tuning.vec_candidates[B->tuning.n_vec] = c;
         B->tuning.vec_us[B->tuning.n_vec] = us;
         B->tuning.n_vec += 1;
-        if (us < best) { best = us; best_t = T; best_c = c; }
+        // candidates in increasing size: a larger chunk is taken only when it is
+        // more than 5% faster, since the timing has every instance active while
+        // a solve runs later iterations on fewer, where smaller blocks balance
+        // the remaining work better
+        if (us < 0.95 * best) { best = us; best_t = T; best_c = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -70,7 +70,7 @@ def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees", kind
     'hf' ({b} and 4 random vectors, the paper's high-frequency set) or 'all'
     (residuals, b and q5..q8)."""
     insts = [mdgen.workload_instance(workload, first + i) for i in range(n_graphs)]
-    ops = [Operator(w["N"], w["graph"], w["beta"]) for w in insts]
+    ops = [Operator(w["N"], w["graph"], w["beta"], **w["physics"]) for w in insts]
     samples, sample_op = [], []
     by_N = {}
     for i, (w, op) in enumerate(zip(insts, ops)):
@@ -82,7 +82,10 @@ def build_set(n_graphs: int, first: int = 0, workload: str = "train_trees", kind
                 sample_op.append(i)
         if kind in ("kry", "base"):
             continue
-        mask = torch.from_numpy(np.concatenate([interior_mask(w["N"]), np.ones(op.n1, bool)])).cuda()
+        # random vectors on the unknowns: with natural conditions on the cube
+        # every grid node is one
+        m3 = interior_mask(w["N"]) if w["physics"].get("dirichlet", True) else np.ones(op.n3, bool)
+        mask = torch.from_numpy(np.concatenate([m3, np.ones(op.n1, bool)])).cuda()
         for k in range(4):
             v = torch.from_numpy(mdgen.normal_vector(w["f_seed"] or 0, first + i, op.n, stream=k).astype(np.float32)).cuda()
             samples.append(v * mask)
@@ -127,6 +130,39 @@ def mean_iterations(net, count: int, order: str = "upper"):
     return float(np.mean(its)), int(np.max(its)), bool(ok), int(fb)
 
 
+def evaluate(net, workload: str, count: int, order: str = "upper", tol: float | None = None,
+             restart: int | None = None, inner: int = 0, maxit: int = 20000) -> dict:
+    """FGMRES iterations to `tol` (the workload's own tolerance by default)
+    with `net` on the first `count` instances of `workload`, solved as one
+    batch from x0 = 0, and Jacobi-CG on the same batch for comparison; every
+    instance as [index, segments, iterations, final true residual]."""
+    w0 = mdgen.WORKLOADS[workload]
+    tol = float(w0.get("tol", 1e-8)) if tol is None else float(tol)
+    restart = int(w0.get("restart", 30)) if restart is None else int(restart)
+    insts = [mdgen.workload_instance(workload, i) for i in range(count)]
+    ops = [Operator(w["N"], w["graph"], w["beta"], **w["physics"]) for w in insts]
+    b = torch.cat([op.rhs(torch.from_numpy(f).cuda() if (f := mdgen.interior_source(w["N"], w["f_seed"])) is not None
+                          else None, w["g"]) for w, op in zip(insts, ops)])
+    out = {"workload": workload, "instances": count, "order": order, "inner": inner, "tol": tol, "restart": restart}
+    for solver in ("fgmres_cnn", "cg_jacobi"):
+        B = Batch(ops, solver, net if solver == "fgmres_cnn" else None, restart=restart)
+        if solver == "fgmres_cnn":
+            B.set_prec_order(order)
+            if inner:
+                B.set_inner_iters(inner)
+        x = torch.zeros_like(b)
+        its, rels, _ = B.solve(b, x, tol=tol, maxit=maxit)
+        fb = B.stats().get("fallback_instances", 0) if solver == "fgmres_cnn" else 0
+        B.close()
+        conv = [k for k in range(count) if rels[k] <= tol]
+        out[solver] = {"converged": len(conv), "mean_iterations_converged": float(np.mean([its[k] for k in conv])) if conv else None,
+                       "median_iterations": float(np.median(its)), "max_iterations": int(np.max(its)),
+                       "jacobi_fallback_instances": int(fb),
+                       "per_instance": [[k, len(insts[k]["graph"]["edges"]), int(its[k]), float(rels[k])]
+                                        for k in range(count)]}
+    return out
+
+
 def ablation(args):
     """One network per training set from the same initialisation, evaluated
     on the 32^3 tree workload (the analogue of the paper's Table 5)."""
@@ -159,7 +195,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=TRAINED)
     ap.add_argument("--init", default=None, help="start from this network file")
-    ap.add_argument("--workload", default="train_trees", choices=["train_trees", "train_trees_wide", "train_trees_mixed"])
+    ap.add_argument("--workload", default="train_trees",
+                    choices=["train_trees", "train_trees_wide", "train_trees_mixed", "train_paper_21"])
     ap.add_argument("--set", default="residuals", choices=["residuals", "base", "kry", "hf", "all"],
                     help="training vectors per graph (see build_set)")
     ap.add_argument("--ablation", action="store_true",
@@ -171,9 +208,21 @@ def main():
     ap.add_argument("--zero-1d", action="store_true",
                     help="train for the block lower-triangular order: the 1D part of every training vector is "
                          "zeroed, so the network sees [r0/s, 0, d] and is fitted to C z0 = r0")
+    ap.add_argument("--eval-workload", default=None,
+                    help="after training (or, with --eval-only, for the --init network) print the FGMRES and "
+                         "Jacobi-CG iterations on the first --eval-count instances of this workload")
+    ap.add_argument("--eval-only", action="store_true")
+    ap.add_argument("--eval-tol", type=float, default=None, help="tolerance (default: the workload's)")
+    ap.add_argument("--eval-inner", type=int, default=0, help="inner FGMRES steps of the 3D block solve")
+    ap.add_argument("--eval-order", default="upper", choices=["upper", "lower"])
     args = ap.parse_args()
     if args.ablation:
         return ablation(args)
+    if args.eval_only:
+        net = Network.load(args.init) if args.init else Network(random_params(args.seed))
+        print(json.dumps({"network": args.init, **evaluate(net, args.eval_workload or "tree15_32", args.eval_count,
+                                                            args.eval_order, args.eval_tol, inner=args.eval_inner)}))
+        return
     t0 = time.time()
     ops, samples, sample_op = build_set(args.graphs, workload=args.workload, kind=args.set)
     if args.zero_1d:
@@ -193,8 +242,13 @@ def main():
     t2 = time.time()
     os.makedirs(os.path.dirname(args.out), exist_ok=True)
     net.save(args.out)
-    print(json.dumps({"workload": args.workload, "set": args.set, "zero_1d": args.zero_1d, "graphs": args.graphs, "samples": len(samples), "epochs": args.epochs,
-                      "set_seconds": t1 - t0, "train_seconds": t2 - t1, "loss": hist}))
+    rec = {"workload": args.workload, "set": args.set, "zero_1d": args.zero_1d, "graphs": args.graphs,
+           "samples": len(samples), "epochs": args.epochs, "set_seconds": t1 - t0, "train_seconds": t2 - t1,
+           "loss": hist}
+    if args.eval_workload:
+        rec["evaluation"] = evaluate(net, args.eval_workload, args.eval_count, args.eval_order, args.eval_tol,
+                                     inner=args.eval_inner)
+    print(json.dumps(rec))
 
 
 if __name__ == "__main__":

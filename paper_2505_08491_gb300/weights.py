@@ -17,6 +17,10 @@ TRAINED = os.path.join(HERE, "weights", "cnn_trained.bin")
 # fine-tuned for the block lower-triangular order (1D parts of the training
 # vectors zeroed: the network fitted to C z0 = r0)
 TRAINED_LOWER = os.path.join(HERE, "weights", "cnn_trained_lower.bin")
+# fine-tuned for the paper's own setting (natural conditions on the cube,
+# k_Omega = sigma_Omega = 1e-3, eps = 1e-3, u_Lambda = 1 at the root: the
+# train_paper_21 graphs), upper block order
+TRAINED_PAPER = os.path.join(HERE, "weights", "cnn_paper21.bin")
 
 
 def layers_to_flat(layers) -> np.ndarray:
@@ -87,6 +91,14 @@ def read_network_file(path: str) -> np.ndarray:
     if int(np.frombuffer(raw[16 + 4 * n:24 + 4 * n], dtype=np.uint64)[0]) != h:
         raise ValueError(f"{path}: checksum mismatch")
     return vals
+
+
+def paper_network_params() -> np.ndarray:
+    """The network shipped for the paper's own setting (else the upper-order
+    network)."""
+    if os.path.exists(TRAINED_PAPER):
+        return read_network_file(TRAINED_PAPER)
+    return default_network_params("upper")
 
 
 def default_network_params(order: str = "upper") -> np.ndarray:
