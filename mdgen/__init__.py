@@ -155,6 +155,9 @@ WORKLOADS = {
     # [1, 100], R ~ U(0.01, 0.03); seeds disjoint from every evaluation workload
     "train_trees_mixed": dict(N=(32, 48, 64), beta="loguniform", kind="tree", depth=(2, 7), elems=8,
                               radius=(0.01, 0.03), f="normal", g=1.0, seed=6_000_000),
+    # the mixed batch's grid sizes at beta = 1 (fine-tuning without the heavy-coupling rows)
+    "train_trees_large": dict(N=(32, 48, 64), beta=1.0, kind="tree", depth=(2, 7), elems=8,
+                              radius=(0.01, 0.03), f="normal", g=1.0, seed=9_000_000),
     "transfer_64": dict(N=64, beta=(1.0, 10.0, 100.0), kind="tree", depth=(5, 7), elems=16,
                         radius=(0.005, 0.02), f="normal", g=1.0, tol=1e-8, restart=50, seed=2_000_000),
     "transfer_128": dict(N=128, beta=(1.0, 10.0, 100.0), kind="tree", depth=(5, 7), elems=16,

@@ -196,7 +196,8 @@ def main():
     ap.add_argument("--out", default=TRAINED)
     ap.add_argument("--init", default=None, help="start from this network file")
     ap.add_argument("--workload", default="train_trees",
-                    choices=["train_trees", "train_trees_wide", "train_trees_mixed", "train_paper_21"])
+                    choices=["train_trees", "train_trees_wide", "train_trees_mixed", "train_trees_large",
+                             "train_paper_21"])
     ap.add_argument("--set", default="residuals", choices=["residuals", "base", "kry", "hf", "all"],
                     help="training vectors per graph (see build_set)")
     ap.add_argument("--ablation", action="store_true",
