@@ -22,8 +22,8 @@
 //               (TMA, cp.async.bulk) of the TPS*128 + 2(Pd+1) + 8 contiguous
 //               rows the taps read, into a ring of NS shared-memory slots,
 //               completion counted on mbarriers (transaction bytes);
-//   warps 1, 18 one thread each issues tcgen05.mma (M=128, N=96 (16 for the
-//               last layer), K=16) for one of the two tiles of a step, fully
+//   warps 1, 18 one thread each issues tcgen05.mma (M=128, N=96 (32 for the
+//               first layer, 16 for the last), K=16) for one of the two tiles of a step, fully
 //               unrolled from per-unit row offsets, into a double-buffered TMEM
 //               accumulator; commits free the accumulator for the epilogue
 //               and the oldest window for the producer;
@@ -31,9 +31,12 @@
 //               BF16 pack, 16-byte stores of the grid rows of the plane
 //               (halo rows are computed but never stored, so the zero padding
 //               is preserved).
-// The first layer (3 input channels in one 8-channel chunk) pairs two taps
-// of one z-window per K=16 step (5 MMAs per window, the ninth tap with a
-// zero-weight partner); the last (1 output channel) puts the nine (dz, dx)
+// The first layer (3 input channels in one 8-channel chunk) pairs two dy
+// taps of one z-window per K=16 step (the third dy with a zero-weight
+// partner) and gives every dx tap its own N = 32 MMA with the A rows moved by
+// dx (18 MMAs per tile), so its epilogue, which bounds it, reads one
+// accumulator per output and exchanges nothing between lanes; the last
+// (1 output channel) puts the nine (dz, dx)
 // taps side by side in N = 16 columns, so each window alone feeds 6 MMAs (3 dy
 // x 2 K-halves) and the epilogue adds the dz contributions of consecutive
 // windows in registers.
@@ -173,6 +176,39 @@ __device__ inline uint4 pack8(const float* v) {
     return r;
 }
 
+// Epilogue store of one lane's CH pre-activations o (bias added) at element
+// offset at0 of its first 8-channel chunk (chunks P rows apart): the optional
+// pre-activation copy, then GELU(o), or, for an input gradient, o GELU'(zprev).
+template <int CH, int GEN>
+__device__ __forceinline__ void epi_store(const float* o, int at0, int P, __nv_bfloat16* outU, __nv_bfloat16* zsU,
+                                          const __nv_bfloat16* zpU) {
+#pragma unroll
+    for (int c8 = 0; c8 < CH / 8; ++c8) {
+        const int at = at0 + c8 * P * 8;
+        if (GEN && zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
+        float gl[8];
+        if (GEN && zpU) {
+            // input gradient: dZ_prev = dA * GELU'(Z_prev)
+            const uint4 zr = *reinterpret_cast<const uint4*>(zpU + at);
+            const __nv_bfloat162* zh = reinterpret_cast<const __nv_bfloat162*>(&zr);
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const float2 zf = __bfloat1622float2(zh[e / 2]);
+                gl[e] = o[c8 * 8 + e] * gelu_grad_fast(zf.x);
+                gl[e + 1] = o[c8 * 8 + e + 1] * gelu_grad_fast(zf.y);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                gl[e] = o[c8 * 8 + e];
+                gl[e + 1] = o[c8 * 8 + e + 1];
+                gelu_fast2(gl[e], gl[e + 1]);
+            }
+        }
+        *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
+    }
+}
+
 // The units of this CTA (TcSched): its share [S b / G, S (b + 1) / G) of
 // the launch's plane steps, walked in order and cut at column ends.  Every
 // role of the CTA walks the same sequence.
@@ -243,12 +279,16 @@ __device__ __forceinline__ bool walk_next(const TcSched& sc, const int* Ns, TcWa
 template <int KIND, int TPS, int GEN>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
     constexpr int CIN8 = (KIND == 1) ? 1 : 4;
-    constexpr int NCOL = (KIND == 2) ? 16 : 96;   // MMA N (accumulator columns per tile)
+    // MMA N (accumulator columns per tile): the hidden layers fold the three dx
+    // taps side by side (96), the last layer nine (dz, dx) taps (16); the first
+    // layer, whose MMAs are few, multiplies each dx tap separately (32) so that
+    // its epilogue needs no recombination across lanes
+    constexpr int NCOL = (KIND == 2) ? 16 : (KIND == 1 ? 32 : 96);
     constexpr int WIMG = tc_wimg_bytes(KIND);
     constexpr uint32_t IDESC = idesc_bf16(128, NCOL);
     // accumulator ring: two stages, eight for the last layer, whose steps are
     // short (6 MMAs per tile) and would otherwise wait on the hand-over latency
-    constexpr int NBUF = (KIND == 2) ? TC_NBUF_MAX : 2;
+    constexpr int NBUF = (KIND == 2) ? TC_NBUF_MAX : (KIND == 1 ? 4 : 2);
     constexpr int TMEM_COLS = (NBUF * TPS * NCOL <= 128) ? 128 : ((NBUF * TPS * NCOL <= 256) ? 256 : 512);
     static_assert(NBUF * TPS * NCOL <= 512, "accumulator ring exceeds tensor memory");
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -316,7 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     mbar_arrive_expect_tx(&full[slot], (uint32_t)(CIN8 * wl * 16));
                     unsigned char* dst = ring + (size_t)slot * slot_bytes;
                     for (int c = 0; c < CIN8; ++c) {
-                        const long long row = (long long)c * P + (long long)w * Pd * Pd + U.s0 - 1 - Pd;
+                        const long long row = (long long)c * P + (long long)w * Pd * Pd + U.s0 - 1 - Pd - (KIND == 1 ? 1 : 0);
                         bulk_g2s(dst + (size_t)c * W * 16, base + row * 8, (uint32_t)(wl * 16), &full[slot]);
                     }
                 }
@@ -331,10 +371,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         // pipe executes N = 96 MMAs); both wait on the same windows and
         // accumulators and both commit to the barriers, which count two arrivals
         const int mi = warp == 1 ? 0 : 1;
-        // tiles this thread issues: the first layer (6 MMAs per tile) is left to
-        // warp 1 alone, the second issuer only commits there
-        auto issues = [mi](int ut) { return KIND == 1 ? mi == 0 : ut % TC_MMA_WARPS == mi; };
-        auto prewaits = [mi](int ut) { return KIND == 1 ? (mi == 0 && ut == 0) : ut == mi; };
+        // tiles this thread issues: tile ut of every step goes to issuer ut mod 2
+        auto issues = [mi](int ut) { return ut % TC_MMA_WARPS == mi; };
+        auto prewaits = [mi](int ut) { return ut == mi; };
         if (lane == 0) {
             int it = 0;
             bool ok = true;
@@ -431,16 +470,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         if (KIND == 1) {
                             // one 8-channel chunk: per z-window the (dy=-1, dy=0) rows in
                             // one K=16 step (second core matrix one grid row further),
-                            // (dy=+1, zero-weight row + 1) in a second (one node further)
+                            // (dy=+1, zero-weight row + 1) in a second (one node further);
+                            // each dx tap its own MMA with the A rows moved by dx (the
+                            // window starts one row early, so dx = -1 is offset 0)
 #pragma unroll
                             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                                for (int pr = 0; pr < 2; ++pr) {
-                                    const uint64_t ad = (a_hi | (pr == 0 ? a_lbo_pd : (1ULL << 16))) +
-                                                        (uint64_t)(sbu[dz] + (uint32_t)(ut * 126) + (uint32_t)(2 * pr) * pdu);
-                                    const uint64_t bd = bd0 + (uint64_t)(((dz * 2 + pr) * 2 * NCOL * 16) >> 4);
-                                    mma_bf16(d, ad, bd, IDESC, (dz > 0 || pr > 0) ? 1u : 0u);
-                                }
+                                for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+                                    for (int dx = 0; dx < 3; ++dx) {
+                                        const uint64_t ad = (a_hi | (pr == 0 ? a_lbo_pd : (1ULL << 16))) +
+                                                            (uint64_t)(sbu[dz] + (uint32_t)(ut * 126 + dx) + (uint32_t)(2 * pr) * pdu);
+                                        const uint64_t bd = bd0 + (uint64_t)((((dz * 2 + pr) * 3 + dx) * 2 * NCOL * 16) >> 4);
+                                        mma_bf16(d, ad, bd, IDESC, (dz > 0 || pr > 0 || dx > 0) ? 1u : 0u);
+                                    }
                         } else {
                             const uint64_t a0 = a_hi | a_lbo_w;
 #pragma unroll
@@ -609,14 +652,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
 #pragma unroll
                 for (int ut = 0; ut < TPS; ++ut) {
                     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
-                    tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm[ut]);
-                    tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc[ut]);
-                    tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp[ut]);
+                    if constexpr (KIND == 1) {
+                        // every dx tap already summed in the lane's own row
+                        tmem_ld_nowait<CH>(tb + cg * CH, dc[ut]);
+                    } else {
+                        tmem_ld_nowait<CH>(tb + 0 * 32 + cg * CH, dm[ut]);
+                        tmem_ld_nowait<CH>(tb + 1 * 32 + cg * CH, dc[ut]);
+                        tmem_ld_nowait<CH>(tb + 2 * 32 + cg * CH, dp[ut]);
+                    }
                 }
                 tmem_wait_ld();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[bsel]);
+                if constexpr (KIND == 1) {
+#pragma unroll
+                    for (int ut = 0; ut < TPS; ++ut) {
+                        float o[CH];
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) o[c] = dc[ut][c] + bias[c];
+                        if (!val[ut]) continue;
+                        epi_store<CH, GEN>(o, ((cg * (CH / 8)) * P + z * P2 + rr[ut]) * 8, P, outU, zsU, zpU);
+                    }
+                    continue;
+                }
                 // warp-boundary values: lane 31's dx=-1 group, lane 0's dx=+1 group,
                 // exchanged among the 4 warps (lane quarters) of this channel
                 // group through a named barrier; buffer xcnt & 1 is rewritten
@@ -663,32 +722,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         o[c] = up + dc[ut][c] + dn + bias[c];
                     }
                     if (!val[ut]) continue;
-                    const int p = z * P2 + rr[ut];
-#pragma unroll
-                    for (int c8 = 0; c8 < CH / 8; ++c8) {
-                        const int at = ((cg * (CH / 8) + c8) * P + p) * 8;
-                        if (zsU) *reinterpret_cast<uint4*>(zsU + at) = pack8(o + c8 * 8);
-                        float gl[8];
-                        if (zpU) {
-                            // input gradient: dZ_prev = dA * GELU'(Z_prev)
-                            const uint4 zr = *reinterpret_cast<const uint4*>(zpU + at);
-                            const __nv_bfloat162* zh = reinterpret_cast<const __nv_bfloat162*>(&zr);
-#pragma unroll
-                            for (int e = 0; e < 8; e += 2) {
-                                const float2 zf = __bfloat1622float2(zh[e / 2]);
-                                gl[e] = o[c8 * 8 + e] * gelu_grad_fast(zf.x);
-                                gl[e + 1] = o[c8 * 8 + e + 1] * gelu_grad_fast(zf.y);
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 8; e += 2) {
-                                gl[e] = o[c8 * 8 + e];
-                                gl[e + 1] = o[c8 * 8 + e + 1];
-                                gelu_fast2(gl[e], gl[e + 1]);
-                            }
-                        }
-                        *reinterpret_cast<uint4*>(outU + at) = pack8(gl);
-                    }
+                    epi_store<CH, GEN>(o, ((cg * (CH / 8)) * P + z * P2 + rr[ut]) * 8, P, outU, zsU, zpU);
                 }
             }
             }  // KIND != 2
@@ -774,8 +808,8 @@ md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s
 // Weight images in the operand layout the MMAs read (n = dx index * 32 + o,
 // i.e. the three dx taps of one (dy, dz) side by side):
 //   kind 0: [combo = dz*3+dy (9)][k-chunk 4][n 96][8]
-//   kind 1: [dz 3][pair 2][k-chunk 2][n 96][8]; pair 0 = (dy -1, dy 0),
-//           pair 1 = (dy +1, zero)
+//   kind 1: [dz 3][pair 2][dx 3][k-chunk 2][n 32][8]; pair 0 = (dy -1, dy 0),
+//           pair 1 = (dy +1, zero); one dx tap per MMA
 //   kind 2: [dy 3][k-chunk 4][n 16][8]; n = 3 dz + dx for o = 0 (9 columns), rest zero
 void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img) {
     img.assign(tc_wimg_bytes(kind) / 2, __float2bfloat16_rn(0.0f));
@@ -786,15 +820,16 @@ void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__
     if (kind == 1) {
         for (int dz = 0; dz < 3; ++dz)
             for (int pr = 0; pr < 2; ++pr)
-                for (int half = 0; half < 2; ++half) {
-                    const int dy = 2 * pr + half;  // 3 = zero partner
-                    for (int n = 0; n < 96; ++n)
-                        for (int l = 0; l < 8; ++l) {
-                            const int g = n / 32, o = n % 32;
-                            const float v = dy < 3 ? w_at(o, l, dz * 9 + dy * 3 + g) : 0.0f;
-                            img[((size_t)((dz * 2 + pr) * 2 + half) * 96 + n) * 8 + l] = __float2bfloat16_rn(v);
-                        }
-                }
+                for (int dx = 0; dx < 3; ++dx)
+                    for (int half = 0; half < 2; ++half) {
+                        const int dy = 2 * pr + half;  // 3 = zero partner
+                        for (int o = 0; o < 32; ++o)
+                            for (int l = 0; l < 8; ++l) {
+                                const float v = dy < 3 ? w_at(o, l, dz * 9 + dy * 3 + dx) : 0.0f;
+                                img[((size_t)(((dz * 2 + pr) * 3 + dx) * 2 + half) * 32 + o) * 8 + l] =
+                                    __float2bfloat16_rn(v);
+                            }
+                    }
     } else if (kind == 0) {
         for (int combo = 0; combo < 9; ++combo)
             for (int kc = 0; kc < 4; ++kc)
