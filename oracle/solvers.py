@@ -11,6 +11,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import cnn as _cnn
+from . import unet as _unet
 
 
 def direct_solve(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
@@ -154,7 +155,11 @@ class BlockPreconditioner:
         'cnn'    -- the network: s = ||b0||, X = [r0/s, l/s, d], z0 = (s/alpha) N(X)
                     on interior nodes (alpha as in the training loss of Section 5.1,
                     evaluated for this instance), z0 = r0 on Dirichlet nodes;
-        'jacobi' -- z0 = b0 / diag(C).
+        'jacobi' -- z0 = b0 / diag(C);
+        'unet'   -- the paper's U-net U3 (oracle/unet.py, FP64) on its two
+                    input channels: s = ||b0||, X = [b0/s, d], z0 = (s/alpha) U(X)
+                    on unknown nodes, z0 = r0 on Dirichlet nodes (params: its
+                    flat parameter vector).
 
     order='lower' inverts the block lower-triangular part instead (the other
     reading of how the 1D unknowns follow from the network): the 3D block
@@ -241,6 +246,8 @@ class BlockPreconditioner:
             return self.C_lu.solve(b0)
         if self.mode == "jacobi":
             return b0 / p.C.diagonal()
+        if self.mode == "unet":
+            return unet_solve(p, r0, l, self.params)
         return network_solve(p, r0, l, self.params, self.bf16)
 
     def __call__(self, r):
@@ -274,6 +281,50 @@ def network_solve(prob, r0, l, params, bf16=True):
     z0 = (s / prob.alpha) * Y
     z0[prob.bd] = r0[prob.bd]
     return z0
+
+
+def unet_input(prob, r0, l):
+    """The U-net's input X = [b0/s, d] (2, N+1, N+1, N+1), b0 = r0 + l, s = ||b0||."""
+    n = prob.N + 1
+    b0 = r0 + l
+    s = float(np.linalg.norm(b0))
+    if s == 0.0:
+        return None, 0.0
+    return np.stack([b0 / s, prob.dist]).reshape(2, n, n, n), s
+
+
+def unet_solve(prob, r0, l, theta):
+    """z0 = (s/alpha) U([b0/s, d]) on unknown nodes, r0 on Dirichlet nodes."""
+    X, s = unet_input(prob, r0, l)
+    if X is None:
+        return r0.copy()
+    z0 = (s / prob.alpha) * _unet.forward(X, theta).reshape(-1)
+    z0[prob.bd] = r0[prob.bd]
+    return z0
+
+
+def training_loss_unet(prob, r0, l, theta, grad=False):
+    """training_loss with the U-net as the 3D solve: L = ||C_II Y_I / alpha -
+    b0_I / s||^2, Y = U([b0/s, d]); grad=True also returns the flat
+    parameter gradient (oracle/unet.py backward)."""
+    p = prob
+    X, s = unet_input(p, r0, l)
+    Y, cache = _unet.forward(X, theta, keep=True)
+    y = Y.reshape(-1).copy()
+    y[p.bd] = 0.0
+    b_hat = (r0 + l) / s
+    b_hat[p.bd] = 0.0
+    Cy = p.C @ y
+    Cy[p.bd] = 0.0
+    res = Cy / p.alpha - b_hat
+    L = float(res @ res)
+    if not grad:
+        return L
+    dy = (2.0 / p.alpha) * (p.C.T @ res)
+    dy[p.bd] = 0.0
+    n = p.N + 1
+    _, g = _unet.backward(dy.reshape(1, n, n, n), cache)
+    return L, g
 
 
 def training_loss(prob, r0, l, params, bf16=False, grad=False):

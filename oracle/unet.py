@@ -25,7 +25,7 @@ up2: transposed convolution with 2x2x2 kernels and stride 2, out[o, 2p + t] =
 bias[o] + sum_c W[c, o, t] X[c, p] (t in {0, 1}^3), then zero planes appended
 up to the skip's size (2 m <= size <= 2 m + 1); GELU(x) = x Phi(x).
 
-Parameters, flat (the library's layout): for each of the six conv3 layers in
+Parameters, flat (the library's layout): for each of the seven conv3 layers in
 the order above, then the two up2 layers (up2 of b, then of d1), the weights
 then the biases; conv3 weights (c_out, c_in, 3, 3, 3) with kernel index =
 offset + 1 in (z, y, x), up2 weights (c_in, c_out, 2, 2, 2) with index t.

@@ -10,7 +10,6 @@ import torch.nn.functional as F
 
 from oracle import unet
 
-torch.set_default_dtype(torch.float64)
 
 
 def t(a):
@@ -116,3 +115,33 @@ def test_forward_matches_torch_composition_at_21():
     Y = unet.forward(X, theta)
     ref = torch_unet(t(X)[None], theta)[0].numpy()
     assert np.max(np.abs(Y - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_unet_training_loss_is_the_coupled_residual_and_its_gradient_is_consistent():
+    """The U-net's training loss (Section 3.2 eq. (risk)) against the coupled
+    system itself, as for the CNN: with the block upper-triangular
+    preconditioner z = Q(r) whose 3D solve is the U-net, the 3D rows of
+    A z - r are C z0 - b0, so the loss is ||(A Q(r) - r)_0||^2 / ||b0||^2 over
+    the unknown rows.  Its parameter gradient against central differences
+    along a random direction."""
+    import mdgen
+    from oracle import fem, solvers
+    p = fem.Problem(8, mdgen.random_tree(77, 0, depth=3, elems=4), beta=10.0)
+    rng = np.random.default_rng(3)
+    theta = unet.random_params(11)
+    r = rng.standard_normal(p.n)
+    r[:p.n3][p.bd] = 0.0
+    Q = solvers.BlockPreconditioner(p, mode="unet", params=theta, order="upper")
+    z = Q(r)
+    e = (p.A @ z - r)[:p.n3][~p.bd]
+    z1 = z[p.n3:]
+    b0 = r[:p.n3] - p.beta * (p.M01 @ z1)
+    want = float(e @ e) / float(b0 @ b0)
+    l = Q.lift(z1)
+    L, g = solvers.training_loss_unet(p, r[:p.n3], l, theta, grad=True)
+    assert L == np.float64(L) and abs(L - want) <= 1e-10 * want
+    d = rng.standard_normal(theta.size)
+    h = 1e-6
+    fd = (solvers.training_loss_unet(p, r[:p.n3], l, theta + h * d) -
+          solvers.training_loss_unet(p, r[:p.n3], l, theta - h * d)) / (2 * h)
+    assert abs(fd - g @ d) <= 1e-5 * abs(fd)
