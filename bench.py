@@ -364,6 +364,54 @@ def network_only(args):
                                        "output_mean_abs": float(Y.abs().mean())}}), flush=True)
 
 
+# the paper's batched U-net forward on its V100 (2 x 21^3 inputs; its Table 11)
+PAPER_UNET_FORWARD_MS = {1: 1.5, 100: 25.5}
+
+
+def unet_flops(n: int) -> float:
+    """Multiply-adds x 2 of one U3 forward on an n^3 grid (the md_unet layers)."""
+    m1, m2 = n // 2, n // 2 // 2
+    v0, v1, v2 = n ** 3, m1 ** 3, m2 ** 3
+    conv = 27 * (2 * 32 * v0 + 32 * 64 * v1 + 64 * 128 * v2 + 128 * 128 * v2 + 128 * 64 * v1 + 64 * 32 * v0 + 32 * v0)
+    up = 128 * 64 * (2 * m2) ** 3 + 64 * 32 * (2 * m1) ** 3
+    return 2.0 * (conv + up)
+
+
+def unet_forward(args):
+    """The U-net U3 forward alone, batched (random weights, N(0,1) inputs of
+    2 x n^3), timed with CUDA events after warm-up: batches of 1 and 100 at
+    the paper's 21^3 (its Table 11 measures the same on a V100).  Prints one
+    JSON line."""
+    import torch
+
+    from paper_2505_08491_gb300 import UNet
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    from paper_2505_08491_gb300.weights import unet_random_params
+    rng = np.random.default_rng(0)
+    n = args.net_n if args.net_n != 33 else 21
+    net = UNet(unet_random_params(0))
+    out = {"nodes_per_edge": n, "flop_per_sample": unet_flops(n), "batches": {}}
+    for batch in (1, 100):
+        X = torch.from_numpy(rng.standard_normal((batch, 2, n, n, n)).astype(np.float32)).cuda()
+        for _ in range(3):
+            net.forward(X)
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            Y = net.forward(X)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out["batches"][str(batch)] = {"ms_per_forward": ms, "ms_per_sample": ms / batch,
+                                      "tflops": batch * unet_flops(n) / ms / 1e9,
+                                      "paper_v100_ms": PAPER_UNET_FORWARD_MS.get(batch) if n == 21 else None,
+                                      "output_mean_abs": float(Y.abs().mean())}
+    net.close()
+    print(json.dumps({"unet_forward": out}), flush=True)
+
+
 def extra_workload(name: str, steps: int, flush):
     """Solves/s of another workload on this GPU, measured like the headline
     (inputs resident, L2 flushed, CUDA events around each batched solve), with
@@ -441,9 +489,13 @@ def main():
     ap.add_argument("--net-batch", type=int, default=16, help="--network-only: grids per pass")
     ap.add_argument("--net-n", type=int, default=33, help="--network-only: grid nodes per edge")
     ap.add_argument("--passes", type=int, default=4, help="--network-only: forward passes")
+    ap.add_argument("--unet-forward", action="store_true",
+                    help="time the U-net U3 forward alone, batches of 1 and 100 at 21^3 (or --net-n)")
     args = ap.parse_args()
     if args.network_only:
         return network_only(args)
+    if args.unet_forward:
+        return unet_forward(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.count is None:

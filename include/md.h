@@ -191,6 +191,55 @@ md_status md_cnn_forward(const md_cnn* c, int n_nodes_edge, int batch, const flo
 md_status md_cnn_backward(const md_cnn* c, int n_nodes_edge, int batch, const float* X,
                           const float* dY, float* dparams, float* dX, md_stream s);
 
+/* ---- The paper's U-net U3 (Section 4.2, the U3 table of Section 5.1) ----
+ * Encoder conv3 2->32 | maxpool2 + conv3 32->64 | maxpool2 + conv3 64->128,
+ * bottleneck conv3 128->128, decoder [up2 128->64 | skip] + conv3 128->64,
+ * [up2 64->32 | skip] + conv3 64->32, output conv3 32->1; GELU x Phi(x)
+ * after every conv3 but the last.  conv3: 3x3x3 zero 'same' padding with
+ * bias; maxpool2: 2x2x2 windows at even offsets (an odd size's last plane
+ * dropped); up2: transposed 2x2x2 convolution with stride 2, zero planes
+ * appended up to the skip's size.  FP32 throughout, CUDA cores.
+ * Parameter layout (host float array, md_unet_num_params() entries): the
+ * seven conv3 layers in the order above, then the two up2 layers; each its
+ * weights (conv3: c_out, c_in, 3, 3, 3 in the cross-correlation orientation
+ * of md_cnn; up2: c_in, c_out, 2, 2, 2) then its biases. */
+typedef struct md_unet md_unet;
+long long md_unet_num_params(void);
+md_status md_unet_create(const float* host_params, long long n_params, md_unet** out);
+void md_unet_destroy(md_unet* u);
+/* md_unet_forward -- Y = U3(X) on `batch` grids of n^3 nodes (4 <= n <= 1024):
+ * X: device float, batch * 2 * n^3, (sample, channel, z, y, x); Y: device
+ * float, batch * n^3.  The first call for a larger (n, batch) allocates the
+ * workspace (synchronising the stream); calls on one handle must not
+ * overlap.  Asynchronous otherwise.  MD_ERR_ARG on a bad size. */
+md_status md_unet_forward(md_unet* u, int n, int batch, const float* X, float* Y, md_stream s);
+/* md_unet_backward -- gradients of sum(dY * Y) for the pass above, summed over
+ * the batch: dparams (device float, md_unet_num_params(), overwritten) and
+ * optionally dX (device float, like X, nullable).  Recomputes the forward
+ * activations (workspace as md_unet_forward, larger).  Weight gradients are
+ * accumulated with atomic additions: their summation order, and so their
+ * last bits, vary from call to call. */
+md_status md_unet_backward(md_unet* u, int n, int batch, const float* X, const float* dY, float* dparams,
+                           float* dX, md_stream s);
+/* Parameters: set from host (on_device = 0) or device memory, asynchronous on
+ * s; get to host (synchronous). */
+md_status md_unet_set_params(md_unet* u, const float* params, int on_device, md_stream s);
+md_status md_unet_get_params(const md_unet* u, float* host_params, long long n_params);
+/* md_unet_train_loss -- md_train_loss with the U-net as the network: per
+ * sample the input X = [b0 / s, d_h] (the U-net's two channels: the 3D block's
+ * right-hand side b0 = r0 + l of eq. (twosteps) scaled by s = ||b0||, and the
+ * distance field), z0 = (s / alpha) U(X), loss ||C z0 - b0||^2 / ||b0||^2
+ * over the unknown 3D rows, averaged over the samples; dparams (device float,
+ * md_unet_num_params(), nullable) its gradient.  Samples share a grid size;
+ * with 1D parts zero (the block lower-triangular order) b0 = r0. */
+md_status md_unet_train_loss(md_unet* u, int count, const md_op* const* ops, const float* const* r,
+                             double* loss, float* dparams, md_stream s);
+/* md_unet_opt_step -- one AdamW step on the U-net's parameters (decoupled
+ * weight decay on the weights, not the biases); the first step allocates the
+ * moment buffers. */
+md_status md_unet_opt_step(md_unet* u, const float* grad, double lr, double beta1, double beta2, double eps,
+                           double weight_decay, md_stream s);
+
 /* md_precondition -- z = Q~ r, eq. (twosteps) with the network as the 3D
  * solve (eq. (decoupled_3d_problem)):
  *   z1 = B11^{-1} r1;  l = beta Pi^T W Psi z1;  b0 = r0 + l;  s = ||b0||;
@@ -349,6 +398,14 @@ md_status md_batch_set_smoothing(md_batch* b, int nu, double omega);
  * length are allocated at the first call); 0 (default): one network
  * application.  Not combined with smoothing (MD_ERR_ARG). */
 md_status md_batch_set_inner_iters(md_batch* b, int m);
+/* md_batch_set_unet -- the 3D block solve of a network-preconditioned FGMRES
+ * batch by the U-net u instead of the batch's md_cnn (u NULL: back to it):
+ * z0 = (s / alpha) U([b0 / s, d_h]) on the unknown nodes, v0 on Dirichlet
+ * nodes, in either block order (b0 = r0 + l upper, r0 lower).  The instances
+ * must share the grid size; not combined with smoothing or inner steps
+ * (MD_ERR_ARG).  The batch borrows u.  The first call runs one U-net pass to
+ * size its workspace (synchronising the device): call it before any capture. */
+md_status md_batch_set_unet(md_batch* b, md_unet* u);
 md_status md_batch_stats(const md_batch* b, md_batch_stats_t* out);
 
 /* Autotuning.  A network- or Jacobi-preconditioned FGMRES batch of at least

@@ -75,6 +75,16 @@ SIGNATURES = {
     "md_cnn_save": (st, [vp, C.c_char_p]),
     "md_cnn_load": (st, [C.c_char_p, C.POINTER(vp)]),
     "md_cnn_forward": (st, [vp, i32, i32, vp, vp, vp]),
+    "md_unet_num_params": (i64, []),
+    "md_unet_create": (st, [C.POINTER(C.c_float), i64, C.POINTER(vp)]),
+    "md_unet_destroy": (None, [vp]),
+    "md_unet_forward": (st, [vp, i32, i32, vp, vp, vp]),
+    "md_unet_backward": (st, [vp, i32, i32, vp, vp, vp, vp, vp]),
+    "md_unet_set_params": (st, [vp, vp, i32, vp]),
+    "md_unet_get_params": (st, [vp, C.POINTER(C.c_float), i64]),
+    "md_unet_train_loss": (st, [vp, i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(f64), vp, vp]),
+    "md_unet_opt_step": (st, [vp, vp, f64, f64, f64, f64, f64, vp]),
+    "md_batch_set_unet": (st, [vp, vp]),
     "md_cnn_backward": (st, [vp, i32, i32, vp, vp, vp, vp, vp]),
     "md_precondition": (st, [vp, vp, vp, vp, vp]),
     "md_lift": (st, [vp, vp, vp, vp, vp]),

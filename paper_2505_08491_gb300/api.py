@@ -251,6 +251,81 @@ class Network:
         return dp, dX
 
 
+class UNet:
+    """The paper's U-net U3 (md_unet_*): 2 input channels, 1 output."""
+
+    def __init__(self, params: np.ndarray):
+        lib = L.load()
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        h = C.c_void_p()
+        L.check(lib.md_unet_create(p.ctypes.data_as(C.POINTER(C.c_float)), p.size, C.byref(h)), "md_unet_create")
+        self._h = h
+
+    @staticmethod
+    def num_params() -> int:
+        return int(L.load().md_unet_num_params())
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        """X: (batch, 2, n, n, n) float32 CUDA -> (batch, 1, n, n, n)."""
+        if X.dim() != 5 or X.shape[1] != 2 or not (X.shape[2] == X.shape[3] == X.shape[4]):
+            raise ValueError("X must be (batch, 2, n, n, n)")
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], 1) + tuple(X.shape[2:]), dtype=torch.float32, device="cuda")
+        L.check(L.load().md_unet_forward(self._h, X.shape[2], X.shape[0], _ptr(X, torch.float32), _ptr(Y), _stream()),
+                "md_unet_forward")
+        return Y
+
+    def backward(self, X: torch.Tensor, dY: torch.Tensor, need_dx: bool = False):
+        """Gradients of sum(dY * U(X)): (dparams (num_params,), dX or None)."""
+        X = X.contiguous()
+        dY = dY.contiguous()
+        dp = torch.empty(self.num_params(), dtype=torch.float32, device="cuda")
+        dX = torch.empty_like(X) if need_dx else None
+        L.check(L.load().md_unet_backward(self._h, X.shape[2], X.shape[0], _ptr(X, torch.float32),
+                                          _ptr(dY, torch.float32), _ptr(dp), _ptr(dX) if dX is not None else None,
+                                          _stream()), "md_unet_backward")
+        return dp, dX
+
+    def train_loss(self, ops: list, residuals: list, with_grad: bool = True):
+        """Mean training loss ||C z0 - b0||^2 / ||b0||^2 with the U-net as the
+        3D block solve (md_unet_train_loss) and its parameter gradient."""
+        loss = C.c_double()
+        grad = torch.empty(self.num_params(), dtype=torch.float32, device="cuda") if with_grad else None
+        rs = (C.c_void_p * len(residuals))(*[r.data_ptr() for r in residuals])
+        L.check(L.load().md_unet_train_loss(self._h, len(ops), _op_array(ops), rs, C.byref(loss),
+                                            _ptr(grad) if with_grad else None, _stream()), "md_unet_train_loss")
+        return loss.value, grad
+
+    def opt_step(self, grad: torch.Tensor, lr: float, betas=(0.9, 0.999), eps: float = 1e-8,
+                 weight_decay: float = 1e-4):
+        """One AdamW step on the parameters (md_unet_opt_step)."""
+        L.check(L.load().md_unet_opt_step(self._h, _ptr(grad, torch.float32), float(lr), float(betas[0]),
+                                          float(betas[1]), float(eps), float(weight_decay), _stream()),
+                "md_unet_opt_step")
+
+    def set_params(self, params: torch.Tensor):
+        """Parameters from a float32 CUDA tensor (num_params,)."""
+        L.check(L.load().md_unet_set_params(self._h, _ptr(params.contiguous(), torch.float32), 1, _stream()),
+                "md_unet_set_params")
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        L.check(L.load().md_unet_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size),
+                "md_unet_get_params")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            L.load().md_unet_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class NetworkFunction(torch.autograd.Function):
     """Y = N(X) with the library's forward and backward kernels, for use
     inside torch autograd graphs.  The parameters are those held by `net`;
@@ -389,6 +464,11 @@ class Batch:
 
     def set_profiling(self, enable: bool):
         L.check(L.load().md_batch_set_profiling(self._h, 1 if enable else 0), "md_batch_set_profiling")
+
+    def set_unet(self, unet: "UNet | None"):
+        """The U-net as the 3D block solve (None: the batch's network)."""
+        L.check(L.load().md_batch_set_unet(self._h, unet._h if unet is not None else None), "md_batch_set_unet")
+        self.unet = unet  # the batch borrows it
 
     def set_host_loop(self, enable: bool):
         """Host-driven restart cycles (for kernel profilers); default: one graph launch per solve."""

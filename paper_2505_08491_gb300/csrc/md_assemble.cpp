@@ -14,6 +14,7 @@
 //   - circle point in cell clamp(floor(x N), 0, N-1), trilinear weights,
 //     boundary-node weights dropped.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -35,6 +36,43 @@ inline Vec3 cross(Vec3 a, Vec3 b) {
 struct Entry { int col; double val; };
 
 }  // namespace
+
+// Operator arrays staged on the host and uploaded with one device allocation,
+// one copy and one clear (each array 256-byte aligned) instead of an
+// allocation and a copy per array.  commit() writes the device pointers to
+// their slots.
+struct UploadArena {
+    std::vector<unsigned char> stage;  // arrays with host data, then the zero-filled ones
+    size_t zero_bytes = 0;
+    std::vector<std::function<void(unsigned char*)>> bind;
+    static size_t align(size_t b) { return (b + 255) & ~(size_t)255; }
+    template <class T>
+    void up(const T** slot, const std::vector<T>& v) {
+        const size_t off = align(stage.size()), bytes = v.size() * sizeof(T);
+        stage.resize(off + (bytes ? bytes : 1));
+        if (bytes) memcpy(stage.data() + off, v.data(), bytes);
+        bind.push_back([slot, off](unsigned char* b) { *slot = reinterpret_cast<const T*>(b + off); });
+    }
+    void up32(const float** slot, const std::vector<double>& v) {
+        const std::vector<float> f(v.begin(), v.end());
+        up(slot, f);
+    }
+    template <class T>
+    void zeros(T** slot, size_t count) {  // placed after every staged array
+        const size_t off = align(zero_bytes);
+        zero_bytes = off + (count ? count : 1) * sizeof(T);
+        bind.push_back([this, slot, off](unsigned char* b) { *slot = reinterpret_cast<T*>(b + align(stage.size()) + off); });
+    }
+    md_status commit(std::vector<void*>* allocs) {
+        const size_t zoff = align(stage.size());
+        unsigned char* base = nullptr;
+        MD_TRY(dev_upload(allocs, &base, (const unsigned char*)nullptr, zoff + zero_bytes));
+        MD_CUDA(cudaMemcpy(base, stage.data(), stage.size(), cudaMemcpyHostToDevice));
+        MD_CUDA(cudaMemset(base + zoff, 0, zero_bytes));
+        for (auto& f : bind) f(base);
+        return MD_OK;
+    }
+};
 
 extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double beta,
                                  const md_params* prm, md_op** out) {
@@ -214,13 +252,9 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         }
     }
 
-    // ---- Pi^T W over touched nodes: entries (q, Pi[q,n] w_q), sorted by node then q
-    struct TE { int node, q; double v; };
-    std::vector<TE> te;
-    te.reserve(pi_col.size());
-    for (int q = 0; q < nq; ++q)
-        for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) te.push_back({pi_col[j], q, pi_val[j] * wq[q]});
-    // rows grouped by the apply's stencil tile, by node within a tile
+    // ---- Pi^T W over touched nodes: entries (q, Pi[q,n] w_q) by node, q ascending
+    // within a node; nodes grouped by the apply's stencil tile, in node order
+    // within a tile
     int ty = 1, tz = 1;
     apply_tile_shape(N, &ty, &tz);
     const int nyt = (N + 1 + ty - 1) / ty, nzt = (N + 1 + tz - 1) / tz;
@@ -228,11 +262,44 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
         const int M = N + 1, z = node / (M * M), y = (node / M) % M;
         return (z / tz) * nyt + y / ty;
     };
-    std::sort(te.begin(), te.end(), [&](const TE& p, const TE& r) {
-        const int tp = tile_of(p.node), tr = tile_of(r.node);
-        if (tp != tr) return tp < tr;
-        return p.node != r.node ? p.node < r.node : p.q < r.q;
-    });
+    struct TE { int node, q; double v; };
+    std::vector<TE> te(pi_col.size());
+    if (n3 <= (1 << 22)) {
+        // counting transpose of the q-major rows of Pi (entries arrive in q
+        // order, so each node's stay in q order), then the touched nodes
+        // visited tile by tile: tiles are (z, y) blocks, and node order within
+        // a tile is (z, y, x) order
+        std::vector<int> start((size_t)n3 + 1, 0);
+        for (int c : pi_col) start[(size_t)c + 1] += 1;
+        for (int i = 0; i < n3; ++i) start[(size_t)i + 1] += start[i];
+        std::vector<TE> byn(pi_col.size());
+        {
+            std::vector<int> fill(start.begin(), start.end() - 1);
+            for (int q = 0; q < nq; ++q)
+                for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) byn[fill[pi_col[j]]++] = {pi_col[j], q, pi_val[j] * wq[q]};
+        }
+        size_t k = 0;
+        for (int zb = 0; zb < nzt; ++zb)
+            for (int yb = 0; yb < nyt; ++yb)
+                for (int z = zb * tz; z < std::min(M, (zb + 1) * tz); ++z)
+                    for (int y = yb * ty; y < std::min(M, (yb + 1) * ty); ++y)
+                        for (int x = 0; x < M; ++x) {
+                            const int node = x + M * (y + M * z);
+                            for (int e = start[node]; e < start[node + 1]; ++e) te[k++] = byn[e];
+                        }
+    } else {
+        // very large grids: the same order by a sort on precomputed keys
+        struct TK { int tile, node, q; double v; };
+        std::vector<TK> tk;
+        tk.reserve(pi_col.size());
+        for (int q = 0; q < nq; ++q)
+            for (int j = pi_ptr[q]; j < pi_ptr[q + 1]; ++j) tk.push_back({tile_of(pi_col[j]), pi_col[j], q, pi_val[j] * wq[q]});
+        std::sort(tk.begin(), tk.end(), [](const TK& p, const TK& r) {
+            if (p.tile != r.tile) return p.tile < r.tile;
+            return p.node != r.node ? p.node < r.node : p.q < r.q;
+        });
+        for (size_t i = 0; i < tk.size(); ++i) te[i] = {tk[i].node, tk[i].q, tk[i].v};
+    }
     // row sums of Pi (less than 1 where boundary weights were dropped)
     std::vector<double> pi_rowsum(nq, 0.0);
     for (int q = 0; q < nq; ++q)
@@ -440,32 +507,23 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
     }
 
     auto fail = [&](md_status s) { dev_free_all(&op->allocs); delete op; return s; };
-    std::vector<float> f32;
-    auto up64 = [&](const double** dst, const std::vector<double>& v) {
-        double* p; md_status s = dev_upload(&op->allocs, &p, v.data(), v.size()); *dst = p; return s; };
-    auto up32 = [&](const float** dst, const std::vector<double>& v) {
-        f32.assign(v.begin(), v.end());
-        float* p; md_status s = dev_upload(&op->allocs, &p, f32.data(), f32.size()); *dst = p; return s; };
-    auto upi = [&](const int** dst, const std::vector<int>& v) {
-        int* p; md_status s = dev_upload(&op->allocs, &p, v.data(), v.size()); *dst = p; return s; };
 #define UP(x) do { md_status s_ = (x); if (s_ != MD_OK) return fail(s_); } while (0)
-    UP(upi(&D.pi_ptr, pi_ptr)); UP(upi(&D.pi_col, pi_col)); UP(up64(&D.pi_v64, pi_val)); UP(up32(&D.pi_v32, pi_val));
-    UP(upi(&D.qa, qa)); UP(upi(&D.qb, qb));
-    UP(up64(&D.psa64, psa)); UP(up64(&D.psb64, psb)); UP(up32(&D.psa32, psa)); UP(up32(&D.psb32, psb));
-    UP(upi(&D.tn_node, tn_node)); UP(upi(&D.tn_ptr, tn_ptr)); UP(upi(&D.tn_q, tn_q)); UP(upi(&D.tile_tptr, tile_tptr));
-    UP(up64(&D.tn_v64, tn_v)); UP(up32(&D.tn_v32, tn_v));
-    UP(upi(&D.k1_ptr, k1_ptr)); UP(upi(&D.k1_col, k1_col)); UP(up64(&D.k1_v64, k1_v)); UP(up32(&D.k1_v32, k1_v));
-    UP(upi(&D.pw_ptr, pw_ptr)); UP(upi(&D.pw_q, pw_q)); UP(up64(&D.pw_v64, pw_v)); UP(up32(&D.pw_v32, pw_v));
-    UP(up64(&D.load1, load1));
-    if (any_d) { UP(up64(&D.rhs0, rhs0)); UP(up64(&D.rhs1, rhs1)); }
+    UploadArena ar;
+    ar.up(&D.pi_ptr, pi_ptr); ar.up(&D.pi_col, pi_col); ar.up(&D.pi_v64, pi_val); ar.up32(&D.pi_v32, pi_val);
+    ar.up(&D.qa, qa); ar.up(&D.qb, qb);
+    ar.up(&D.psa64, psa); ar.up(&D.psb64, psb); ar.up32(&D.psa32, psa); ar.up32(&D.psb32, psb);
+    ar.up(&D.tn_node, tn_node); ar.up(&D.tn_ptr, tn_ptr); ar.up(&D.tn_q, tn_q); ar.up(&D.tile_tptr, tile_tptr);
+    ar.up(&D.tn_v64, tn_v); ar.up32(&D.tn_v32, tn_v);
+    ar.up(&D.k1_ptr, k1_ptr); ar.up(&D.k1_col, k1_col); ar.up(&D.k1_v64, k1_v); ar.up32(&D.k1_v32, k1_v);
+    ar.up(&D.pw_ptr, pw_ptr); ar.up(&D.pw_q, pw_q); ar.up(&D.pw_v64, pw_v); ar.up32(&D.pw_v32, pw_v);
+    ar.up(&D.load1, load1);
+    if (any_d) { ar.up(&D.rhs0, rhs0); ar.up(&D.rhs1, rhs1); }
     {
-        std::vector<double> lo(n1), dio(n1);
-        for (int i = 0; i < n1; ++i) { lo[i] = tl[i]; dio[i] = tdinv[i]; }
-        UP(upi(&D.tr_order, tr_order)); UP(upi(&D.tr_parent, tr_parent));
         D.nlvu = nlvu; D.nlvd = nlvd;
-        UP(upi(&D.lvu_ptr, lvu_ptr)); UP(upi(&D.lv_up, lv_up)); UP(upi(&D.ch_ptr, ch_ptr)); UP(upi(&D.ch_idx, ch_idx));
-        UP(upi(&D.lvd_ptr, lvd_ptr)); UP(upi(&D.lv_dn, lv_dn));
-        UP(up64(&D.tr_l64, lo)); UP(up64(&D.tr_dinv64, dio)); UP(up32(&D.tr_l32, lo)); UP(up32(&D.tr_dinv32, dio));
+        ar.up(&D.tr_order, tr_order); ar.up(&D.tr_parent, tr_parent);
+        ar.up(&D.lvu_ptr, lvu_ptr); ar.up(&D.lv_up, lv_up); ar.up(&D.ch_ptr, ch_ptr); ar.up(&D.ch_idx, ch_idx);
+        ar.up(&D.lvd_ptr, lvd_ptr); ar.up(&D.lv_dn, lv_dn);
+        ar.up(&D.tr_l64, tl); ar.up(&D.tr_dinv64, tdinv); ar.up32(&D.tr_l32, tl); ar.up32(&D.tr_dinv32, tdinv);
     }
     {
         std::vector<double> segs((size_t)E * 6);
@@ -473,16 +531,17 @@ extern "C" md_status md_assemble(int N, const md_graph* g, double radius, double
             int a = g->edges[2 * e], b = g->edges[2 * e + 1];
             for (int c = 0; c < 3; ++c) { segs[6 * e + c] = g->xyz[3 * a + c]; segs[6 * e + 3 + c] = g->xyz[3 * b + c]; }
         }
-        UP(up64(&D.segs, segs));
+        ar.up(&D.segs, segs);
     }
-    {
-        float* p; UP(dev_alloc(&op->allocs, &p, (size_t)n3, false)); D.dist = p;
-        double* dp; UP(dev_alloc(&op->allocs, &dp, (size_t)D.n, false)); D.dinv64 = dp;
-        UP(dev_alloc(&op->allocs, &p, (size_t)D.n, false)); D.dinv32 = p;
-        UP(dev_alloc(&op->allocs, &p, (size_t)n3, false)); D.sminv32 = p;
-        UP(dev_alloc(&op->allocs, &D.t64, (size_t)nq)); UP(dev_alloc(&op->allocs, &D.t32, (size_t)nq));
-        UP(dev_alloc(&op->allocs, &D.lift32, (size_t)n3)); UP(dev_alloc(&op->allocs, &D.ltouch32, (size_t)ntouch));
-    }
+    ar.zeros(&D.dist, (size_t)n3);
+    ar.zeros(&D.dinv64, (size_t)D.n);
+    ar.zeros(&D.dinv32, (size_t)D.n);
+    ar.zeros(&D.sminv32, (size_t)n3);
+    ar.zeros(&D.t64, (size_t)nq);
+    ar.zeros(&D.t32, (size_t)nq);
+    ar.zeros(&D.lift32, (size_t)n3);
+    ar.zeros(&D.ltouch32, (size_t)ntouch);
+    UP(ar.commit(&op->allocs));
     UP(dev_upload(&op->allocs, &op->d, &D, 1));
     {
         std::vector<const InstDesc*> one{&op->h};

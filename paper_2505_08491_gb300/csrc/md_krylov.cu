@@ -92,6 +92,12 @@ struct md_batch {
     int graph_smooth_nu = 0;
     float graph_smooth_omega = 1.f;
     unsigned long long graph_cnn_uid = 0;  // network the graph was captured with (0: none)
+    // the U-net as the 3D block solve (md_batch_set_unet; uniform grid size un):
+    // its input (ninst x 2 x un^3) and output (ninst x un^3)
+    md_unet* unet = nullptr;
+    const md_unet* graph_unet = nullptr;
+    float *ux = nullptr, *uy = nullptr;
+    int un = 0;
     bool graph_prof = false;
     int graph_engine = -1;
     long long graph_kernels = 0;
@@ -1441,6 +1447,42 @@ static md_status launch_precond_inner(md_batch* B, const md_cnn* cnn, const floa
     return MD_OK;
 }
 
+// The U-net's input [b0 / s, d] per instance (b0 = v0 + l in the upper
+// order, v0 in the lower), as the network input pack does for the CNN.
+__global__ void k_unet_in(const Seg* __restrict__ seg, const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                          const float* __restrict__ v, const KState* __restrict__ st, int use_lift, float* __restrict__ X) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const InstDesc& d = D[sg.inst];
+    const long long n3 = d.n3;
+    const double s = st[sg.inst].s;
+    const float inv_s = s > 0.0 ? (float)(1.0 / s) : 0.f;
+    const float* vi = v + off[sg.inst];
+    float* x = X + (long long)sg.inst * 2 * n3;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        x[e] = (vi[e] + (use_lift ? d.lift32[e] : 0.f)) * inv_s;
+        x[n3 + e] = d.dist[e];
+    }
+}
+
+// z0 = (s / alpha) y on the unknown grid nodes, v0 on Dirichlet nodes
+__global__ void k_unet_out(const Seg* __restrict__ seg, const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                           const float* __restrict__ v, const KState* __restrict__ st, const float* __restrict__ Y,
+                           float* __restrict__ z) {
+    const Seg sg = seg[blockIdx.x];
+    if (!cnn_runs(st, sg.inst)) return;
+    const InstDesc& d = D[sg.inst];
+    const float scale = (float)(st[sg.inst].s / d.alpha);
+    const float* y = Y + (long long)sg.inst * d.n3;
+    const long long o = off[sg.inst];
+    const int M = d.N + 1;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        const int i = e % M, j = (e / M) % M, k = e / (M * M);
+        const bool bd = !d.natural && (i == 0 || i == d.N || j == 0 || j == d.N || k == 0 || k == d.N);
+        z[o + e] = bd ? v[o + e] : scale * y[e];
+    }
+}
+
 static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin, float* zout, float* tmp,
                                 cudaStream_t s, unsigned long long* e_conv0 = nullptr,
                                 unsigned long long* e_conv1 = nullptr) {
@@ -1464,9 +1506,20 @@ static md_status launch_precond(md_batch* B, const md_cnn* cnn, const float* vin
         MD_TRY(launch_upper_1d(T, B->d, B->off, B->ninst, B->max_n1, vin, zout, B->st, B->part, s));
     }
     MD_CHECK_LAUNCH();
-    MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, zout, s, !lower));
-    OutIO io{zout, B->off, vin, B->off, B->st, B->d};
-    MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
+    if (B->unet) {
+        // the U-net over every instance of the batch (one grid size)
+        k_unet_in<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->d, B->off, vin, B->st, lower ? 0 : 1, B->ux);
+        MD_CHECK_LAUNCH();
+        stamp(e_conv0, s);
+        MD_TRY(md_unet_forward(B->unet, B->un, B->ninst, B->ux, B->uy, (md_stream)s));
+        stamp(e_conv1, s);
+        k_unet_out<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, B->d, B->off, vin, B->st, B->uy, zout);
+        MD_CHECK_LAUNCH();
+    } else {
+        MD_TRY(cnn_pack_prec(B->cw, B->d, vin, B->off, B->st, zout, s, !lower));
+        OutIO io{zout, B->off, vin, B->off, B->st, B->d};
+        MD_TRY(cnn_forward_layers(cnn, B->cw, io, CONV_PREC, s, e_conv0, e_conv1));
+    }
     if (lower) {
         MD_TRY(launch_lower_1d(B, vin, zout, s));
     }
@@ -1712,7 +1765,7 @@ static md_status build_graph(md_batch* B) {
     const int engine = B->cnn ? B->cnn->engine : 0;
     const unsigned long long uid = B->cnn ? B->cnn->uid : 0;
     const bool have = B->host_loop ? B->cycle_graph != nullptr : B->solve_graph != nullptr;
-    if (have && B->graph_cnn_uid == uid && B->graph_prof == B->profiling && B->graph_engine == engine &&
+    if (have && B->graph_cnn_uid == uid && B->graph_unet == B->unet && B->graph_prof == B->profiling && B->graph_engine == engine &&
         B->graph_prec_order == B->prec_order && B->graph_smooth_nu == B->smooth_nu &&
         B->graph_smooth_omega == B->smooth_omega && B->graph_inner_m == B->inner_m)
         return MD_OK;
@@ -1720,6 +1773,7 @@ static md_status build_graph(md_batch* B) {
     if (B->host_loop) {
         MD_TRY(build_host_loop(B));
         B->graph_cnn_uid = uid;
+        B->graph_unet = B->unet;
         B->graph_prec_order = B->prec_order;
         B->graph_smooth_nu = B->smooth_nu;
         B->graph_smooth_omega = B->smooth_omega;
@@ -1743,6 +1797,7 @@ static md_status build_graph(md_batch* B) {
     cudaGraphDestroy(g);
     MD_CUDA(e);
     B->graph_cnn_uid = uid;
+    B->graph_unet = B->unet;
     B->graph_prec_order = B->prec_order;
     B->graph_smooth_nu = B->smooth_nu;
     B->graph_smooth_omega = B->smooth_omega;
@@ -2042,6 +2097,30 @@ extern "C" md_status md_batch_set_prec_order(md_batch* B, int lower) {
     return MD_OK;
 }
 
+extern "C" md_status md_batch_set_unet(md_batch* B, md_unet* u) {
+    if (!B) { md_set_error("md_batch_set_unet: NULL batch"); return MD_ERR_ARG; }
+    if (!u) { B->unet = nullptr; return MD_OK; }
+    if (B->solver != MD_SOLVER_FGMRES_CNN) { md_set_error("md_batch_set_unet: a network-preconditioned FGMRES batch only"); return MD_ERR_ARG; }
+    if (B->inner_m > 0 || B->smooth_nu > 0) {
+        md_set_error("md_batch_set_unet: not combined with inner steps or smoothing"); return MD_ERR_ARG;
+    }
+    const int N = B->hdesc[0].N;
+    for (const InstDesc& d : B->hdesc)
+        if (d.N != N) { md_set_error("md_batch_set_unet: the instances must share the grid size"); return MD_ERR_ARG; }
+    if (N + 1 < 4) { md_set_error("md_batch_set_unet: grids of at least 4^3 nodes"); return MD_ERR_ARG; }
+    const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
+    if (!B->ux) {
+        MD_TRY(dev_alloc(&B->allocs, &B->ux, (size_t)(2 * n3 * B->ninst)));
+        MD_TRY(dev_alloc(&B->allocs, &B->uy, (size_t)(n3 * B->ninst)));
+    }
+    B->un = N + 1;
+    // a first pass outside any capture sizes the U-net's workspace for this batch
+    MD_TRY(md_unet_forward(u, B->un, B->ninst, B->ux, B->uy, nullptr));
+    MD_CUDA(cudaDeviceSynchronize());
+    B->unet = u;
+    return MD_OK;
+}
+
 extern "C" md_status md_batch_set_profiling(md_batch* B, int enable) {
     if (!B) { md_set_error("md_batch_set_profiling: NULL batch"); return MD_ERR_ARG; }
     B->profiling = enable != 0;
@@ -2208,6 +2287,7 @@ extern "C" md_status md_batch_set_smoothing(md_batch* B, int nu, double omega) {
         md_set_error("md_batch_set_smoothing: not combined with inner FGMRES steps");
         return MD_ERR_ARG;
     }
+    if (nu > 0 && B->unet) { md_set_error("md_batch_set_smoothing: not combined with the U-net"); return MD_ERR_ARG; }
     B->smooth_nu = nu;
     B->smooth_omega = (float)omega;
     return MD_OK;
@@ -2287,6 +2367,7 @@ extern "C" md_status md_batch_set_inner_iters(md_batch* B, int m) {
         md_set_error("md_batch_set_inner_iters: not combined with smoothing");
         return MD_ERR_ARG;
     }
+    if (m > 0 && B->unet) { md_set_error("md_batch_set_inner_iters: not combined with the U-net"); return MD_ERR_ARG; }
     if (m > 0) MD_TRY(ensure_inner(B));
     B->inner_m = m;
     return MD_OK;

@@ -620,6 +620,115 @@ extern "C" md_status md_train_loss(const md_cnn* c, int count, const md_op* cons
     return st;
 }
 
+// ---- the U-net's training loss (the same risk, Section 3.2 eq. (risk)) ----
+// Input X = [b0 / s, d] (the U-net's two channels: the 3D block's right-hand
+// side b0 = r0 + l scaled by s = ||b0||, and the distance field), output y;
+// z0 = (s / alpha) y; loss ||C y / alpha - b0 / s||^2 over the unknown rows.
+
+__global__ void k_unet_pack(const Seg* __restrict__ seg, const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                            const float* __restrict__ r, const KState* __restrict__ st, float* __restrict__ X) {
+    const Seg sg = seg[blockIdx.x];
+    const InstDesc& d = D[sg.inst];
+    const long long n3 = d.n3, o = off[sg.inst];
+    const double s = st[sg.inst].s;
+    const float inv_s = s > 0 ? (float)(1.0 / s) : 0.f;
+    float* x = X + (long long)sg.inst * 2 * n3;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) {
+        x[e] = (r[o + e] + d.lift32[e]) * inv_s;
+        x[n3 + e] = d.dist[e];
+    }
+}
+
+// the network output into the instance vector's 3D part (1D part zero)
+__global__ void k_unet_scatter(const Seg* __restrict__ seg, const InstDesc* __restrict__ D,
+                               const long long* __restrict__ off, const float* __restrict__ Y, float* __restrict__ v) {
+    const Seg sg = seg[blockIdx.x];
+    const InstDesc& d = D[sg.inst];
+    const float* y = Y + (long long)sg.inst * d.n3;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x) v[off[sg.inst] + e] = e < d.n3 ? y[e] : 0.f;
+}
+
+// dY = scale (C res) / alpha on the unknown grid nodes, 0 elsewhere
+__global__ void k_unet_dy(const Seg* __restrict__ seg, const InstDesc* __restrict__ D, const long long* __restrict__ off,
+                          const float* __restrict__ cres, float scale, float* __restrict__ dY) {
+    const Seg sg = seg[blockIdx.x];
+    const InstDesc& d = D[sg.inst];
+    float* g = dY + (long long)sg.inst * d.n3;
+    for (int e = sg.begin + threadIdx.x; e < sg.end; e += blockDim.x)
+        g[e] = (d.natural || !is_bd(e, d.N)) ? scale * cres[off[sg.inst] + e] / (float)d.alpha : 0.f;
+}
+
+extern "C" md_status md_unet_train_loss(md_unet* u, int count, const md_op* const* ops, const float* const* r,
+                                        double* loss, float* dparams, md_stream stream) {
+    if (!u || !loss) { md_set_error("md_unet_train_loss: NULL argument"); return MD_ERR_ARG; }
+    MD_TRY(check_samples(count, ops, r));
+    const int N = ops[0]->h.N;
+    int max_n1 = 0, max_nq = 0, max_t = 0;
+    for (int i = 0; i < count; ++i) {
+        if (ops[i]->h.N != N) { md_set_error("md_unet_train_loss: samples of one call share the grid size"); return MD_ERR_ARG; }
+        max_n1 = std::max(max_n1, ops[i]->h.n1);
+        max_nq = std::max(max_nq, ops[i]->h.nq);
+        max_t = std::max(max_t, ops[i]->h.ntouch);
+    }
+    if (N + 1 < 4) { md_set_error("md_unet_train_loss: grids of at least 4^3 nodes"); return MD_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    TrainWork* t = nullptr;
+    MD_TRY(train_work_create(count, N, max_n1, max_nq, max_t, &t));
+    const int B = count;
+    const long long n3 = (long long)(N + 1) * (N + 1) * (N + 1);
+    std::vector<InstDesc> desc(B);
+    std::vector<const InstDesc*> ptrs(B);
+    for (int i = 0; i < B; ++i) {
+        desc[i] = ops[i]->h;
+        desc[i].t32 = t->scratch[3 * i];
+        desc[i].lift32 = t->scratch[3 * i + 1];
+        desc[i].ltouch32 = t->scratch[3 * i + 2];
+        ptrs[i] = &desc[i];
+    }
+    std::vector<void*> tmp;
+    float *X = nullptr, *Y = nullptr, *dY = nullptr;
+    Tables T;
+    md_status st = build_tables(ptrs, &T, &tmp);
+    if (st == MD_OK) st = dev_alloc(&tmp, &X, (size_t)(2 * n3 * B), false);
+    if (st == MD_OK) st = dev_alloc(&tmp, &Y, (size_t)(n3 * B), false);
+    if (st == MD_OK) st = dev_alloc(&tmp, &dY, (size_t)(n3 * B), false);
+    auto run = [&]() -> md_status {
+        MD_CUDA(cudaMemcpyAsync(t->d, desc.data(), sizeof(InstDesc) * B, cudaMemcpyHostToDevice, s));
+        for (int i = 0; i < B; ++i) {
+            MD_CUDA(cudaMemsetAsync(desc[i].lift32, 0, sizeof(float) * desc[i].n3, s));
+            MD_CUDA(cudaMemcpyAsync(t->rv + i * t->stride, r[i], sizeof(float) * desc[i].n, cudaMemcpyDeviceToDevice, s));
+        }
+        MD_CUDA(cudaMemsetAsync(t->loss, 0, sizeof(double) * B, s));
+        k_mask_grid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, t->d, t->voff, t->rv, 0);
+        k_set_active<<<(B + 31) / 32, 32, 0, s>>>(t->st, B);
+        MD_CHECK_LAUNCH();
+        // ||r0||, the 1D solve and its lift l, s = ||r0 + l||
+        MD_TRY(launch_prec_input(T, t->d, t->voff, t->rv, t->yv, t->st, B, t->max_n1, t->part3, s));
+        k_unet_pack<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, t->d, t->voff, t->rv, t->st, X);
+        MD_CHECK_LAUNCH();
+        MD_TRY(md_unet_forward(u, N + 1, B, X, Y, (md_stream)s));
+        k_unet_scatter<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, t->d, t->voff, Y, t->yv);
+        k_mask_grid<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, t->d, t->voff, t->yv, 1);
+        MD_CHECK_LAUNCH();
+        MD_TRY(launch_apply(T, t->d, B, MD_FP32, t->yv, t->voff, t->cy, s));
+        k_train_res<<<T.vec.nblocks, MD_TB, 0, s>>>(T.vec.seg, t->d, t->voff, t->cy, t->rv, t->st, t->res, t->loss);
+        MD_CHECK_LAUNCH();
+        MD_TRY(launch_apply(T, t->d, B, MD_FP32, t->res, t->voff, t->cres, s));
+        k_unet_dy<<<T.n3.nblocks, MD_TB, 0, s>>>(T.n3.seg, t->d, t->voff, t->cres, 2.0f / B, dY);
+        MD_CHECK_LAUNCH();
+        if (dparams) MD_TRY(md_unet_backward(u, N + 1, B, X, dY, dparams, nullptr, (md_stream)s));
+        std::vector<double> l(B);
+        MD_CUDA(cudaMemcpyAsync(l.data(), t->loss, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+        MD_CUDA(cudaStreamSynchronize(s));
+        *loss = std::accumulate(l.begin(), l.end(), 0.0) / B;
+        return MD_OK;
+    };
+    if (st == MD_OK) st = run();
+    dev_free_all(&tmp);
+    train_work_destroy(t);
+    return st;
+}
+
 extern "C" md_status md_train(md_cnn* c, const md_train_cfg* cfg) {
     if (!c || !cfg) { md_set_error("md_train: NULL argument"); return MD_ERR_ARG; }
     if (cfg->n_ops < 1 || !cfg->ops || cfg->n_samples < 1 || !cfg->sample_op || !cfg->sample_r || cfg->epochs < 1 ||

@@ -131,7 +131,7 @@ def mean_iterations(net, count: int, order: str = "upper"):
 
 
 def evaluate(net, workload: str, count: int, order: str = "upper", tol: float | None = None,
-             restart: int | None = None, inner: int = 0, maxit: int = 20000) -> dict:
+             restart: int | None = None, inner: int = 0, maxit: int = 20000, unet=None) -> dict:
     """FGMRES iterations to `tol` (the workload's own tolerance by default)
     with `net` on the first `count` instances of `workload`, solved as one
     batch from x0 = 0, and Jacobi-CG on the same batch for comparison; every
@@ -143,13 +143,16 @@ def evaluate(net, workload: str, count: int, order: str = "upper", tol: float | 
     ops = [Operator(w["N"], w["graph"], w["beta"], **w["physics"]) for w in insts]
     b = torch.cat([op.rhs(torch.from_numpy(f).cuda() if (f := mdgen.interior_source(w["N"], w["f_seed"])) is not None
                           else None, w["g"]) for w, op in zip(insts, ops)])
-    out = {"workload": workload, "instances": count, "order": order, "inner": inner, "tol": tol, "restart": restart}
+    out = {"workload": workload, "instances": count, "order": order, "inner": inner, "tol": tol, "restart": restart,
+           "network": "unet" if unet is not None else "cnn"}
     for solver in ("fgmres_cnn", "cg_jacobi"):
         B = Batch(ops, solver, net if solver == "fgmres_cnn" else None, restart=restart)
         if solver == "fgmres_cnn":
             B.set_prec_order(order)
             if inner:
                 B.set_inner_iters(inner)
+            if unet is not None:
+                B.set_unet(unet)
         x = torch.zeros_like(b)
         its, rels, _ = B.solve(b, x, tol=tol, maxit=maxit)
         fb = B.stats().get("fallback_instances", 0) if solver == "fgmres_cnn" else 0
@@ -161,6 +164,37 @@ def evaluate(net, workload: str, count: int, order: str = "upper", tol: float | 
                        "per_instance": [[k, len(insts[k]["graph"]["edges"]), int(its[k]), float(rels[k])]
                                         for k in range(count)]}
     return out
+
+
+def train_unet(net, ops, sample_op, samples, *, epochs: int, batch: int, lr: float, lr_min: float, seed: int = 0):
+    """The U-net's unsupervised training: AdamW (md_unet_opt_step) on the
+    mean loss of minibatches of samples that share a grid size
+    (md_unet_train_loss), cosine decay of the learning rate from lr to
+    lr_min.  Returns the mean loss per epoch."""
+    by_n = {}
+    for i, k in enumerate(sample_op):
+        by_n.setdefault(ops[k].N, []).append(i)
+    rng = np.random.default_rng(seed)
+    steps = sum(len(v) // batch for v in by_n.values())
+    if steps == 0:
+        raise ValueError("fewer samples than one minibatch")
+    total, k, hist = steps * epochs, 0, []
+    for _ in range(epochs):
+        batches = []
+        for idx in by_n.values():
+            perm = rng.permutation(idx)
+            batches += [perm[j * batch:(j + 1) * batch] for j in range(len(perm) // batch)]
+        order = rng.permutation(len(batches))
+        acc = 0.0
+        for bi in order:
+            mb = batches[bi]
+            loss, grad = net.train_loss([ops[sample_op[i]] for i in mb], [samples[i] for i in mb])
+            frac = k / (total - 1) if total > 1 else 1.0
+            net.opt_step(grad, lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * frac)))
+            acc += loss
+            k += 1
+        hist.append(acc / len(batches))
+    return hist
 
 
 def ablation(args):
@@ -216,7 +250,12 @@ def main():
     ap.add_argument("--eval-tol", type=float, default=None, help="tolerance (default: the workload's)")
     ap.add_argument("--eval-inner", type=int, default=0, help="inner FGMRES steps of the 3D block solve")
     ap.add_argument("--eval-order", default="upper", choices=["upper", "lower"])
+    ap.add_argument("--arch", default="cnn", choices=["cnn", "unet"],
+                    help="the network: the six-layer CNN (md_cnn) or the paper's U-net U3 (md_unet; its parameters "
+                         "saved as a float32 .npy, --init loads one)")
     args = ap.parse_args()
+    if args.arch == "unet":
+        return main_unet(args)
     if args.ablation:
         return ablation(args)
     if args.eval_only:
@@ -249,6 +288,38 @@ def main():
     if args.eval_workload:
         rec["evaluation"] = evaluate(net, args.eval_workload, args.eval_count, args.eval_order, args.eval_tol,
                                      inner=args.eval_inner)
+    print(json.dumps(rec))
+
+
+def main_unet(args):
+    """--arch unet: train (or, with --eval-only, evaluate) the U-net."""
+    from paper_2505_08491_gb300 import Network, UNet
+    from paper_2505_08491_gb300.weights import default_network_params, unet_random_params
+    params = np.load(args.init).astype(np.float32) if args.init else unet_random_params(args.seed)
+    net = UNet(params)
+    rec = {"arch": "unet", "init": args.init}
+    if not args.eval_only:
+        t0 = time.time()
+        ops, samples, sample_op = build_set(args.graphs, workload=args.workload, kind=args.set)
+        if args.zero_1d:
+            for i, r in enumerate(samples):
+                samples[i] = r.clone()
+                samples[i][ops[sample_op[i]].n3:] = 0.0
+        torch.cuda.synchronize()
+        t1 = time.time()
+        hist = train_unet(net, ops, sample_op, samples, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                          lr_min=args.lr_min, seed=args.seed)
+        t2 = time.time()
+        out = args.out if args.out.endswith(".npy") else os.path.splitext(args.out)[0] + ".npy"
+        os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
+        np.save(out, net.params())
+        rec.update({"workload": args.workload, "set": args.set, "zero_1d": args.zero_1d, "graphs": args.graphs,
+                    "samples": len(samples), "epochs": args.epochs, "set_seconds": t1 - t0,
+                    "train_seconds": t2 - t1, "loss": hist, "out": out})
+    if args.eval_workload:
+        cnn = Network(default_network_params(args.eval_order))
+        rec["evaluation"] = evaluate(cnn, args.eval_workload, args.eval_count, args.eval_order, args.eval_tol,
+                                     unet=net)
     print(json.dumps(rec))
 
 

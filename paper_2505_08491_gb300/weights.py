@@ -109,3 +109,20 @@ def default_network_params(order: str = "upper") -> np.ndarray:
     if os.path.exists(path):
         return read_network_file(path)
     return identity_pair_params()
+
+
+# ---- the U-net U3 (md_unet_*): conv3 layers (c_in, c_out), then the up2 layers
+UNET_CONVS = ((2, 32), (32, 64), (64, 128), (128, 128), (128, 64), (64, 32), (32, 1))
+UNET_UPS = ((128, 64), (64, 32))
+
+
+def unet_random_params(seed: int = 0) -> np.ndarray:
+    """He-normal U-net weights (std sqrt(2 / fan_in); fan_in 27 c_in for a conv3,
+    c_in for an up2), biases N(0, 0.01^2); the md_unet parameter layout."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in UNET_CONVS:
+        parts += [rng.normal(0.0, np.sqrt(2.0 / (27 * ci)), co * ci * 27), rng.normal(0.0, 0.01, co)]
+    for ci, co in UNET_UPS:
+        parts += [rng.normal(0.0, np.sqrt(2.0 / ci), ci * co * 8), rng.normal(0.0, 0.01, co)]
+    return np.concatenate(parts).astype(np.float32)
