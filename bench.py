@@ -412,15 +412,17 @@ def unet_forward(args):
     print(json.dumps({"unet_forward": out}), flush=True)
 
 
-def extra_workload(name: str, steps: int, flush):
+def extra_workload(name: str, steps: int, flush, unet_params=None):
     """Solves/s of another workload on this GPU, measured like the headline
     (inputs resident, L2 flushed, CUDA events around each batched solve), with
-    Jacobi-CG on the same batch beside it.  Rank 0 of a one-GPU run only."""
+    Jacobi-CG on the same batch beside it.  unet_params: the U-net (one
+    application per iteration) as the 3D block solve instead of the CNN.
+    Rank 0 of a one-GPU run only."""
     import torch
 
-    from paper_2505_08491_gb300 import Batch, Network, Operator
+    from paper_2505_08491_gb300 import Batch, Network, Operator, UNet
     order = DEFAULT_ORDER[name]
-    inner = DEFAULT_INNER.get(name, 0)
+    inner = DEFAULT_INNER.get(name, 0) if unet_params is None else 0
     tol = tol_of(name)
     insts = instances(name, 0, DEFAULT_COUNT[name])
     ops = [make_operator(w) for w in insts]
@@ -430,7 +432,10 @@ def extra_workload(name: str, steps: int, flush):
     x_all = torch.zeros_like(b_all)
     stream = torch.cuda.current_stream()
     out = {"workload": f"{name}: {len(insts)} {WORKLOAD_TEXT[name]}", "prec_order": order, "tol": tol,
-           "inner_fgmres_steps": inner}
+           "inner_fgmres_steps": inner, "network": "unet" if unet_params is not None else "cnn"}
+    un = None
+    # a U-net that leaves an instance stalled would otherwise run 1e5 iterations per step
+    maxit = 100000 if unet_params is None else 20000
     for solver in ("fgmres_cnn", "cg_jacobi"):
         if solver == "fgmres_cnn":
             net = Network(network_params(name, order))
@@ -438,18 +443,21 @@ def extra_workload(name: str, steps: int, flush):
             B.set_prec_order(order)
             if inner:
                 B.set_inner_iters(inner)
+            if unet_params is not None:
+                un = UNet(unet_params)
+                B.set_unet(un)
         else:
             B = Batch(ops, solver)
         for _ in range(3):
             x_all.zero_()
-            B.solve(b_all, x_all, tol=tol, maxit=100000)
+            B.solve(b_all, x_all, tol=tol, maxit=maxit)
         ms = 0.0
         for _ in range(steps):
             flush.zero_()
             x_all.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            its, rels, ok = B.solve(b_all, x_all, tol=tol, maxit=100000)
+            its, rels, ok = B.solve(b_all, x_all, tol=tol, maxit=maxit)
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
@@ -457,6 +465,9 @@ def extra_workload(name: str, steps: int, flush):
                        "max_iterations": int(np.max(its)), "max_relres": float(max(rels)),
                        "converged": int(sum(1 for r in rels if r <= tol)), "instances": len(insts)}
         B.close()
+        if un is not None:
+            un.close()
+            un = None
     out["speedup_fgmres_cnn_over_cg"] = out["fgmres_cnn"]["solves_per_s"] / out["cg_jacobi"]["solves_per_s"]
     return out
 
@@ -634,6 +645,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_extra:
         other = {name: extra_workload(name, max(1, min(args.steps, 5)), flush)
                  for name in ("tree15_32", "paper_21") if name != args.workload}
+        from paper_2505_08491_gb300.weights import paper_unet_params
+        up = paper_unet_params()
+        if up is not None:
+            other["paper_21_unet"] = extra_workload("paper_21", max(1, min(args.steps, 5)), flush, unet_params=up)
 
     pk = peaks()
     launches = stats["conv_hidden_launches"]

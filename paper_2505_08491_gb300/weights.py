@@ -111,6 +111,15 @@ def default_network_params(order: str = "upper") -> np.ndarray:
     return identity_pair_params()
 
 
+# the U-net trained for the paper's own setting (train_paper_21), float32 .npy
+TRAINED_UNET_PAPER = os.path.join(HERE, "weights", "unet_paper21.npy")
+
+
+def paper_unet_params():
+    """The shipped U-net for the paper's setting, or None."""
+    return np.load(TRAINED_UNET_PAPER).astype(np.float32) if os.path.exists(TRAINED_UNET_PAPER) else None
+
+
 # ---- the U-net U3 (md_unet_*): conv3 layers (c_in, c_out), then the up2 layers
 UNET_CONVS = ((2, 32), (32, 64), (64, 128), (128, 128), (128, 64), (64, 32), (32, 1))
 UNET_UPS = ((128, 64), (64, 32))

@@ -46,3 +46,29 @@ def test_noalloc_rejects_oversized_operator():
     u = torch.zeros(op.n, dtype=torch.float64, device="cuda")
     with pytest.raises(MdError, match="MD_ERR_ARG"):
         op.apply_noalloc(u, torch.empty_like(u))
+
+
+def test_noalloc_allocates_nothing_and_runs_on_a_side_stream():
+    """After the first call (the set-up), a burst of calls on a non-default
+    stream, alternating FP32 and FP64 on the shared scratch, leaves the
+    device's free memory unchanged and gives md_apply's results."""
+    from paper_2505_08491_gb300 import Operator
+    cases = instance_cases()
+    op = Operator(*[cases[1][k] for k in (1, 2, 3)])
+    rng = np.random.default_rng(9)
+    u64 = torch.from_numpy(rng.standard_normal(op.n)).cuda()
+    u32 = u64.float()
+    ref64, ref32 = op.apply(u64), op.apply(u32)
+    o64, o32 = torch.empty_like(u64), torch.empty_like(u32)
+    side = torch.cuda.Stream()
+    op.apply_noalloc(u64, o64)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with torch.cuda.stream(side):
+        for _ in range(10):
+            op.apply_noalloc(u64, o64)
+            op.apply_noalloc(u32, o32)
+    side.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert rel_l2(o64.cpu().numpy(), ref64.cpu().numpy()) <= 1e-12
+    assert rel_l2(o32.cpu().numpy(), ref32.cpu().numpy()) <= 1e-5
