@@ -310,7 +310,8 @@ def main_unet(args):
         hist = train_unet(net, ops, sample_op, samples, epochs=args.epochs, batch=args.batch, lr=args.lr,
                           lr_min=args.lr_min, seed=args.seed)
         t2 = time.time()
-        out = args.out if args.out.endswith(".npy") else os.path.splitext(args.out)[0] + ".npy"
+        out = os.path.join(os.path.dirname(TRAINED), "unet_trained.npy") if args.out == TRAINED else args.out
+        out = out if out.endswith(".npy") else os.path.splitext(out)[0] + ".npy"
         os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
         np.save(out, net.params())
         rec.update({"workload": args.workload, "set": args.set, "zero_1d": args.zero_1d, "graphs": args.graphs,
