@@ -562,11 +562,13 @@ def main():
     stream = torch.cuda.current_stream()
 
     tol = tol_of(args.workload)
+    # the timed solves record device timestamps (the time breakdown); the graph
+    # with them is captured by the warm-up solves, outside the timed region
+    B.set_profiling(True)
     for _ in range(args.warmup):
         x_all.zero_()
         B.solve(b_all, x_all, tol=tol)
     B.reset_stats()
-    B.set_profiling(True)
     clocks = ClockSampler(local)
     clocks.start()
     total_ms = 0.0
@@ -598,6 +600,10 @@ def main():
     b_host = b_all.cpu().pin_memory()
     x_host = torch.empty_like(b_host).pin_memory()
     b_dev = torch.empty_like(b_all)
+    # the solve graph without the device timestamps is captured once, untimed
+    b_dev.copy_(b_host, non_blocking=True)
+    x_all.zero_()
+    B.solve(b_dev, x_all, tol=tol)
     barrier()
     e2e_ms = 0.0
     for _ in range(args.steps):
