@@ -619,7 +619,8 @@ md_status cnn_forward_layers(const md_cnn* c, CnnWork* w, const OutIO& io, ConvO
 }
 
 // ---- input packing -------------------------------------------------------------------
-// Network input X = [v0 / s, l / s, d] in the padded BF16 layout; and the
+// Network input X = [v0 / s, l / s, d] in the dx-paired one-chunk BF16
+// layout (store_dx_pair); and the
 // preconditioner output on Dirichlet nodes, z0 = v0 (the last layer writes
 // the interior nodes only).
 __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__ Ns, const InstDesc* __restrict__ D,
@@ -635,16 +636,18 @@ __global__ void k_pack_prec(const Seg* __restrict__ seg, const int* __restrict__
     const float sf = (float)s;
     const float* vi = v + voff[sg.inst];
     __nv_bfloat16* xo = x0 + x0off[sg.inst];
+    auto chan = [&](int m, float (&c)[3]) {
+        c[0] = s > 0.0 ? vi[m] / sf : 0.f;
+        c[1] = (s > 0.0 && use_lift) ? d.lift32[m] / sf : 0.f;
+        c[2] = d.dist[m];
+    };
     for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
         const int i = n % M, r = n / M, j = r % M, k = r / M;
         const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
-        float c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (s > 0.0) {
-            c[0] = vi[n] / sf;
-            c[1] = use_lift ? d.lift32[n] / sf : 0.f;
-        }
-        c[2] = d.dist[n];
-        *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
+        float own[3], nx[3] = {0.f, 0.f, 0.f};
+        chan(n, own);
+        if (i < N) chan(n + 1, nx);
+        store_dx_pair(xo + p * 8, own, nx, i == 0);
         if (!d.natural && (i == 0 || i == N || j == 0 || j == N || k == 0 || k == N)) z[voff[sg.inst] + n] = vi[n];
     }
 }
@@ -666,8 +669,14 @@ __global__ void k_pack_raw(const Seg* __restrict__ seg, const int* __restrict__ 
     for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
         const int i = n % M, r = n / M, j = r % M, k = r / M;
         const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
-        float c[8] = {xi[n], xi[n3 + n], xi[2 * n3 + n], 0, 0, 0, 0, 0};
-        *reinterpret_cast<uint4*>(xo + p * 8) = pack8(c);
+        const float own[3] = {xi[n], xi[n3 + n], xi[2 * n3 + n]};
+        float nx[3] = {0.f, 0.f, 0.f};
+        if (i < N) {
+            nx[0] = xi[n + 1];
+            nx[1] = xi[n3 + n + 1];
+            nx[2] = xi[2 * n3 + n + 1];
+        }
+        store_dx_pair(xo + p * 8, own, nx, i == 0);
     }
 }
 

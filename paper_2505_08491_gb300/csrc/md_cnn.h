@@ -8,8 +8,35 @@
 // (c * P + p) * 8 + l.  Halo rows are never written and stay zero, which is
 // the zero 'same' padding of every layer.  Each buffer has a zero margin of
 // CNN_MARGIN_ROWS rows before the first and after the last instance, which
-// the tensor-core windows of halo-only tiles may read.
+// the tensor-core windows of halo-only tiles may read.  The one exception to
+// zero halo rows is the dx-paired one-chunk layout below.
 #define CNN_MARGIN_ROWS 8192
+
+#ifdef __CUDACC__
+// One-chunk inputs of the first layer's kind (the network input X0, and the
+// last layer's adjoint input dY in training) are stored dx-paired: row p holds
+// the node's channels (at most 3) in lanes 0-2 and those of the next node
+// along x in lanes 3-5 (zero past the grid row's end), lanes 6-7 zero, so that
+// one 8-lane chunk carries two dx taps of the convolution; the halo row just
+// before the first node of every grid row holds that node's channels in lanes
+// 3-5.  rowp: the node's row; first: the node starts its grid row (i = 0).
+__device__ __forceinline__ void store_dx_pair(__nv_bfloat16* rowp, const float (&own)[3], const float (&next)[3],
+                                              bool first) {
+    uint4 r;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&r);
+    h[0] = __floats2bfloat162_rn(own[0], own[1]);
+    h[1] = __floats2bfloat162_rn(own[2], next[0]);
+    h[2] = __floats2bfloat162_rn(next[1], next[2]);
+    h[3] = __floats2bfloat162_rn(0.f, 0.f);
+    *reinterpret_cast<uint4*>(rowp) = r;
+    if (first) {
+        h[0] = __floats2bfloat162_rn(0.f, 0.f);
+        h[1] = __floats2bfloat162_rn(0.f, own[0]);
+        h[2] = __floats2bfloat162_rn(own[1], own[2]);
+        *reinterpret_cast<uint4*>(rowp - 8) = r;
+    }
+}
+#endif
 struct CnnWork {
     int ninst = 0;
     std::vector<void*> allocs;
@@ -31,7 +58,7 @@ struct CnnWork {
     int* run_count = nullptr;
     int ngroups = 1, tps = 2, W = 0, NS = 0, nsm = 148, pd_max = 0;
     int* err = nullptr;            // set by a timed-out wait in a conv kernel
-    __nv_bfloat16* x0 = nullptr;   // 1 chunk (3 channels + 5 zero lanes)
+    __nv_bfloat16* x0 = nullptr;   // 1 chunk, dx-paired (store_dx_pair)
     __nv_bfloat16* a = nullptr;    // 4 chunks
     __nv_bfloat16* b = nullptr;    // 4 chunks
     long long* off_x0 = nullptr;   // per instance, element offset into x0

@@ -31,11 +31,12 @@
 //               BF16 pack, 16-byte stores of the grid rows of the plane
 //               (halo rows are computed but never stored, so the zero padding
 //               is preserved).
-// The first layer (3 input channels in one 8-channel chunk) pairs two dy
-// taps of one z-window per K=16 step (the third dy with a zero-weight
-// partner) and gives every dx tap its own N = 32 MMA with the A rows moved by
-// dx (18 MMAs per tile), so its epilogue, which bounds it, reads one
-// accumulator per output and exchanges nothing between lanes; the last
+// The first layer (3 input channels) reads a one-chunk input whose row holds
+// a node's channels and its x-neighbour's (two dx taps per 8-lane chunk), so
+// one K=16 step covers four (dy, dx) taps, or two with a zero-weight dx = +2
+// partner: 3 steps per z-window, 9 MMAs of N = 32 per tile; every dx tap sums
+// into the lane's own row, so its epilogue reads one accumulator per output
+// and exchanges nothing between lanes; the last
 // (1 output channel) puts the nine (dz, dx)
 // taps side by side in N = 16 columns, so each window alone feeds 6 MMAs (3 dy
 // x 2 K-halves) and the epilogue adds the dz contributions of consecutive
@@ -399,6 +400,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
             while (ok && walk_next<TPS>(a.sched, a.Ns, wk, U)) {
                 const uint32_t pdu = (uint32_t)(a.Ns[U.inst] + 3);  // one grid row of Pd nodes, in 16-byte rows
                 const uint64_t a_lbo_pd = (uint64_t)(pdu & 0x3FFF) << 16;
+                const uint64_t a_lbo_2pd = (uint64_t)((2 * pdu - 2) & 0x3FFF) << 16;  // first layer: 2 Pd - 2 rows
                 // A offsets of the (dy, K-half) combinations, in 16-byte rows
                 uint32_t offu[3][2];
 #pragma unroll
@@ -468,22 +470,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                         if (!issues(ut)) continue;
                         const uint32_t d = tmem + (uint32_t)((bsel * TPS + ut) * NCOL);
                         if (KIND == 1) {
-                            // one 8-channel chunk: per z-window the (dy=-1, dy=0) rows in
-                            // one K=16 step (second core matrix one grid row further),
-                            // (dy=+1, zero-weight row + 1) in a second (one node further);
-                            // each dx tap its own MMA with the A rows moved by dx (the
-                            // window starts one row early, so dx = -1 is offset 0)
+                            // one dx-paired chunk (a row holds dx taps dx and dx + 1):
+                            // per z-window three K=16 steps, each two chunks at rows
+                            // (dy + 1) Pd + (dx + 1) from the window start (which is one
+                            // row early): (dy -1, dx -1 | dy 0, dx -1), (dy -1, dx +1 |
+                            // dy +1, dx -1), (dy 0, dx +1 | dy +1, dx +1); the second
+                            // chunk LBO rows after the first
 #pragma unroll
                             for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-                                for (int pr = 0; pr < 2; ++pr)
-#pragma unroll
-                                    for (int dx = 0; dx < 3; ++dx) {
-                                        const uint64_t ad = (a_hi | (pr == 0 ? a_lbo_pd : (1ULL << 16))) +
-                                                            (uint64_t)(sbu[dz] + (uint32_t)(ut * 126 + dx) + (uint32_t)(2 * pr) * pdu);
-                                        const uint64_t bd = bd0 + (uint64_t)((((dz * 2 + pr) * 3 + dx) * 2 * NCOL * 16) >> 4);
-                                        mma_bf16(d, ad, bd, IDESC, (dz > 0 || pr > 0 || dx > 0) ? 1u : 0u);
-                                    }
+                                for (int m = 0; m < 3; ++m) {
+                                    const uint32_t o0 = m == 0 ? 0u : (m == 1 ? 2u : pdu + 2u);
+                                    const uint64_t ad = (a_hi | (m == 1 ? a_lbo_2pd : a_lbo_pd)) +
+                                                        (uint64_t)(sbu[dz] + (uint32_t)(ut * 126) + o0);
+                                    const uint64_t bd = bd0 + (uint64_t)((((dz * 3 + m) * 2 * NCOL * 16)) >> 4);
+                                    mma_bf16(d, ad, bd, IDESC, (dz > 0 || m > 0) ? 1u : 0u);
+                                }
                         } else {
                             const uint64_t a0 = a_hi | a_lbo_w;
 #pragma unroll
@@ -808,8 +810,9 @@ md_status tc_launch(int kind, int tps, const TcArgs& a, int grid, cudaStream_t s
 // Weight images in the operand layout the MMAs read (n = dx index * 32 + o,
 // i.e. the three dx taps of one (dy, dz) side by side):
 //   kind 0: [combo = dz*3+dy (9)][k-chunk 4][n 96][8]
-//   kind 1: [dz 3][pair 2][dx 3][k-chunk 2][n 32][8]; pair 0 = (dy -1, dy 0),
-//           pair 1 = (dy +1, zero); one dx tap per MMA
+//   kind 1: [dz 3][step m 3][k-chunk 2][n 32][8]; chunk (dy, dx) of step m as
+//           the MMA loop lists them, lanes 0-2 channel l at tap dx, lanes 3-5
+//           channel l - 3 at tap dx + 1 (zero for dx + 1 = 2), lanes 6-7 zero
 //   kind 2: [dy 3][k-chunk 4][n 16][8]; n = 3 dz + dx for o = 0 (9 columns), rest zero
 void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__nv_bfloat16>& img) {
     img.assign(tc_wimg_bytes(kind) / 2, __float2bfloat16_rn(0.0f));
@@ -818,18 +821,19 @@ void tc_weight_image(int kind, const float* W, int cin, int cout, std::vector<__
         return W[((size_t)o * cin + c) * 27 + tap];
     };
     if (kind == 1) {
+        // (dy, dx) + 1 of the two chunks of each step
+        static const int chunk_dy[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        static const int chunk_dx[3][2] = {{0, 0}, {2, 0}, {2, 2}};
         for (int dz = 0; dz < 3; ++dz)
-            for (int pr = 0; pr < 2; ++pr)
-                for (int dx = 0; dx < 3; ++dx)
-                    for (int half = 0; half < 2; ++half) {
-                        const int dy = 2 * pr + half;  // 3 = zero partner
-                        for (int o = 0; o < 32; ++o)
-                            for (int l = 0; l < 8; ++l) {
-                                const float v = dy < 3 ? w_at(o, l, dz * 9 + dy * 3 + dx) : 0.0f;
-                                img[((size_t)(((dz * 2 + pr) * 3 + dx) * 2 + half) * 32 + o) * 8 + l] =
-                                    __float2bfloat16_rn(v);
-                            }
-                    }
+            for (int m = 0; m < 3; ++m)
+                for (int half = 0; half < 2; ++half)
+                    for (int o = 0; o < 32; ++o)
+                        for (int l = 0; l < 6; ++l) {
+                            const int dy = chunk_dy[m][half], dx = chunk_dx[m][half] + (l >= 3 ? 1 : 0);
+                            const int ch = l % 3;
+                            const float v = dx < 3 ? w_at(o, ch, dz * 9 + dy * 3 + dx) : 0.0f;
+                            img[((size_t)((dz * 3 + m) * 2 + half) * 32 + o) * 8 + l] = __float2bfloat16_rn(v);
+                        }
     } else if (kind == 0) {
         for (int combo = 0; combo < 9; ++combo)
             for (int kc = 0; kc < 4; ++kc)

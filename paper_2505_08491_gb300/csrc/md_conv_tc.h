@@ -57,12 +57,12 @@ struct TcArgs {
 };
 
 __host__ __device__ constexpr int tc_wimg_bytes(int kind) {
-    return kind == 1 ? 3 * 2 * 3 * 2 * 32 * 16 : (kind == 2 ? 3 * 4 * 16 * 16 : 9 * 4 * 96 * 16);
+    return kind == 1 ? 3 * 3 * 2 * 32 * 16 : (kind == 2 ? 3 * 4 * 16 * 16 : 9 * 4 * 96 * 16);
 }
 // rows one window copy holds: TPS tiles 126 rows apart, 128 rows each, read
 // at dy offsets 0..2 Pd from the window start, plus 8 rows of slack (the
-// first layer's window starts one row early and reads up to 4 rows past the
-// last tile's dy = +1 rows: dx = +1 and the zero-weight partner row)
+// first layer's window starts one row early and reads up to 2 rows past the
+// last tile's dy = +1 rows: its dx = +1 chunk)
 __host__ __device__ constexpr int tc_window_load_rows(int tps, int pd) { return (tps - 1) * 126 + 128 + 2 * pd + 8; }
 __host__ __device__ constexpr int tc_align(int b) { return (b + 1023) & ~1023; }
 

@@ -276,7 +276,7 @@ __global__ void k_train_res(const Seg* __restrict__ seg, const InstDesc* __restr
 }
 
 // dY (network output gradient) = scale * (C res) on interior nodes, packed
-// as channel 0 of a one-chunk BF16 padded buffer
+// as channel 0 of a dx-paired one-chunk BF16 padded buffer
 __global__ void k_train_dy(const Seg* __restrict__ seg, const InstDesc* __restrict__ D, const long long* __restrict__ off,
                            const float* __restrict__ cres, float scale, __nv_bfloat16* __restrict__ dy,
                            const long long* __restrict__ dy_off) {
@@ -287,13 +287,14 @@ __global__ void k_train_dy(const Seg* __restrict__ seg, const InstDesc* __restri
     for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
         const int i = n % M, r = n / M, j = r % M, k = r / M;
         const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
-        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (d.natural || !is_bd(n, N)) v[0] = scale * cres[off[sg.inst] + n] / (float)d.alpha;
-        *reinterpret_cast<uint4*>(dy + dy_off[sg.inst] + p * 8) = pack8(v);
+        float own[3] = {0.f, 0.f, 0.f}, nx[3] = {0.f, 0.f, 0.f};
+        if (d.natural || !is_bd(n, N)) own[0] = scale * cres[off[sg.inst] + n] / (float)d.alpha;
+        if (i < N && (d.natural || !is_bd(n + 1, N))) nx[0] = scale * cres[off[sg.inst] + n + 1] / (float)d.alpha;
+        store_dx_pair(dy + dy_off[sg.inst] + p * 8, own, nx, i == 0);
     }
 }
 
-// raw dY (FP32 grid per sample) -> one-chunk BF16 padded buffer
+// raw dY (FP32 grid per sample) -> dx-paired one-chunk BF16 padded buffer
 __global__ void k_pack_dy_raw(const Seg* __restrict__ seg, const int* __restrict__ Ns, const float* __restrict__ dY,
                               __nv_bfloat16* __restrict__ dy, const long long* __restrict__ dy_off) {
     const Seg sg = seg[blockIdx.x];
@@ -302,8 +303,9 @@ __global__ void k_pack_dy_raw(const Seg* __restrict__ seg, const int* __restrict
     for (int n = sg.begin + threadIdx.x; n < sg.end; n += blockDim.x) {
         const int i = n % M, r = n / M, j = r % M, k = r / M;
         const long long p = (i + 1) + Pd * ((j + 1) + Pd * (k + 1));
-        float v[8] = {dY[sg.inst * n3 + n], 0, 0, 0, 0, 0, 0, 0};
-        *reinterpret_cast<uint4*>(dy + dy_off[sg.inst] + p * 8) = pack8(v);
+        const float own[3] = {dY[sg.inst * n3 + n], 0.f, 0.f};
+        const float nx[3] = {i < N ? dY[sg.inst * n3 + n + 1] : 0.f, 0.f, 0.f};
+        store_dx_pair(dy + dy_off[sg.inst] + p * 8, own, nx, i == 0);
     }
 }
 
