@@ -40,7 +40,7 @@
 // (1 output channel) puts the nine (dz, dx)
 // taps side by side in N = 16 columns, so each window alone feeds 6 MMAs (3 dy
 // x 2 K-halves) and the epilogue adds the dz contributions of consecutive
-// windows in registers.
+// windows in registers (one group of 4 epilogue warps per tile of a step).
 //
 // Every mbarrier wait is bounded (2 s of globaltimer); on timeout the kernel
 // sets an error flag, waits (bounded) for its own work in flight, frees its
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         }
         for (int i = 0; i < NBUF; ++i) {
             mbar_init(&tfull[i], TC_MMA_WARPS);  // every issuer's MMAs of the step
-            mbar_init(&tempty[i], KIND == 2 ? 4 : TC_EPI_WARPS);  // last layer: one channel group
+            mbar_init(&tempty[i], KIND == 2 ? 4 * TPS : TC_EPI_WARPS);  // last layer: one channel group per tile
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -534,11 +534,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
         float bias[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) bias[c] = (KIND == 2) ? a.bias[0] : a.bias[cg * CH + c];
-        const bool writer = KIND != 2 || cg == 0;
+        // the last layer's single output channel: channel group cg handles tile
+        // cg of every step (its own accumulator columns, lane exchange and dz
+        // sums); groups beyond the tiles of a step go straight to the end
+        const bool writer = KIND != 2 || cg < TPS;
         int it = 0, xcnt = 0;
-        // the last layer's single output channel is handled by channel group 0
-        // alone; the other epilogue warps go straight to the end
-        bool ok = KIND != 2 || cg == 0;
+        bool ok = writer;
         TcWalk wk = walk_begin(a.sched);
         TcUnit U;
         while (ok && walk_next<TPS>(a.sched, a.Ns, wk, U)) {
@@ -586,6 +587,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     float v[TPS][16];
 #pragma unroll
                     for (int ut = 0; ut < TPS; ++ut) {
+                        if (ut != cg) continue;
                         const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((bsel * TPS + ut) * NCOL);
                         float* lo = v[ut];
                         tmem_ld_nowait<8>(tb, *reinterpret_cast<float(*)[8]>(lo));
@@ -599,6 +601,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     float* xb = xch + (size_t)xbuf * (TPS * 4 * TC_EPI_GROUPS * 2 * TC_EPI_CH);
 #pragma unroll
                     for (int ut = 0; ut < TPS; ++ut) {
+                        if (ut != cg) continue;
                         float* mine = xb + ((ut * 4 + q) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
                         if (lane == 31)
 #pragma unroll
@@ -611,6 +614,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv_tc(TcArgs a) {
                     ++xcnt;
 #pragma unroll
                     for (int ut = 0; ut < TPS; ++ut) {
+                        if (ut != cg) continue;
                         const float* prev = xb + ((ut * 4 + ((q + 3) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH;
                         const float* next = xb + ((ut * 4 + ((q + 1) & 3)) * TC_EPI_GROUPS + cg) * 2 * TC_EPI_CH + TC_EPI_CH;
                         float P[3];
