@@ -606,18 +606,22 @@ def main():
     B.solve(b_dev, x_all, tol=tol)
     barrier()
     e2e_ms = 0.0
+    e2e_parts = [0.0, 0.0, 0.0]  # b in, solve (with its result read), x out
     for _ in range(args.steps):
         flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         b_dev.copy_(b_host, non_blocking=True)
+        ev[1].record(stream)
         x_all.zero_()
         B.solve(b_dev, x_all, tol=tol)
+        ev[2].record(stream)
         x_host.copy_(x_all, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms += e0.elapsed_time(e1)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        e2e_ms += ev[0].elapsed_time(ev[3])
+        for k in range(3):
+            e2e_parts[k] += ev[k].elapsed_time(ev[k + 1])
     _, _, e2e_value = job_throughput(e2e_ms, args.count * args.steps, world, "cuda", dist)
 
     # Jacobi-CG on the same batch and GPU
@@ -704,7 +708,9 @@ def main():
             "other_workloads": other,
             "roofline": roofline, "time_breakdown_ms": breakdown,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(b_all.numel() * 8),
-                    "d2h_bytes_per_step": int(x_all.numel() * 8)},
+                    "d2h_bytes_per_step": int(x_all.numel() * 8),
+                    "ms_per_step": {"h2d": e2e_parts[0] / args.steps, "solve": e2e_parts[1] / args.steps,
+                                    "d2h": e2e_parts[2] / args.steps}},
             "gpu_launches": int(stats["kernel_launches"]),
             "launches_per_solve": {"host_graph_launches": stats["graph_launches"] / args.steps,
                                    "kernels_run": stats["kernel_launches"] / args.steps, "slot_gating": stats["slot_gating"],

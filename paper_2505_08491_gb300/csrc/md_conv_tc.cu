@@ -77,17 +77,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false (and the error flag set) after ~2 s.
+// Bounded wait: false (and the error flag set) after ~2 s.  The error flag
+// (another role gave up) is read only once a wait has lasted 20 us, so that an
+// ordinary wait never has a global load in flight when its phase completes.
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
         for (int i = 0; i < 4; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (*(volatile int*)err) return false;
-        if (globaltimer() - t0 > 2000000000ULL) {
-            atomicExch(err, 1);
-            return false;
+        const unsigned long long dt = globaltimer() - t0;
+        if (dt > 20000ULL) {
+            if (*(volatile int*)err) return false;
+            if (dt > 2000000000ULL) {
+                atomicExch(err, 1);
+                return false;
+            }
         }
     }
 }
