@@ -7,6 +7,8 @@ Tensors are torch CUDA tensors (torch provides device memory and streams).
 from __future__ import annotations
 
 import ctypes as C
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 import torch
@@ -178,6 +180,33 @@ class Operator:
                                       int(maxit), C.byref(it), C.byref(rr), _stream()),
                     "md_solve", allow=(L.MD_OK, L.MD_NOT_CONVERGED))
         return x, it.value, rr.value, s == L.MD_OK
+
+
+def assemble(specs, threads: int | None = None) -> list[Operator]:
+    """Operators of several independent instances, assembled on host threads.
+
+    specs: one (N, graph, beta, keyword arguments of Operator) tuple per
+    instance; the result is in the order of specs.  Each instance is one
+    md_assemble call, whose FP64 geometry runs on the calling host thread (the
+    call releases the interpreter lock) and whose uploads and distance-field
+    kernel go to the current device of the caller, so instances are built
+    side by side on up to `threads` host cores (default: the cores available)."""
+    specs = list(specs)
+    if not specs:
+        return []
+    torch.cuda.init()
+    dev = torch.cuda.current_device()
+
+    def one(spec):
+        torch.cuda.set_device(dev)
+        N, graph, beta, kw = spec
+        return Operator(N, graph, beta, **kw)
+
+    workers = min(len(specs), threads if threads else (len(os.sched_getaffinity(0)) or 1))
+    if workers <= 1:
+        return [one(sp) for sp in specs]
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        return list(pool.map(one, specs))
 
 
 class Network:
