@@ -310,26 +310,90 @@ md_status launch_rhs(const md_op* op, const double* f, double g, double* b, cuda
 }
 
 // ---- distance field d_h: min over the graph's straight segments, FP64
-__global__ void k_dist(const InstDesc* __restrict__ D) {
+// Squared distance from a grid point to segment e in FP64 (NaN for a segment
+// of zero length, which the minimum then ignores).
+__device__ __forceinline__ double seg_q64(const double* sg, double px, double py, double pz) {
+    const double ax = sg[0], ay = sg[1], az = sg[2];
+    const double dx = sg[3] - ax, dy = sg[4] - ay, dz = sg[5] - az;
+    const double dd = dx * dx + dy * dy + dz * dz;
+    double t = ((px - ax) * dx + (py - ay) * dy + (pz - az) * dz) / dd;
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+    const double ex = px - (ax + t * dx), ey = py - (ay + t * dy), ez = pz - (az + t * dz);
+    return ex * ex + ey * ey + ez * ez;
+}
+
+// Segments staged in shared memory for the FP32 search: start point, direction,
+// 1 / squared length; a zero-length segment is staged far away (never nearest).
+#define DIST_CHUNK 256
+__device__ __forceinline__ void stage_seg(float* s7, const double* sg) {
+    const double dx = sg[3] - sg[0], dy = sg[4] - sg[1], dz = sg[5] - sg[2];
+    const double dd = dx * dx + dy * dy + dz * dz;
+    const bool ok = dd > 0.0;
+    s7[0] = ok ? (float)sg[0] : 1e18f;
+    s7[1] = (float)sg[1];
+    s7[2] = (float)sg[2];
+    s7[3] = ok ? (float)dx : 0.f;
+    s7[4] = ok ? (float)dy : 0.f;
+    s7[5] = ok ? (float)dz : 0.f;
+    s7[6] = ok ? (float)(1.0 / dd) : 0.f;
+}
+__device__ __forceinline__ float seg_q32(const float* s7, float fx, float fy, float fz) {
+    const float ux = fx - s7[0], uy = fy - s7[1], uz = fz - s7[2];
+    float t = (ux * s7[3] + uy * s7[4] + uz * s7[5]) * s7[6];
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float ex = ux - t * s7[3], ey = uy - t * s7[4], ez = uz - t * s7[5];
+    return ex * ex + ey * ey + ez * ez;
+}
+
+// The minimum over all segments is searched in FP32, then taken in FP64 over
+// the segments whose FP32 value lies within 1e-5 of the FP32 minimum: with
+// coordinates in [0, 1] an FP32 squared distance is within ~2e-6 of its FP64
+// value, so the FP64 minimiser is always among them and d_h is the FP64
+// minimum over every segment (FP64 runs at a small fraction of the FP32 rate
+// on this GPU; the FP64 pass now touches one to a few segments per node).
+__global__ void __launch_bounds__(MD_TB) k_dist(const InstDesc* __restrict__ D) {
+    __shared__ float sseg[DIST_CHUNK * 7];
     const InstDesc& d = *D;
-    const int N = d.N, M = N + 1;
+    const int N = d.N, M = N + 1, S = d.nsegs;
     float* out = const_cast<float*>(d.dist);
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < d.n3; n += gridDim.x * blockDim.x) {
-        const int i = n % M, r = n / M, j = r % M, k = r / M;
-        const double px = (double)i / N, py = (double)j / N, pz = (double)k / N;
-        double best = 1e300;
-        for (int e = 0; e < d.nsegs; ++e) {
-            const double* sg = d.segs + 6 * e;
-            const double ax = sg[0], ay = sg[1], az = sg[2];
-            const double dx = sg[3] - ax, dy = sg[4] - ay, dz = sg[5] - az;
-            const double dd = dx * dx + dy * dy + dz * dz;
-            double t = ((px - ax) * dx + (py - ay) * dy + (pz - az) * dz) / dd;
-            t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
-            const double ex = px - (ax + t * dx), ey = py - (ay + t * dy), ez = pz - (az + t * dz);
-            const double q = ex * ex + ey * ey + ez * ez;
-            best = q < best ? q : best;
+    const float invN = 1.0f / (float)N;
+    // block-uniform trips: every thread takes part in the staging
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < d.n3; base += (long long)gridDim.x * blockDim.x) {
+        const int n = (int)base + threadIdx.x;
+        const bool valid = n < d.n3;
+        int i = 0, j = 0, k = 0;
+        if (valid) {
+            i = n % M;
+            const int r = n / M;
+            j = r % M;
+            k = r / M;
         }
-        out[n] = (float)sqrt(best);
+        const float fx = i * invN, fy = j * invN, fz = k * invN;
+        const double px = (double)i / N, py = (double)j / N, pz = (double)k / N;
+        float best32 = 3.0e38f;
+        for (int c0 = 0; c0 < S; c0 += DIST_CHUNK) {
+            const int cn = min(DIST_CHUNK, S - c0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < cn; e += blockDim.x) stage_seg(sseg + 7 * e, d.segs + 6 * (c0 + e));
+            __syncthreads();
+            for (int e = 0; e < cn; ++e) best32 = fminf(best32, seg_q32(sseg + 7 * e, fx, fy, fz));
+        }
+        const float lim = best32 + 1e-5f;
+        double best = 1e300;
+        for (int c0 = 0; c0 < S; c0 += DIST_CHUNK) {
+            const int cn = min(DIST_CHUNK, S - c0);
+            if (S > DIST_CHUNK) {  // one chunk stays staged from the search
+                __syncthreads();
+                for (int e = threadIdx.x; e < cn; e += blockDim.x) stage_seg(sseg + 7 * e, d.segs + 6 * (c0 + e));
+                __syncthreads();
+            }
+            for (int e = 0; e < cn; ++e)
+                if (seg_q32(sseg + 7 * e, fx, fy, fz) <= lim) {
+                    const double q = seg_q64(d.segs + 6 * (c0 + e), px, py, pz);
+                    best = q < best ? q : best;
+                }
+        }
+        if (valid) out[n] = (float)sqrt(best);
     }
 }
 
